@@ -1,0 +1,406 @@
+"""Pins of the FP64 CPU oracle against facts that do not come from the oracle.
+
+Each test checks one part of the oracle against a library routine, a closed
+form, an exact identity or a brute-force case, so that a dropped term, a
+wrong sign or index, or a transposed operand in the oracle fails one of them:
+
+* Philox4x32-10       -> cuRAND's host Philox4x32-10 generator (library)
+* hot start            -> Haar moments; <P> = 0 at beta = 0 (closed form)
+* cold start           -> P = L = C(r) = 1 exactly (definitions, Sec. 2.1/2.2)
+* plaquette indices    -> abelian (U(1)-embedded) closed form
+* staple               -> sum_x,mu 1/2 Tr(U A) = 24 V P (exact identity)
+* gauge invariance     -> P, L, C(r) unchanged by a random g(x) (Sec. 2.2, Eq. 3)
+* Polyakov / C(r)      -> constant-link closed form cos(Nt theta); brute force
+* Kennedy-Pendleton    -> KS test against the exact density sqrt(1-a0^2)e^{alpha a0},
+                          mean I2(alpha)/I1(alpha) (Bessel functions, scipy)
+* U_new = X Vhat^+     -> <1/2 Tr(U A)/k> = I2(beta k)/I1(beta k), isotropy
+* checkerboard         -> a phase touches only its links; site order irrelevant
+* whole chain          -> strong coupling <P> = I2(beta)/I1(beta) at beta = 0.5,
+                          weak coupling beta (1 - <P>) -> 3/4
+"""
+import ctypes
+import ctypes.util
+import glob
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, special, stats
+
+from oracle import oracle as O
+from paper_1104_5432_gb300 import inputs
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10 against cuRAND's host generator
+# --------------------------------------------------------------------------
+def _curand():
+    cands = []
+    found = ctypes.util.find_library("curand")
+    if found:
+        cands.append(found)
+    for d in ("/usr/local/cuda/lib64", "/usr/local/cuda/targets/sbsa-linux/lib",
+              "/usr/local/cuda/targets/x86_64-linux/lib"):
+        cands += sorted(glob.glob(os.path.join(d, "libcurand.so*")))
+    for c in cands:
+        try:
+            return ctypes.CDLL(c)
+        except OSError:
+            continue
+    return None
+
+
+CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161
+
+
+def _curand_host_words(lib, seed, offset, n):
+    gen = ctypes.c_void_p()
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), CURAND_RNG_PSEUDO_PHILOX4_32_10) == 0
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
+        buf = (ctypes.c_uint32 * n)()
+        assert lib.curandGenerate(gen, buf, ctypes.c_size_t(n)) == 0
+        return np.array(buf, dtype=np.uint32)
+    finally:
+        lib.curandDestroyGenerator(gen)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 0x123456789ABCDEF, 0xFFFFFFFFFFFFFFFF])
+@pytest.mark.parametrize("block0", [0, 65536 * 3 + 17, 65536 * (2 ** 32 + 5) + 65533])
+def test_philox_matches_curand_host(seed, block0):
+    """cuRAND's host Philox generator emits, for output block B (four words),
+    Philox4x32-10 of counter (B div 65536 as 64 bits in words 0..1,
+    B mod 65536 in word 2, 0) under key (seed lo, seed hi).  The last case
+    puts a non-zero value in counter words 0, 1 and 2 at once."""
+    lib = _curand()
+    if lib is None:
+        pytest.skip("libcurand not found")
+    nblk = 6
+    words = _curand_host_words(lib, seed, 4 * block0, 4 * nblk)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for j in range(nblk):
+        B = block0 + j
+        hi = B // 65536
+        ctr = [hi & 0xFFFFFFFF, hi >> 32, B % 65536, 0]
+        np.testing.assert_array_equal(O.philox(ctr, key), words[4 * j:4 * j + 4])
+
+
+def test_u01_cells():
+    # the 2^23 cells are centred: smallest 2^-24, largest 1 - 2^-24, symmetric
+    assert O.u01(0) == 2.0 ** -24
+    assert O.u01(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+    for w in (0x12345678, 0x80000000, 0xDEADBEEF):
+        assert O.u01(w) + O.u01(0xFFFFFFFF - w) == 1.0
+    # only the top 23 bits matter
+    assert O.u01(0x1FF) == O.u01(0)
+
+
+# --------------------------------------------------------------------------
+# start configurations and observables
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("Ns,Nt", [(4, 4), (4, 6), (6, 2)])
+def test_cold_start_exact(Ns, Nt):
+    links = O.init(Ns, Nt, hot=False, seed=0)
+    assert O.plaquette(Ns, Nt, links) == 1.0
+    m, a, field = O.polyakov(Ns, Nt, links)
+    assert m == 1.0 and a == 1.0 and np.all(field == 1.0)
+    np.testing.assert_array_equal(O.correlator(Ns, Nt, links, Ns // 2), np.ones(Ns // 2 + 1))
+
+
+def test_hot_start_haar_moments():
+    Ns, Nt = 8, 8
+    links = O.init(Ns, Nt, hot=True, seed=1).reshape(-1, 4)
+    n = links.shape[0]
+    np.testing.assert_allclose(np.linalg.norm(links, axis=1), 1.0, atol=1e-14)
+    # Haar on S^3: <a_i> = 0, <a_i^2> = 1/4 (var of a_i^2 is 1/8 - 1/16 = 1/16)
+    assert np.all(np.abs(links.mean(0)) < 5 * 0.5 / np.sqrt(n))
+    assert np.all(np.abs((links ** 2).mean(0) - 0.25) < 5 * 0.25 / np.sqrt(n))
+    # <P> = 0 for independent Haar links (beta = 0), sd of one plaquette 1/2
+    links = links.reshape(-1, 4, 4)
+    P = O.plaquette(Ns, Nt, links)
+    assert abs(P) < 5 * 0.5 / np.sqrt(6 * Ns ** 3 * Nt)
+    # different seeds give different configurations
+    assert not np.array_equal(O.init(4, 4, True, 1), O.init(4, 4, True, 2))
+
+
+def _abelian(theta):
+    """theta[V,4] -> links exp(i theta sigma_3) = (cos theta, 0, 0, sin theta)"""
+    q = np.zeros(theta.shape + (4,))
+    q[..., 0] = np.cos(theta)
+    q[..., 3] = np.sin(theta)
+    return np.ascontiguousarray(q)
+
+
+@pytest.mark.parametrize("Ns,Nt", [(4, 4), (4, 6)])
+def test_plaquette_abelian_closed_form(Ns, Nt):
+    """For commuting links exp(i theta sigma_3) the plaquette is
+    cos(theta_mu(x) + theta_nu(x+mu) - theta_mu(x+nu) - theta_nu(x))."""
+    rng = np.random.default_rng(3)
+    th = rng.uniform(-np.pi, np.pi, size=(Nt, Ns, Ns, Ns, 4))  # [t,z,y,x,mu]
+    links = _abelian(th.reshape(-1, 4))
+    axis = {0: 3, 1: 2, 2: 1, 3: 0}  # direction -> array axis of [t,z,y,x]
+    tot = 0.0
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            fwd_mu = lambda a: np.roll(a, -1, axis=axis[mu])
+            fwd_nu = lambda a: np.roll(a, -1, axis=axis[nu])
+            ang = th[..., mu] + fwd_mu(th[..., nu]) - fwd_nu(th[..., mu]) - th[..., nu]
+            tot += np.cos(ang).sum()
+    expect = tot / (6 * Ns ** 3 * Nt)
+    assert abs(O.plaquette(Ns, Nt, links) - expect) < 1e-14
+
+
+@pytest.mark.parametrize("Ns,Nt,seed", [(2, 2, 1), (4, 4, 2), (4, 6, 3), (6, 4, 4)])
+def test_staple_identity(Ns, Nt, seed):
+    """Every plaquette holds four links, so sum_{x,mu} 1/2 Re Tr(U_mu(x) A_mu(x))
+    = 4 * 6V * <P> exactly (up to rounding) for ANY configuration."""
+    links = inputs.random_links(Ns, Nt, seed)
+    V = Ns ** 3 * Nt
+    lhs = O.staple_trace_sum(Ns, Nt, links)
+    rhs = 24 * V * O.plaquette(Ns, Nt, links)
+    assert abs(lhs - rhs) < 1e-12 * V
+
+
+def test_staple_is_multiple_of_su2():
+    links = inputs.random_links(4, 4, 5)
+    for lex, mu in [(0, 0), (17, 1), (100, 2), (255, 3)]:
+        A = O.staple(4, 4, links, lex, mu)
+        assert np.linalg.norm(A) <= 6.0 + 1e-12
+    # cold start: each of the six staples is the identity
+    cold = O.init(4, 4, False, 0)
+    np.testing.assert_array_equal(O.staple(4, 4, cold, 9, 2), [6.0, 0, 0, 0])
+
+
+@pytest.mark.parametrize("Ns,Nt,sweeps", [(4, 4, 0), (4, 6, 2), (6, 2, 1)])
+def test_gauge_invariance(Ns, Nt, sweeps):
+    links = O.init(Ns, Nt, True, 11)
+    if sweeps:
+        links, _, _ = O.heatbath(Ns, Nt, links, 2.2, sweeps, 5)
+    g = O.gauge_transform(Ns, Nt, links, 99)
+    assert np.max(np.abs(g - links)) > 0.1  # the links really changed
+    assert abs(O.plaquette(Ns, Nt, g) - O.plaquette(Ns, Nt, links)) < 1e-14
+    m0, a0, f0 = O.polyakov(Ns, Nt, links)
+    m1, a1, f1 = O.polyakov(Ns, Nt, g)
+    np.testing.assert_allclose(f1, f0, atol=1e-14, rtol=0)
+    np.testing.assert_allclose(O.correlator(Ns, Nt, g, Ns // 2),
+                               O.correlator(Ns, Nt, links, Ns // 2), atol=1e-14, rtol=0)
+    assert np.max(np.abs(np.linalg.norm(g, axis=2) - 1)) < 1e-14
+
+
+@pytest.mark.parametrize("Nt", [2, 4, 6])
+def test_polyakov_constant_links(Nt):
+    """U_3(x,t) = W = (cos th, sin th n) for all sites gives L = cos(Nt th)."""
+    Ns = 4
+    th = 0.37
+    n = np.array([0.48, -0.6, 0.64])
+    links = O.init(Ns, Nt, False, 0)
+    links[:, 3, 0] = np.cos(th)
+    links[:, 3, 1:] = np.sin(th) * n
+    m, a, field = O.polyakov(Ns, Nt, links)
+    np.testing.assert_allclose(field, np.cos(Nt * th), atol=1e-14)
+    np.testing.assert_allclose(O.correlator(Ns, Nt, links, 2), np.cos(Nt * th) ** 2, atol=1e-14)
+
+
+def test_polyakov_single_slice_and_correlator_brute_force():
+    """Only U_3(x, t=0) differs from 1, so L(x) = a0(U_3(x,0)); the
+    correlator is then checked against a brute-force sum over shifts."""
+    Ns, Nt = 6, 4
+    links = O.init(Ns, Nt, False, 0)
+    q = inputs.random_unit_quaternions(Ns ** 3, 21)
+    links[:Ns ** 3, 3, :] = q
+    m, a, field = O.polyakov(Ns, Nt, links)
+    np.testing.assert_allclose(field, q[:, 0], atol=1e-15)
+    assert abs(m - q[:, 0].mean()) < 1e-15 and abs(a - abs(q[:, 0].mean())) < 1e-15
+    Lg = q[:, 0].reshape(Ns, Ns, Ns)  # [z,y,x]
+    expect = []
+    for r in range(Ns // 2 + 1):
+        s = 0.0
+        for z in range(Ns):
+            for y in range(Ns):
+                for x in range(Ns):
+                    s += Lg[z, y, x] * (Lg[z, y, (x + r) % Ns] + Lg[z, (y + r) % Ns, x]
+                                        + Lg[(z + r) % Ns, y, x])
+        expect.append(s / (3 * Ns ** 3))
+    np.testing.assert_allclose(O.correlator(Ns, Nt, links, Ns // 2), expect, atol=1e-15)
+    with pytest.raises(ValueError):
+        O.correlator(Ns, Nt, links, Ns // 2 + 1)
+
+
+# --------------------------------------------------------------------------
+# the Kennedy-Pendleton sampler and the link update
+# --------------------------------------------------------------------------
+def _a0_cdf(alpha):
+    """Exact CDF of the density proportional to sqrt(1-a0^2) exp(alpha a0)
+    on [-1,1], built with a0 = cos(theta): density sin^2 theta exp(alpha
+    (cos theta - 1)) on [0, pi]; normaliser pi I1(alpha) e^-alpha / alpha."""
+    z = np.pi * special.ive(1, alpha) / alpha
+    th = np.linspace(0.0, np.pi, 4001)
+    f = lambda t: np.sin(t) ** 2 * np.exp(alpha * (np.cos(t) - 1.0))
+    pieces = [integrate.quad(f, th[i], th[i + 1], epsabs=1e-14)[0] for i in range(len(th) - 1)]
+    tail = np.concatenate([[0.0], np.cumsum(pieces)])  # mass in [0, theta]
+    assert abs(tail[-1] - z) < 1e-9 * z
+    a0_grid = np.cos(th)[::-1]
+    cdf_grid = (1.0 - tail / z)[::-1]  # P(a0' <= cos theta) = mass in [theta, pi]
+
+    def cdf(a0):
+        return np.interp(a0, a0_grid, cdf_grid)
+    return cdf
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 5.0, 20.0, 60.0])
+def test_kp_sampler_distribution(alpha):
+    n = 100000
+    a0, trials = O.kp_samples(alpha, seed=1234 + int(alpha * 10), sweep=3, n=n)
+    assert np.all(trials >= 1)
+    assert np.all((a0 >= -1.0) & (a0 <= 1.0))
+    ks = stats.kstest(a0, _a0_cdf(alpha))
+    assert ks.pvalue > 1e-4, ks
+    mean = special.ive(2, alpha) / special.ive(1, alpha)
+    assert abs(a0.mean() - mean) < 5 * a0.std() / np.sqrt(n)
+
+
+def test_kp_sampler_rejects_wrong_alpha():
+    """The KS test does see a factor-two error in alpha (guards the pin itself)."""
+    a0, _ = O.kp_samples(5.0, seed=77, sweep=0, n=100000)
+    assert stats.kstest(a0, _a0_cdf(10.0)).pvalue < 1e-10
+    assert stats.kstest(a0, _a0_cdf(2.5)).pvalue < 1e-10
+
+
+def test_update_from_staple_conditional_law():
+    """For a fixed staple A = k Vhat, the heat-bath link U satisfies
+    1/2 Tr(U Vhat) ~ sqrt(1-a0^2) exp(beta k a0) and the vector part of
+    U Vhat is isotropic."""
+    beta, k = 2.0, 2.7
+    V = inputs.random_unit_quaternions(1, 8)[0]
+    A = k * V
+    n = 20000
+    a0 = np.empty(n)
+    vec = np.empty((n, 3))
+    # quaternion product written out for the check only: (U Vhat)
+    for i in range(n):
+        U, t = O.update_from_staple(A, beta, seed=4242, c0=i, sweep=7)
+        assert t >= 1
+        u0, u1, u2, u3 = U
+        v0, v1, v2, v3 = V
+        # matrices: U = u0 + i u.sigma; product via 2x2 complex matrices
+        Um = np.array([[u0 + 1j * u3, u2 + 1j * u1], [-u2 + 1j * u1, u0 - 1j * u3]])
+        Vm = np.array([[v0 + 1j * v3, v2 + 1j * v1], [-v2 + 1j * v1, v0 - 1j * v3]])
+        P = Um @ Vm
+        a0[i] = 0.5 * (P[0, 0] + P[1, 1]).real
+        vec[i] = [0.5 * (P[0, 1] + P[1, 0]).imag, 0.5 * (P[0, 1] - P[1, 0]).real,
+                  0.5 * (P[0, 0] - P[1, 1]).imag]
+    alpha = beta * k
+    expect = special.ive(2, alpha) / special.ive(1, alpha)
+    assert abs(a0.mean() - expect) < 5 * a0.std() / np.sqrt(n)
+    assert stats.kstest(a0, _a0_cdf(alpha)).pvalue > 1e-4
+    np.testing.assert_allclose(a0 ** 2 + (vec ** 2).sum(1), 1.0, atol=1e-13)
+    u = vec / np.linalg.norm(vec, axis=1, keepdims=True)
+    assert np.all(np.abs(u.mean(0)) < 5 * np.sqrt(1 / 3 / n))
+    assert np.all(np.abs((u ** 2).mean(0) - 1 / 3) < 5 * np.sqrt(4 / 45 / n))
+
+
+def test_update_degenerate_cases():
+    # zero staple: Haar draw, zero trials, unit quaternion
+    U, t = O.update_from_staple([0, 0, 0, 0], 2.3, seed=1, c0=5, sweep=0)
+    assert t == 0 and abs(np.linalg.norm(U) - 1) < 1e-15
+    # beta = 0: also the Haar draw (the exact alpha -> 0 limit)
+    U2, t2 = O.update_from_staple([1, 0, 0, 0], 0.0, seed=1, c0=5, sweep=0)
+    assert t2 == 0 and np.array_equal(U, U2)
+    # vanishing alpha > 0: Kennedy-Pendleton rejects every trial -> cap hit
+    U3, t3 = O.update_from_staple([1, 0, 0, 0], 1e-9, seed=1, c0=5, sweep=0)
+    assert t3 == -1
+
+
+# --------------------------------------------------------------------------
+# phases and sweeps
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mu,parity", [(0, 0), (1, 1), (3, 0), (2, 1)])
+def test_phase_touches_only_its_links_and_is_order_free(mu, parity):
+    Ns, Nt = 4, 6
+    links = inputs.random_links(Ns, Nt, 31)
+    new, trials, cnt = O.heatbath_phase(Ns, Nt, links, 2.4, mu, parity, seed=9, sweep=4)
+    rev, trials_r, _ = O.heatbath_phase(Ns, Nt, links, 2.4, mu, parity, seed=9, sweep=4,
+                                        reverse=True)
+    np.testing.assert_array_equal(new, rev)
+    np.testing.assert_array_equal(trials, trials_r)
+    t, z, y, x = np.meshgrid(range(Nt), range(Ns), range(Ns), range(Ns), indexing="ij")
+    par = ((x + y + z + t) % 2).reshape(-1)
+    changed = np.any(new != links, axis=2)
+    in_phase = np.zeros_like(changed)
+    in_phase[par == parity, mu] = True
+    np.testing.assert_array_equal(changed, in_phase)
+    assert np.all(trials[in_phase] >= 1) and np.all(trials[~in_phase] == -2)
+    assert cnt[1] == in_phase.sum() and cnt[0] == trials[in_phase].sum() and cnt[2] == 0
+    np.testing.assert_allclose(np.linalg.norm(new, axis=2), 1.0, atol=2e-16 * 8)
+
+
+def test_sweeps_compose_and_are_deterministic():
+    Ns, Nt = 4, 4
+    start = O.init(Ns, Nt, True, 3)
+    two, p2, c2 = O.heatbath(Ns, Nt, start, 2.3, 2, seed=17, sweep0=0)
+    one, p1a, _ = O.heatbath(Ns, Nt, start, 2.3, 1, seed=17, sweep0=0)
+    one, p1b, _ = O.heatbath(Ns, Nt, one, 2.3, 1, seed=17, sweep0=1)
+    np.testing.assert_array_equal(one, two)
+    np.testing.assert_array_equal(np.concatenate([p1a, p1b]), p2)
+    again, _, _ = O.heatbath(Ns, Nt, start, 2.3, 2, seed=17, sweep0=0)
+    np.testing.assert_array_equal(again, two)
+    other, _, _ = O.heatbath(Ns, Nt, start, 2.3, 2, seed=18, sweep0=0)
+    assert np.max(np.abs(other - two)) > 0.1
+    assert abs(p2[-1] - O.plaquette(Ns, Nt, two)) == 0.0
+
+
+def test_cap_hit_keeps_links():
+    Ns, Nt = 2, 2
+    links = inputs.random_links(Ns, Nt, 4)
+    new, trials, cnt = O.heatbath_phase(Ns, Nt, links, 1e-9, 1, 0, seed=3, sweep=0)
+    np.testing.assert_array_equal(new, links)
+    assert cnt[2] == cnt[1] == Ns ** 3 * Nt // 2 and cnt[0] == O.KP_CAP * cnt[1]
+
+
+def test_zero_staple_takes_haar_branch():
+    """Ns = Nt = 2 with U_nu = 1 for nu != 0: the staple of U_0(0) is
+    2 * sum_nu U_0(e_nu)^+, which vanishes for three quaternions at 120 deg."""
+    Ns, Nt = 2, 2
+    links = O.init(Ns, Nt, False, 0)
+    s = np.sqrt(3.0) / 2
+    for d, q in zip((1, 2, 4), ([1, 0, 0, 0], [-0.5, s, 0, 0], [-0.5, -s, 0, 0])):
+        links[d, 0] = q  # lex 1 = (1,0,0,0), 2 = (0,1,0,0), 4 = (0,0,1,0)
+    assert np.all(O.staple(Ns, Nt, links, 0, 0) == 0.0)
+    new, trials, cnt = O.heatbath_phase(Ns, Nt, links, 2.3, 0, 0, seed=1, sweep=0)
+    assert trials[0, 0] == 0
+    assert abs(np.linalg.norm(new[0, 0]) - 1) < 1e-15
+
+
+@pytest.mark.slow
+def test_strong_coupling_limit():
+    """beta = 0.5: <P> = I2(beta)/I1(beta) up to O(u^5) ~ 1e-4."""
+    Ns = Nt = 6
+    links = O.init(Ns, Nt, True, 7)
+    links, _, _ = O.heatbath(Ns, Nt, links, 0.5, 20, 11)
+    links, p, c = O.heatbath(Ns, Nt, links, 0.5, 600, 11, sweep0=20)
+    b = p.reshape(-1, 20).mean(1)
+    err = b.std(ddof=1) / np.sqrt(len(b))
+    u = special.ive(2, 0.5) / special.ive(1, 0.5)
+    assert abs(p.mean() - u) < 3 * err + 2e-4, (p.mean(), u, err)
+    assert c[2] == 0
+
+
+@pytest.mark.slow
+def test_weak_coupling_limit():
+    """beta (1 - <P>) -> 3/4 as beta -> infinity (equipartition over the nine
+    physical modes per site); a linear fit in 1/beta over beta = 10, 20, 40
+    extrapolates to 3/4 within 0.02."""
+    xs, ys, ws = [], [], []
+    for beta in (10.0, 20.0, 40.0):
+        links = O.init(4, 4, False, 0)
+        links, p, _ = O.heatbath(4, 4, links, beta, 300, int(beta))
+        p = p[50:]
+        b = p.reshape(-1, 25).mean(1)
+        xs.append(1 / beta)
+        ys.append(beta * (1 - p.mean()))
+        ws.append(1 / (beta * b.std(ddof=1) / np.sqrt(len(b))) ** 2)
+    A = np.vstack([np.ones(3), xs]).T
+    W = np.diag(ws)
+    coef = np.linalg.solve(A.T @ W @ A, A.T @ W @ np.array(ys))
+    assert abs(coef[0] - 0.75) < 0.02, coef

@@ -1,0 +1,412 @@
+"""Benchmark of the SU(2) heat-bath hot path on GB300.
+
+One step = the paper's benchmark (Sec. 2.1): random (Haar) SU(2) start,
+100 checkerboard heat-bath sweeps, mean plaquette after every sweep.
+
+Default workload: 64^4 lattice, beta = 2.5, FP32 links and update with FP64
+reductions (1 GiB of links, larger than the 129 MB L2, so no flush is
+needed between steps).  Companion arms on the same GPU: FP64 throughout on
+the same lattice ("FP64 plain") and a 64-lattice FP32 ensemble of uneven
+shapes advanced by the same calls ("FP32 batched").
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import platform
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SU(2) heat-bath link updates/s and % roofline, FP32-batched vs FP64 plain, 1 GB300"
+UNIT = "link updates/s"
+BYTES_PER_UPDATE = {"f32": 8 * 16, "f64": 8 * 32}  # 7 link reads + 1 write per update
+WORKLOAD = dict(Ns=64, Nt=64, beta=2.5, sweeps=100, init_seed=3, hb_seed=3)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-arms", action="store_true", help="skip the FP64 and batched arms")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_name(prec):
+    w = WORKLOAD
+    return (f"SU(2) {w['Ns']}^3x{w['Nt']} lattice, beta={w['beta']}, hot (Haar) start seed "
+            f"{w['init_seed']}, {w['sweeps']} checkerboard heat-bath sweeps + mean plaquette "
+            f"per sweep, {prec}")
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax.append(float(row[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "heatbath_phase_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_1104_5432_gb300", "csrc", "heatbath.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = rec.get(kernel_key)
+    if not ent or ent.get("source_sha256_16") != h:
+        return None
+    return ent.get("dram_bytes_per_launch_full_size")
+
+
+def gpu_arm(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1104_5432_gb300 import inputs, su2
+
+    torch.cuda.set_device(local)
+    w = WORKLOAD
+    Ns, Nt, sweeps = w["Ns"], w["Nt"], w["sweeps"]
+    V = Ns ** 3 * Nt
+    seed_init = w["init_seed"] + 1000003 * rank   # independent lattice per rank
+    seed_hb = w["hb_seed"] + 1000003 * rank
+    stream = torch.cuda.current_stream()
+    ups_step = 4 * V * sweeps
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def time_steps(step, K, W):
+        for _ in range(W):
+            step()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1) / 1e3)
+
+    # ---- main arm: FP32, inputs resident in HBM --------------------------------
+    lat = su2.Lattice(Ns, Nt, su2.F32)
+    plaq_dev = torch.zeros(sweeps, dtype=torch.float64, device="cuda")
+
+    def step_f32():
+        lat.init(su2.HOT, seed_init)
+        lat.heatbath(w["beta"], sweeps, seed_hb, plaq=plaq_dev)
+
+    clk = ClockSampler(local)
+    for _ in range(args.warmup):
+        step_f32()
+    torch.cuda.synchronize()
+    clk.start()
+    t_main = time_steps(step_f32, args.steps, 0)
+    clocks = clk.stop()
+    lat.sync()
+    value = world * ups_step * args.steps / t_main
+    launches_per_step = 1 + 1 + 9 * sweeps  # init, parameter kernel, 8 phases + sweep end
+
+    # ---- dominant kernel, timed per launch with events on its stream ----------
+    n_ph = 16
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(n_ph)]
+    for i in range(n_ph):
+        mu, p = (i // 2) % 4, i % 2
+        ev[i][0].record(stream)
+        lat.heatbath_phase(w["beta"], mu, p, seed_hb)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    lat.sync()
+    phase_s = float(np.mean([a.elapsed_time(b) for a, b in ev])) / 1e3
+    hbm, peak_kind = peaks()
+    bytes_launch = BYTES_PER_UPDATE["f32"] * (V // 2)
+    achieved = bytes_launch / phase_s / 1e9
+    traffic = recorded_traffic("f32_64^4")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": traffic,
+                "kernel": "hb_phase_kernel<float> (one checkerboard phase, V/2 link updates)",
+                "bytes_per_launch": bytes_launch, "launch_ms": round(phase_s * 1e3, 4),
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
+                "measured" else "fallback 6.8 TB/s"}
+    # whole-step effective bandwidth (all kernels, all gaps)
+    step_gbs = value / world * BYTES_PER_UPDATE["f32"] / 1e9
+
+    # ---- e2e: the same step through host buffers -------------------------------
+    host_links = torch.empty((V, 4, 4), dtype=torch.float64, pin_memory=True).numpy()
+    lat.init(su2.HOT, seed_init)
+    lat.get_links(out=host_links)
+    plaq_host = np.zeros((1, sweeps), np.float64)
+
+    def step_e2e():
+        lat.set_links(host_links)
+        lat.set_sweep(0)
+        lat.heatbath(w["beta"], sweeps, seed_hb, plaq=plaq_host)
+
+    for _ in range(1):
+        step_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    k_e2e = max(1, min(args.steps, 3))
+    for _ in range(k_e2e):
+        step_e2e()
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * ups_step * k_e2e / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(host_links.nbytes), "d2h_bytes_per_step": int(plaq_host.nbytes),
+           "steps": k_e2e,
+           "path": "su2_set_links(pinned host, canonical FP64) + su2_heatbath(100 sweeps, "
+                   "plaquette to host)"}
+    del host_links
+    lat.close()
+    torch.cuda.empty_cache()
+
+    arms = {}
+    if not args.no_arms:
+        # ---- FP64 plain: same lattice, FP64 throughout ---------------------------
+        lat64 = su2.Lattice(Ns, Nt, su2.F64)
+        sw64 = 10
+        pl64 = torch.zeros(sw64, dtype=torch.float64, device="cuda")
+
+        def step_f64():
+            lat64.init(su2.HOT, seed_init)
+            lat64.heatbath(w["beta"], sw64, seed_hb, plaq=pl64)
+
+        t64 = time_steps(step_f64, 2, 1)
+        lat64.sync()
+        arms["fp64_plain"] = {"value": world * 4 * V * sw64 * 2 / t64, "unit": UNIT,
+                              "workload": workload_name("FP64 throughout").replace(
+                                  f"{sweeps} checkerboard", f"{sw64} checkerboard"),
+                              "ms_per_sweep": t64 / (2 * sw64) * 1e3}
+        lat64.close()
+        torch.cuda.empty_cache()
+
+        # ---- FP32 batched ensemble -------------------------------------------------
+        ens = inputs.batched_ensemble(64, 5)
+        B = su2.Lattice([e["Ns"] for e in ens], [e["Nt"] for e in ens], su2.F32)
+        betas = [e["beta"] for e in ens]
+        seeds = [e["seed"] + 1000003 * rank for e in ens]
+        swb = 200
+        plb = torch.zeros(len(ens) * swb, dtype=torch.float64, device="cuda")
+        Vtot = sum(e["Ns"] ** 3 * e["Nt"] for e in ens)
+
+        def step_b():
+            B.batch_init(su2.HOT, seeds)
+            B.batch_heatbath(betas, swb, seeds, plaq=plb)
+
+        tb = time_steps(step_b, 2, 1)
+        B.sync()
+        arms["fp32_batched"] = {
+            "value": world * 4 * Vtot * swb * 2 / tb, "unit": UNIT,
+            "workload": "64 independent lattices, Ns in {16..48}, Nt in {4,6,8}, beta in "
+                        "[2.2,2.6] (numpy default_rng(5)), hot start, 200 sweeps + plaquette "
+                        "per sweep, FP32 links + FP64 reductions, one call per step",
+            "sites": Vtot, "ms_per_sweep": tb / (2 * swb) * 1e3}
+        B.close()
+        torch.cuda.empty_cache()
+        if "fp64_plain" in arms:
+            arms["fp32_over_fp64_plain"] = value / arms["fp64_plain"]["value"]
+
+    return dict(t_main=t_main, value=value, clocks=clocks, roofline=roofline, e2e=e2e,
+                arms=arms, launches=launches_per_step * args.steps, step_gbs=step_gbs,
+                phase_s=phase_s)
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle legs
+# ----------------------------------------------------------------------------
+def oracle_sample(n_phases, links=None):
+    """Time the FP64 oracle on n_phases checkerboard phases of the 64^4
+    workload, single-threaded; returns (updates/s, updates, seconds)."""
+    import ctypes as C
+
+    from oracle import oracle as O
+
+    w = WORKLOAD
+    Ns, Nt = w["Ns"], w["Nt"]
+    if links is None:
+        links = O.init(Ns, Nt, True, w["init_seed"])
+    cnt = np.zeros(3, np.uint64)
+    lib = O.lib()
+    t0 = time.perf_counter()
+    for i in range(n_phases):
+        mu, p = (i // 2) % 4, i % 2
+        lib.or_heatbath_phase(Ns, Nt, links.ctypes.data_as(C.c_void_p), w["beta"], mu, p,
+                              w["hb_seed"], 0, 0, None, cnt.ctypes.data_as(C.c_void_p))
+    dt = time.perf_counter() - t0
+    return float(cnt[1]) / dt, int(cnt[1]), dt, links
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    O.build()
+    links = O.init(WORKLOAD["Ns"], WORKLOAD["Nt"], True, WORKLOAD["init_seed"])
+    for _ in range(args.warmup):
+        oracle_sample(1, links)
+    tot_u, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        _, u, dt, _ = oracle_sample(1, links)
+        tot_u += u
+        tot_t += dt
+    v = tot_u / tot_t
+    sample = ("one checkerboard phase (V/2 = 8,388,608 link updates) of the 64^4 beta=2.5 "
+              "hot-start workload per step, FP64 CPU oracle, one thread")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name("FP64 CPU oracle"), "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model()},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    r = gpu_arm(args, rank, world, local)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from paper_1104_5432_gb300 import su2
+        v, u, dt, _ = oracle_sample(2)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"phases (0,0) and (0,1) of the 64^4 beta=2.5 hot-start workload "
+                         f"({u} link updates, {dt:.1f} s), FP64 CPU oracle, one thread",
+               "cpu": cpu_model()}
+    if rank == 0:
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": r["t_main"] / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_name("FP32 links and update, FP64 reductions"),
+                           "link_bytes": 4 * WORKLOAD["Ns"] ** 3 * WORKLOAD["Nt"] * 16,
+                           "l2": "inputs larger than L2 (1 GiB of links vs 129 MB L2), no flush",
+                           "parallelism": f"{world} independent lattice(s), one per GPU"},
+                "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
+                "gpu_launches": r["launches"], "clocks": r["clocks"],
+                "step_effective_gbs": round(r["step_gbs"], 1), "arms": r["arms"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

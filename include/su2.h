@@ -1,0 +1,202 @@
+/*
+ * su2.h -- C ABI of the GB300 (sm_103a) SU(2) pure-gauge heat-bath library.
+ *
+ * The library implements the lattice part of Cardoso, Cardoso & Bicudo,
+ * "Finite temperature lattice QCD with GPUs" (Excited QCD 2011):
+ *   - random SU(2) start and heat-bath iterations with the mean plaquette
+ *     after every iteration (Sec. 2.1, the benchmark workload);
+ *   - the Polyakov loop, the order parameter of Sec. 2.2 (Eq. 1);
+ *   - the Polyakov-loop correlator behind the colour-averaged free energy
+ *     (Sec. 2.2, Eq. 3).
+ * The paper leaves the algorithmic details to its companion paper; this
+ * library fixes them as follows:
+ *   - Wilson action S = beta sum_P (1 - 1/2 Re Tr U_P), beta = 4/g^2;
+ *   - a link is a unit quaternion (a0,a1,a2,a3) for U = a0 + i a.sigma;
+ *   - lattice extents (Ns,Ns,Ns,Nt) for (x,y,z,t), both even and >= 2,
+ *     lex = x + Ns(y + Ns(z + Ns t)), parity = (x+y+z+t) mod 2;
+ *   - a sweep is the eight checkerboard phases (mu, parity) in the order
+ *     (0,0),(0,1),(1,0),(1,1),(2,0),(2,1),(3,0),(3,1); each link is drawn
+ *     with the Kennedy-Pendleton method from its staple sum A = k Vhat,
+ *     U = X Vhat^dagger, then renormalised;
+ *   - all random numbers come from Philox4x32-10, key = seed, counter =
+ *     (lex*4+mu, sweep, tag<<24 | trial, sweep>>32), so results are
+ *     independent of launch shape, batching and graph replay, and
+ *     heatbath(n) followed by heatbath(m) equals heatbath(n+m).
+ *
+ * Handles and memory.  A handle holds n >= 1 independent lattices (n = 1
+ * for su2_lattice_create).  The library allocates NO device memory: the
+ * caller queries su2_memory_requirements, allocates two device buffers
+ * (any allocator; 256-byte aligned) and binds them with su2_bind_memory.
+ * The buffers stay owned by the caller and must outlive the handle's use.
+ * Host buffers passed to any call are owned by the caller.
+ *
+ * Pointers marked "host or device" may point to host memory (pageable or
+ * pinned) or to device memory of the bound device; the library detects
+ * which.  With a device pointer the call is asynchronous on the handle's
+ * stream; with a host pointer it returns after the data has arrived.
+ *
+ * Errors.  Every int-returning call returns SU2_OK (0) or a negative
+ * status; su2_last_error() gives a message for the calling thread.  An
+ * invalid argument (SU2_E_INVAL) leaves the handle unchanged.  A
+ * Kennedy-Pendleton cap hit (4096 rejected trials for one link; happens
+ * only for beta*k below ~1e-2) keeps that link unchanged, completes the
+ * sweep and is reported as SU2_E_TRIALS by the next synchronising call
+ * (su2_sync or any call that writes host memory).
+ */
+#ifndef SU2_GB300_H
+#define SU2_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SU2_OK 0
+#define SU2_E_INVAL (-1)    /* bad argument, shape or handle state */
+#define SU2_E_NOMEM (-2)    /* bound buffers smaller than required */
+#define SU2_E_CUDA (-3)     /* a CUDA runtime call failed */
+#define SU2_E_TRIALS (-4)   /* Kennedy-Pendleton cap hit since the last sync */
+
+#define SU2_F32 0           /* FP32 links and update, FP64 reductions */
+#define SU2_F64 1           /* FP64 throughout */
+
+#define SU2_COLD 0          /* every link the identity */
+#define SU2_HOT 1           /* Haar-random links (Sec. 2.1 "random SU(2)") */
+
+typedef struct su2_lattice su2_lattice;
+
+/* ------------------------------------------------------------------ */
+/* handles                                                             */
+/* ------------------------------------------------------------------ */
+
+/* One lattice of extents Ns^3 x Nt (even, >= 2, Ns^3 Nt <= 2^30), link
+ * precision dtype (SU2_F32 / SU2_F64).  *out receives the handle. */
+int su2_lattice_create(int Ns, int Nt, int dtype, su2_lattice** out);
+
+/* n independent lattices Ns[l]^3 x Nt[l] of one precision, advanced
+ * together by every call (the finite-temperature scans and ensembles of
+ * Sec. 2.2).  Ns, Nt: host arrays of length n, 1 <= n <= 4096. */
+int su2_batch_create(int n, const int* Ns, const int* Nt, int dtype, su2_lattice** out);
+
+/* Releases the handle (never the caller's buffers).  NULL is a no-op. */
+int su2_lattice_destroy(su2_lattice* lat);
+
+/* Number of lattices and volume V = Ns^3 Nt of lattice l. */
+int su2_lattice_count(const su2_lattice* lat, int* n);
+int su2_lattice_volume(const su2_lattice* lat, int l, uint64_t* V);
+
+/* Bytes of the two device buffers a handle needs.  The link buffer holds
+ * 4V links per lattice (16 B each in FP32, 32 B in FP64); the work buffer
+ * holds descriptors, reduction partials, the Polyakov field, the
+ * plaquette ring and a 32 MiB staging area for host transfers. */
+int su2_memory_requirements(const su2_lattice* lat, size_t* link_bytes, size_t* work_bytes);
+
+/* Binds caller-owned device buffers of the CURRENT device (256-byte
+ * aligned, at least the required sizes; SU2_E_NOMEM otherwise) and writes
+ * the lattice descriptors into the work buffer (synchronous).  Links are
+ * undefined until su2_init or su2_set_links.  May be called again to move
+ * the handle to other buffers (contents are not copied). */
+int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work,
+                    size_t work_bytes);
+
+/* cudaStream_t (as void*) every later call is ordered on; 0 = legacy
+ * default stream (the initial setting). */
+int su2_set_stream(su2_lattice* lat, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* the method: start, heat-bath sweeps, measurements                   */
+/* ------------------------------------------------------------------ */
+
+/* Start configuration (Sec. 2.1 "random SU(2) matrix initialization"):
+ * start = SU2_COLD or SU2_HOT (Haar links, Philox tag 2 with key
+ * seed + l for lattice l).  Resets each lattice's sweep counter and its
+ * statistics to 0.  Asynchronous. */
+int su2_init(su2_lattice* lat, int start, uint64_t seed);
+
+/* As su2_init with one seed per lattice (host array of length n). */
+int su2_batch_init(su2_lattice* lat, int start, const uint64_t* seeds);
+
+/* nsweeps >= 0 heat-bath sweeps at coupling beta >= 0 ("100 iterations of
+ * the heat bath method", Sec. 2.1).  Lattice l draws with Philox key
+ * seed + l and counter field sweep = its cumulative sweep counter, which
+ * advances by nsweeps.
+ * plaq (nullable; host or device; double[n][nsweeps]): the mean plaquette
+ * (1/6V) sum_x sum_{mu<nu} 1/2 Re Tr U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+ * after every sweep ("the calculation of the mean average plaquette at
+ * each iteration", Sec. 2.1), fused into the sweep at no extra memory
+ * traffic.  With plaq = NULL the fused measurement is skipped.
+ * beta = 0 gives Haar links (the alpha -> 0 limit of the draw). */
+int su2_heatbath(su2_lattice* lat, double beta, int nsweeps, uint64_t seed, double* plaq);
+
+/* As su2_heatbath with one beta and one seed per lattice (host arrays of
+ * length n): the temperature scan of Sec. 2.2 in one call. */
+int su2_batch_heatbath(su2_lattice* lat, const double* betas, int nsweeps,
+                       const uint64_t* seeds, double* plaq);
+
+/* One checkerboard phase (mu in 0..3, parity 0/1) of every lattice at the
+ * current sweep counter, which does NOT advance (the unit the sweep is
+ * made of; for testing).  trials (nullable, device int32[V], n == 1
+ * only) receives, at lex of every updated link, the Kennedy-Pendleton
+ * trials used, 0 for a Haar draw, -1 for a cap hit. */
+int su2_heatbath_phase(su2_lattice* lat, double beta, int mu, int parity, uint64_t seed,
+                       int32_t* trials);
+
+/* Mean plaquette of every lattice, out: host or device double[n]. */
+int su2_plaquette(su2_lattice* lat, double* out);
+
+/* Polyakov loop (Sec. 2.2, Eq. 1): L(x) = 1/2 Re Tr prod_{t=0}^{Nt-1}
+ * U_3(x,t) and its spatial mean.  out_signed: host or device double[n],
+ * the mean; out_abs (nullable): |mean|.  Also stores the field L(x) on
+ * the device for su2_polyakov_correlator. */
+int su2_polyakov_loop(su2_lattice* lat, double* out_signed, double* out_abs);
+
+/* Polyakov-loop correlator (Sec. 2.2, Eq. 3; for SU(2) the traces are
+ * real): C(r) = (1/(3 Ns^3)) sum_x sum_{i=x,y,z} L(x) L(x + r e_i),
+ * r = 0..rmax, periodic, rmax <= Ns/2 of every lattice.  Measures L first.
+ * out: host or device double[n][rmax+1]; accumulate != 0 adds to out
+ * (running sums over measured sweeps) instead of overwriting it. */
+int su2_polyakov_correlator(su2_lattice* lat, int rmax, double* out, int accumulate);
+
+/* ------------------------------------------------------------------ */
+/* state, statistics, checkpoints                                      */
+/* ------------------------------------------------------------------ */
+
+/* Links of lattice l in the canonical layout double[V][4][4] =
+ * [lex][mu][a0,a1,a2,a3] (host or device).  set rounds to FP32 for an
+ * SU2_F32 handle.  Synchronous for host pointers. */
+int su2_get_links(su2_lattice* lat, int l, double* dst);
+int su2_set_links(su2_lattice* lat, int l, const double* src);
+
+/* U_mu(x) -> g(x) U_mu(x) g(x+mu)^+ with Haar g(x) (Philox tag 3, key
+ * seed): leaves the plaquette, the Polyakov loop and the correlator
+ * unchanged ("which is gauge invariant", Sec. 2.2). */
+int su2_gauge_transform(su2_lattice* lat, int l, uint64_t seed);
+
+/* Counters of lattice l since its last init: out[0] Kennedy-Pendleton
+ * trials, out[1] link updates, out[2] cap hits.  Synchronous. */
+int su2_stats(su2_lattice* lat, int l, uint64_t out[3]);
+
+/* Cumulative sweep counter of lattice l (the RNG counter field);
+ * checkpoint = get_links + get_sweep, resume = set_links + set_sweep. */
+int su2_get_sweep(su2_lattice* lat, int l, uint64_t* sweep);
+int su2_set_sweep(su2_lattice* lat, int l, uint64_t sweep);
+
+/* Waits for the handle's stream; returns SU2_E_TRIALS (once) if a cap hit
+ * occurred since the previous synchronising call. */
+int su2_sync(su2_lattice* lat);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* su2_last_error(void);
+
+/* Self-test of the host-side exact division used for site indexing:
+ * returns the number of n in [0, limit) and divisors 1..dmax for which
+ * it differs from n / d. */
+uint64_t su2_selftest_fastdiv(uint32_t dmax, uint32_t limit);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SU2_GB300_H */

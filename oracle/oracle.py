@@ -59,6 +59,8 @@ def lib():
             L.or_heatbath_phase.restype = i
             L.or_update_from_staple.argtypes = [P, d, u64, u32, u64, P]
             L.or_update_from_staple.restype = i
+            L.or_heatbath_link.argtypes = [i, i, P, d, i, C.c_long, u64, u64, P]
+            L.or_heatbath_link.restype = i
             L.or_kp_samples.argtypes = [d, u64, u64, C.c_long, P, P]
             L.or_kp_samples.restype = None
             L.or_plaquette.argtypes = [i, i, P]
@@ -143,6 +145,14 @@ def update_from_staple(A, beta, seed, c0, sweep):
     a = np.ascontiguousarray(np.asarray(A, np.float64))
     out = np.zeros(4, np.float64)
     t = lib().or_update_from_staple(_ptr(a), float(beta), seed, c0, sweep, _ptr(out))
+    return out, t
+
+
+def heatbath_link(Ns, Nt, links, beta, mu, lex, seed, sweep):
+    """(new link, trials) that a phase would draw for U_mu(lex) from `links`."""
+    out = np.zeros(4, np.float64)
+    t = lib().or_heatbath_link(Ns, Nt, _ptr(links), float(beta), mu, int(lex), seed, sweep,
+                               _ptr(out))
     return out, t
 
 

@@ -424,6 +424,19 @@ int or_heatbath_phase(int Ns, int Nt, double *links, double beta, int mu, int pa
     return 0;
 }
 
+/* The link the phase (mu, parity(x)) would draw for U_mu(x) alone, from
+ * the configuration as given (for sampled checks on large lattices).
+ * Returns trials as or_update_from_staple; unew is untouched on a cap hit. */
+int or_heatbath_link(int Ns, int Nt, const double *links, double beta, int mu, long lex,
+                     uint64_t seed, uint64_t sweep, double unew[4])
+{
+    geom g = mkgeom(Ns, Nt);
+    int c[4];
+    coords_of(&g, lex, c);
+    mat2 A = staple(&g, links, c, mu);
+    return update_from_staple(&A, beta, seed, (uint32_t)(lex * 4 + mu), sweep, unew);
+}
+
 /* Test hook for the sampler: the link drawn by the heat-bath step for a
  * given staple quaternion A (any real multiple of an SU(2) element). */
 int or_update_from_staple(const double A[4], double beta, uint64_t seed, uint32_t c0,

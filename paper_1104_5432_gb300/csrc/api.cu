@@ -1,0 +1,653 @@
+// api.cu -- the C ABI (include/su2.h): handles, binding of caller-owned
+// device memory, sweep orchestration through a replayed CUDA graph, host /
+// device output handling, checkpoints and statistics.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "su2.h"
+#include "su2_internal.h"
+
+using namespace su2;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(SU2_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SU2_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+uint32_t blocks_of(uint64_t n) { return (uint32_t)((n + TPB - 1) / TPB); }
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (dev < 0) return;
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+__global__ void put_u64_kernel(uint64_t* dst, uint64_t v) { *dst = v; }
+
+}  // namespace
+
+struct su2_lattice {
+    int n = 0;
+    int dtype = 0;
+    std::vector<int> Ns, Nt;
+    std::vector<uint64_t> V, Vs, link_off, field_off;
+    std::vector<uint32_t> phase_start, site_start, spat_start;
+    uint32_t phase_blocks = 0, site_blocks = 0, spat_blocks = 0;
+    int rmax_limit = 0;             // rmax <= min_l Ns_l / 2
+    size_t link_bytes = 0, work_bytes = 0;
+    size_t off_status = 0, off_desc = 0, off_pstart = 0, off_sstart = 0, off_spstart = 0;
+    size_t off_plaq = 0, off_obs = 0, off_field = 0, off_ring = 0, off_res = 0, off_stage = 0;
+    size_t res_doubles = 0;
+    // bound state
+    void* links = nullptr;
+    char* work = nullptr;
+    int device = -1;
+    cudaStream_t stream = 0;
+    cudaStream_t capture = nullptr;
+    cudaGraphExec_t sweep_graph[2] = {nullptr, nullptr};
+    Ctx ctx{};
+
+    bool bound() const { return links != nullptr && work != nullptr; }
+    LatDesc* desc_dev(int l) const
+    {
+        return reinterpret_cast<LatDesc*>(work + off_desc) + l;
+    }
+    uint32_t* status_dev() const { return reinterpret_cast<uint32_t*>(work + off_status); }
+    double* res_dev() const { return reinterpret_cast<double*>(work + off_res); }
+    double* ring_dev() const { return reinterpret_cast<double*>(work + off_ring); }
+    double* stage_dev() const { return reinterpret_cast<double*>(work + off_stage); }
+
+    void drop_graphs()
+    {
+        for (auto& g : sweep_graph)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
+};
+
+namespace {
+
+int check_handle(const su2_lattice* lat, bool need_bound = true)
+{
+    if (!lat) return fail(SU2_E_INVAL, "null handle");
+    if (need_bound && !lat->bound()) return fail(SU2_E_INVAL, "no device memory bound");
+    return SU2_OK;
+}
+
+// true when p is device (or managed) memory of some device
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int layout(su2_lattice* L)
+{
+    const int n = L->n;
+    L->V.resize(n);
+    L->Vs.resize(n);
+    L->link_off.resize(n);
+    L->field_off.resize(n);
+    L->phase_start.assign(n + 1, 0);
+    L->site_start.assign(n + 1, 0);
+    L->spat_start.assign(n + 1, 0);
+    size_t lb = 0;
+    uint64_t fo = 0;
+    int rlim = 1 << 30;
+    const size_t link_size = L->dtype == SU2_F32 ? 16 : 32;
+    for (int l = 0; l < n; ++l) {
+        const uint64_t Ns = (uint64_t)L->Ns[l], Nt = (uint64_t)L->Nt[l];
+        L->Vs[l] = Ns * Ns * Ns;
+        L->V[l] = L->Vs[l] * Nt;
+        L->link_off[l] = lb;
+        lb += align256(4 * L->V[l] * link_size);
+        L->field_off[l] = fo;
+        fo += (L->Vs[l] + 31) & ~uint64_t(31);
+        L->phase_start[l + 1] = L->phase_start[l] + blocks_of(L->V[l] / 2);
+        L->site_start[l + 1] = L->site_start[l] + blocks_of(L->V[l]);
+        L->spat_start[l + 1] = L->spat_start[l] + blocks_of(L->Vs[l]);
+        rlim = std::min(rlim, L->Ns[l] / 2);
+    }
+    L->phase_blocks = L->phase_start[n];
+    L->site_blocks = L->site_start[n];
+    L->spat_blocks = L->spat_start[n];
+    L->rmax_limit = rlim;
+    L->link_bytes = lb;
+
+    size_t w = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = w;
+        w += align256(bytes);
+        return o;
+    };
+    L->off_status = take(256);
+    L->off_desc = take(sizeof(LatDesc) * n);
+    L->off_pstart = take(4 * (n + 1));
+    L->off_sstart = take(4 * (n + 1));
+    L->off_spstart = take(4 * (n + 1));
+    L->off_plaq = take(8 * 3 * (size_t)L->phase_blocks);
+    const size_t obs_rows = std::max<size_t>(L->site_blocks,
+                                             (size_t)L->spat_blocks * (size_t)(rlim + 1));
+    L->off_obs = take(8 * obs_rows);
+    L->off_field = take(8 * fo);
+    L->off_ring = take(8 * (size_t)PLAQ_RING * n);
+    L->res_doubles = (size_t)n * (rlim + 1) + 2 * (size_t)n;
+    L->off_res = take(8 * L->res_doubles);
+    L->off_stage = take(STAGE_BYTES);
+    L->work_bytes = w;
+    return SU2_OK;
+}
+
+int create(int n, const int* Ns, const int* Nt, int dtype, su2_lattice** out)
+{
+    if (!out) return fail(SU2_E_INVAL, "out is null");
+    *out = nullptr;
+    if (n < 1 || n > 4096) return fail(SU2_E_INVAL, "n must be in 1..4096 (got %d)", n);
+    if (!Ns || !Nt) return fail(SU2_E_INVAL, "null shape array");
+    if (dtype != SU2_F32 && dtype != SU2_F64) return fail(SU2_E_INVAL, "bad dtype %d", dtype);
+    for (int l = 0; l < n; ++l) {
+        if (Ns[l] < 2 || Nt[l] < 2 || (Ns[l] & 1) || (Nt[l] & 1))
+            return fail(SU2_E_INVAL, "lattice %d: Ns=%d Nt=%d must be even and >= 2", l, Ns[l],
+                        Nt[l]);
+        const uint64_t V = (uint64_t)Ns[l] * Ns[l] * Ns[l] * Nt[l];
+        if (V > (uint64_t(1) << 30))
+            return fail(SU2_E_INVAL, "lattice %d: volume %llu above 2^30", l,
+                        (unsigned long long)V);
+    }
+    su2_lattice* L = new su2_lattice;
+    L->n = n;
+    L->dtype = dtype;
+    L->Ns.assign(Ns, Ns + n);
+    L->Nt.assign(Nt, Nt + n);
+    layout(L);
+    *out = L;
+    return SU2_OK;
+}
+
+// per-lattice parameters for the next sweeps; plaq_out[l] may be null
+int set_params(su2_lattice* L, const double* betas, double beta, const uint64_t* seeds,
+               uint64_t seed, double* plaq_dev, int nsweeps)
+{
+    for (int first = 0; first < L->n; first += PARAM_CHUNK) {
+        ParamChunk pc{};
+        pc.first = first;
+        pc.count = std::min(PARAM_CHUNK, L->n - first);
+        for (int j = 0; j < pc.count; ++j) {
+            const int l = first + j;
+            pc.beta[j] = betas ? betas[l] : beta;
+            pc.seed[j] = seeds ? seeds[l] : seed + (uint64_t)l;
+            pc.plaq_out[j] = plaq_dev ? plaq_dev + (size_t)l * nsweeps : nullptr;
+        }
+        SU2_CUDA(launch_set_params(L->ctx, pc, L->stream));
+    }
+    return SU2_OK;
+}
+
+int record_sweep(su2_lattice* L, bool plaq, cudaStream_t s)
+{
+    for (int mu = 0; mu < 4; ++mu)
+        for (int p = 0; p < 2; ++p) SU2_CUDA(launch_phase(L->ctx, L->dtype, mu, p, plaq, nullptr, s));
+    SU2_CUDA(launch_sweep_end(L->ctx, plaq, s));
+    return SU2_OK;
+}
+
+// one sweep as a graph of 9 kernels, built once per handle and binding
+int sweep_graph(su2_lattice* L, bool plaq, cudaGraphExec_t* exec)
+{
+    cudaGraphExec_t& g = L->sweep_graph[plaq ? 1 : 0];
+    if (!g) {
+        if (!L->capture) SU2_CUDA(cudaStreamCreateWithFlags(&L->capture, cudaStreamNonBlocking));
+        SU2_CUDA(cudaStreamBeginCapture(L->capture, cudaStreamCaptureModeThreadLocal));
+        const int rc = record_sweep(L, plaq, L->capture);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(L->capture, &graph);
+        if (rc != SU2_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        const cudaError_t ei = cudaGraphInstantiate(&g, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            g = nullptr;
+            return cuda_fail(ei, "cudaGraphInstantiate");
+        }
+    }
+    *exec = g;
+    return SU2_OK;
+}
+
+// synchronise and turn a latched cap hit into SU2_E_TRIALS
+int sync_status(su2_lattice* L)
+{
+    SU2_CUDA(cudaStreamSynchronize(L->stream));
+    uint32_t st = 0;
+    SU2_CUDA(cudaMemcpy(&st, L->status_dev(), sizeof st, cudaMemcpyDeviceToHost));
+    if (st) {
+        SU2_CUDA(cudaMemset(L->status_dev(), 0, sizeof st));
+        if (st & STATUS_CAP_HIT)
+            return fail(SU2_E_TRIALS, "Kennedy-Pendleton trial cap (%d) hit; links kept", KP_CAP);
+    }
+    return SU2_OK;
+}
+
+int heatbath_impl(su2_lattice* L, const double* betas, double beta, int nsweeps,
+                  const uint64_t* seeds, uint64_t seed, double* plaq)
+{
+    if (int rc = check_handle(L)) return rc;
+    if (nsweeps < 0) return fail(SU2_E_INVAL, "nsweeps < 0");
+    for (int l = 0; l < L->n; ++l) {
+        const double b = betas ? betas[l] : beta;
+        if (!(b >= 0.0) || !std::isfinite(b)) return fail(SU2_E_INVAL, "beta must be finite and >= 0");
+    }
+    DeviceGuard dg(L->device);
+    const bool want = plaq != nullptr;
+    const bool dev_out = want && is_device_ptr(plaq);
+    cudaGraphExec_t g = nullptr;
+    if (int rc = sweep_graph(L, want, &g)) return rc;
+    int done = 0;
+    while (done < nsweeps) {
+        const int chunk = (want && !dev_out) ? std::min(PLAQ_RING, nsweeps - done) : nsweeps;
+        if (int rc = set_params(L, betas, beta, seeds, seed, dev_out ? plaq : nullptr, nsweeps))
+            return rc;
+        for (int s = 0; s < chunk; ++s) SU2_CUDA(cudaGraphLaunch(g, L->stream));
+        if (want && !dev_out) {
+            for (int l = 0; l < L->n; ++l)
+                SU2_CUDA(cudaMemcpyAsync(plaq + (size_t)l * nsweeps + done,
+                                         L->ring_dev() + (size_t)l * PLAQ_RING,
+                                         sizeof(double) * chunk, cudaMemcpyDeviceToHost, L->stream));
+        }
+        done += chunk;
+    }
+    if (want && !dev_out) return sync_status(L);
+    SU2_CUDA(cudaGetLastError());
+    return SU2_OK;
+}
+
+int init_impl(su2_lattice* L, int start, const uint64_t* seeds, uint64_t seed)
+{
+    if (int rc = check_handle(L)) return rc;
+    if (start != SU2_COLD && start != SU2_HOT) return fail(SU2_E_INVAL, "bad start %d", start);
+    DeviceGuard dg(L->device);
+    for (int l = 0; l < L->n; ++l)
+        SU2_CUDA(launch_init(L->ctx, L->dtype, l, (uint32_t)L->V[l], start,
+                             seeds ? seeds[l] : seed + (uint64_t)l, L->stream));
+    return SU2_OK;
+}
+
+// out: host or device; produce n*rows doubles through the result area
+int finish_output(su2_lattice* L, double* out, const double* dev_src, size_t count)
+{
+    SU2_CUDA(cudaMemcpyAsync(out, dev_src, sizeof(double) * count, cudaMemcpyDeviceToHost,
+                             L->stream));
+    return sync_status(L);
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// exported
+// --------------------------------------------------------------------------
+extern "C" {
+
+int su2_lattice_create(int Ns, int Nt, int dtype, su2_lattice** out)
+{
+    return create(1, &Ns, &Nt, dtype, out);
+}
+
+int su2_batch_create(int n, const int* Ns, const int* Nt, int dtype, su2_lattice** out)
+{
+    return create(n, Ns, Nt, dtype, out);
+}
+
+int su2_lattice_destroy(su2_lattice* lat)
+{
+    if (!lat) return SU2_OK;
+    {
+        DeviceGuard dg(lat->device);
+        lat->drop_graphs();
+        if (lat->capture) cudaStreamDestroy(lat->capture);
+    }
+    delete lat;
+    return SU2_OK;
+}
+
+int su2_lattice_count(const su2_lattice* lat, int* n)
+{
+    if (int rc = check_handle(lat, false)) return rc;
+    if (!n) return fail(SU2_E_INVAL, "null output");
+    *n = lat->n;
+    return SU2_OK;
+}
+
+int su2_lattice_volume(const su2_lattice* lat, int l, uint64_t* V)
+{
+    if (int rc = check_handle(lat, false)) return rc;
+    if (!V || l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index or output");
+    *V = lat->V[l];
+    return SU2_OK;
+}
+
+int su2_memory_requirements(const su2_lattice* lat, size_t* link_bytes, size_t* work_bytes)
+{
+    if (int rc = check_handle(lat, false)) return rc;
+    if (link_bytes) *link_bytes = lat->link_bytes;
+    if (work_bytes) *work_bytes = lat->work_bytes;
+    return SU2_OK;
+}
+
+int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work, size_t work_bytes)
+{
+    if (int rc = check_handle(lat, false)) return rc;
+    if (!links || !work) return fail(SU2_E_INVAL, "null buffer");
+    if (((uintptr_t)links & 255) || ((uintptr_t)work & 255))
+        return fail(SU2_E_INVAL, "buffers must be 256-byte aligned");
+    if (link_bytes < lat->link_bytes || work_bytes < lat->work_bytes)
+        return fail(SU2_E_NOMEM, "buffers too small: need %zu + %zu bytes, got %zu + %zu",
+                    lat->link_bytes, lat->work_bytes, link_bytes, work_bytes);
+    if (!is_device_ptr(links) || !is_device_ptr(work))
+        return fail(SU2_E_INVAL, "buffers must be device memory");
+    int dev = 0;
+    SU2_CUDA(cudaGetDevice(&dev));
+    lat->drop_graphs();
+    lat->links = links;
+    lat->work = static_cast<char*>(work);
+    lat->device = dev;
+
+    std::vector<LatDesc> d(lat->n);
+    for (int l = 0; l < lat->n; ++l) {
+        LatDesc& D = d[l];
+        memset(&D, 0, sizeof D);
+        D.Ns = lat->Ns[l];
+        D.Nt = lat->Nt[l];
+        D.Nh = lat->Ns[l] / 2;
+        D.Vs = (int32_t)lat->Vs[l];
+        D.V = (uint32_t)lat->V[l];
+        D.Vh = (uint32_t)(lat->V[l] / 2);
+        D.div_nh = make_fastdiv((uint32_t)D.Nh);
+        D.div_ns = make_fastdiv((uint32_t)D.Ns);
+        D.link_off = lat->link_off[l];
+        D.field_off = lat->field_off[l];
+    }
+    char* w = lat->work;
+    SU2_CUDA(cudaMemset(w + lat->off_status, 0, 256));
+    SU2_CUDA(cudaMemcpy(w + lat->off_desc, d.data(), sizeof(LatDesc) * lat->n,
+                        cudaMemcpyHostToDevice));
+    SU2_CUDA(cudaMemcpy(w + lat->off_pstart, lat->phase_start.data(), 4 * (lat->n + 1),
+                        cudaMemcpyHostToDevice));
+    SU2_CUDA(cudaMemcpy(w + lat->off_sstart, lat->site_start.data(), 4 * (lat->n + 1),
+                        cudaMemcpyHostToDevice));
+    SU2_CUDA(cudaMemcpy(w + lat->off_spstart, lat->spat_start.data(), 4 * (lat->n + 1),
+                        cudaMemcpyHostToDevice));
+    SU2_CUDA(cudaMemset(w + lat->off_ring, 0, 8 * (size_t)PLAQ_RING * lat->n));
+
+    Ctx& c = lat->ctx;
+    c.links = links;
+    c.desc = reinterpret_cast<LatDesc*>(w + lat->off_desc);
+    c.phase_start = reinterpret_cast<const uint32_t*>(w + lat->off_pstart);
+    c.site_start = reinterpret_cast<const uint32_t*>(w + lat->off_sstart);
+    c.spat_start = reinterpret_cast<const uint32_t*>(w + lat->off_spstart);
+    c.plaq_partial = reinterpret_cast<double*>(w + lat->off_plaq);
+    c.obs_partial = reinterpret_cast<double*>(w + lat->off_obs);
+    c.field = reinterpret_cast<double*>(w + lat->off_field);
+    c.ring = reinterpret_cast<double*>(w + lat->off_ring);
+    c.status = reinterpret_cast<uint32_t*>(w + lat->off_status);
+    c.n = lat->n;
+    c.phase_blocks = lat->phase_blocks;
+    c.site_blocks = lat->site_blocks;
+    c.spat_blocks = lat->spat_blocks;
+    return SU2_OK;
+}
+
+int su2_set_stream(su2_lattice* lat, void* stream)
+{
+    if (int rc = check_handle(lat, false)) return rc;
+    lat->stream = static_cast<cudaStream_t>(stream);
+    return SU2_OK;
+}
+
+int su2_init(su2_lattice* lat, int start, uint64_t seed)
+{
+    return init_impl(lat, start, nullptr, seed);
+}
+
+int su2_batch_init(su2_lattice* lat, int start, const uint64_t* seeds)
+{
+    if (!seeds) return fail(SU2_E_INVAL, "null seeds");
+    return init_impl(lat, start, seeds, 0);
+}
+
+int su2_heatbath(su2_lattice* lat, double beta, int nsweeps, uint64_t seed, double* plaq)
+{
+    return heatbath_impl(lat, nullptr, beta, nsweeps, nullptr, seed, plaq);
+}
+
+int su2_batch_heatbath(su2_lattice* lat, const double* betas, int nsweeps, const uint64_t* seeds,
+                       double* plaq)
+{
+    if (!betas || !seeds) return fail(SU2_E_INVAL, "null betas or seeds");
+    return heatbath_impl(lat, betas, 0.0, nsweeps, seeds, 0, plaq);
+}
+
+int su2_heatbath_phase(su2_lattice* lat, double beta, int mu, int parity, uint64_t seed,
+                       int32_t* trials)
+{
+    if (int rc = check_handle(lat)) return rc;
+    if (mu < 0 || mu > 3 || (parity != 0 && parity != 1))
+        return fail(SU2_E_INVAL, "bad phase (mu=%d parity=%d)", mu, parity);
+    if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(SU2_E_INVAL, "bad beta");
+    if (trials && lat->n != 1) return fail(SU2_E_INVAL, "trials output needs n == 1");
+    if (trials && !is_device_ptr(trials)) return fail(SU2_E_INVAL, "trials must be device memory");
+    DeviceGuard dg(lat->device);
+    if (int rc = set_params(lat, nullptr, beta, nullptr, seed, nullptr, 0)) return rc;
+    SU2_CUDA(launch_phase(lat->ctx, lat->dtype, mu, parity, false, trials, lat->stream));
+    return SU2_OK;
+}
+
+int su2_plaquette(su2_lattice* lat, double* out)
+{
+    if (int rc = check_handle(lat)) return rc;
+    if (!out) return fail(SU2_E_INVAL, "null output");
+    DeviceGuard dg(lat->device);
+    const bool dev = is_device_ptr(out);
+    double* tgt = dev ? out : lat->res_dev();
+    SU2_CUDA(launch_plaquette(lat->ctx, lat->dtype, tgt, lat->stream));
+    if (!dev) return finish_output(lat, out, tgt, lat->n);
+    return SU2_OK;
+}
+
+int su2_polyakov_loop(su2_lattice* lat, double* out_signed, double* out_abs)
+{
+    if (int rc = check_handle(lat)) return rc;
+    if (!out_signed) return fail(SU2_E_INVAL, "null output");
+    DeviceGuard dg(lat->device);
+    const bool dev = is_device_ptr(out_signed);
+    if (out_abs && is_device_ptr(out_abs) != dev)
+        return fail(SU2_E_INVAL, "out_signed and out_abs must both be host or both device");
+    double* ts = dev ? out_signed : lat->res_dev();
+    double* ta = out_abs ? (dev ? out_abs : lat->res_dev() + lat->n) : nullptr;
+    SU2_CUDA(launch_polyakov(lat->ctx, lat->dtype, ts, ta, lat->stream));
+    if (!dev) {
+        SU2_CUDA(cudaMemcpyAsync(out_signed, ts, sizeof(double) * lat->n, cudaMemcpyDeviceToHost,
+                                 lat->stream));
+        if (out_abs)
+            SU2_CUDA(cudaMemcpyAsync(out_abs, ta, sizeof(double) * lat->n,
+                                     cudaMemcpyDeviceToHost, lat->stream));
+        return sync_status(lat);
+    }
+    return SU2_OK;
+}
+
+int su2_polyakov_correlator(su2_lattice* lat, int rmax, double* out, int accumulate)
+{
+    if (int rc = check_handle(lat)) return rc;
+    if (!out) return fail(SU2_E_INVAL, "null output");
+    if (rmax < 0 || rmax > lat->rmax_limit)
+        return fail(SU2_E_INVAL, "rmax %d outside 0..%d", rmax, lat->rmax_limit);
+    DeviceGuard dg(lat->device);
+    const bool dev = is_device_ptr(out);
+    const size_t cnt = (size_t)lat->n * (rmax + 1);
+    double* scratch = lat->res_dev();  // [2n] Polyakov means, then correlator rows
+    double* tgt = dev ? out : scratch + 2 * lat->n;
+    SU2_CUDA(launch_polyakov(lat->ctx, lat->dtype, scratch, scratch + lat->n, lat->stream));
+    if (!dev && accumulate)
+        SU2_CUDA(cudaMemcpyAsync(tgt, out, sizeof(double) * cnt, cudaMemcpyHostToDevice,
+                                 lat->stream));
+    SU2_CUDA(launch_correlator(lat->ctx, rmax, tgt, accumulate, lat->stream));
+    if (!dev) return finish_output(lat, out, tgt, cnt);
+    return SU2_OK;
+}
+
+int su2_get_links(su2_lattice* lat, int l, double* dst)
+{
+    if (int rc = check_handle(lat)) return rc;
+    if (!dst || l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index or buffer");
+    DeviceGuard dg(lat->device);
+    const uint32_t V = (uint32_t)lat->V[l];
+    if (is_device_ptr(dst)) {
+        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, 0, V, dst, lat->stream));
+        return SU2_OK;
+    }
+    const uint32_t per = (uint32_t)(STAGE_BYTES / (16 * sizeof(double)));
+    for (uint32_t lex0 = 0; lex0 < V; lex0 += per) {
+        const uint32_t cnt = std::min(per, V - lex0);
+        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, lex0, cnt, lat->stage_dev(),
+                                           lat->stream));
+        SU2_CUDA(cudaMemcpyAsync(dst + (size_t)lex0 * 16, lat->stage_dev(),
+                                 sizeof(double) * 16 * cnt, cudaMemcpyDeviceToHost, lat->stream));
+        SU2_CUDA(cudaStreamSynchronize(lat->stream));
+    }
+    return sync_status(lat);
+}
+
+int su2_set_links(su2_lattice* lat, int l, const double* src)
+{
+    if (int rc = check_handle(lat)) return rc;
+    if (!src || l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index or buffer");
+    DeviceGuard dg(lat->device);
+    const uint32_t V = (uint32_t)lat->V[l];
+    if (is_device_ptr(src)) {
+        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, 0, V, src, lat->stream));
+        return SU2_OK;
+    }
+    const uint32_t per = (uint32_t)(STAGE_BYTES / (16 * sizeof(double)));
+    for (uint32_t lex0 = 0; lex0 < V; lex0 += per) {
+        const uint32_t cnt = std::min(per, V - lex0);
+        SU2_CUDA(cudaMemcpyAsync(lat->stage_dev(), src + (size_t)lex0 * 16,
+                                 sizeof(double) * 16 * cnt, cudaMemcpyHostToDevice, lat->stream));
+        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, lex0, cnt, lat->stage_dev(),
+                                             lat->stream));
+    }
+    SU2_CUDA(cudaStreamSynchronize(lat->stream));
+    return SU2_OK;
+}
+
+int su2_gauge_transform(su2_lattice* lat, int l, uint64_t seed)
+{
+    if (int rc = check_handle(lat)) return rc;
+    if (l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index");
+    DeviceGuard dg(lat->device);
+    SU2_CUDA(launch_gauge(lat->ctx, lat->dtype, l, (uint32_t)lat->V[l], seed, lat->stream));
+    return SU2_OK;
+}
+
+int su2_stats(su2_lattice* lat, int l, uint64_t out[3])
+{
+    if (int rc = check_handle(lat)) return rc;
+    if (!out || l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index or output");
+    DeviceGuard dg(lat->device);
+    SU2_CUDA(cudaStreamSynchronize(lat->stream));
+    LatDesc d;
+    SU2_CUDA(cudaMemcpy(&d, lat->desc_dev(l), sizeof d, cudaMemcpyDeviceToHost));
+    out[0] = d.trials;
+    out[1] = d.updates;
+    out[2] = d.caps;
+    return SU2_OK;
+}
+
+int su2_get_sweep(su2_lattice* lat, int l, uint64_t* sweep)
+{
+    if (int rc = check_handle(lat)) return rc;
+    if (!sweep || l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index or output");
+    DeviceGuard dg(lat->device);
+    SU2_CUDA(cudaStreamSynchronize(lat->stream));
+    SU2_CUDA(cudaMemcpy(sweep, &lat->desc_dev(l)->sweep, sizeof *sweep, cudaMemcpyDeviceToHost));
+    return SU2_OK;
+}
+
+int su2_set_sweep(su2_lattice* lat, int l, uint64_t sweep)
+{
+    if (int rc = check_handle(lat)) return rc;
+    if (l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index");
+    DeviceGuard dg(lat->device);
+    put_u64_kernel<<<1, 1, 0, lat->stream>>>(&lat->desc_dev(l)->sweep, sweep);
+    SU2_CUDA(cudaGetLastError());
+    return SU2_OK;
+}
+
+int su2_sync(su2_lattice* lat)
+{
+    if (int rc = check_handle(lat)) return rc;
+    DeviceGuard dg(lat->device);
+    return sync_status(lat);
+}
+
+const char* su2_last_error(void) { return g_err.c_str(); }
+
+uint64_t su2_selftest_fastdiv(uint32_t dmax, uint32_t limit)
+{
+    uint64_t bad = 0;
+    for (uint32_t d = 1; d <= dmax; ++d) {
+        const FastDiv f = make_fastdiv(d);
+        for (uint32_t n = 0; n < limit; ++n)
+            if (fdiv(n, f) != n / d) ++bad;
+        // the top of the supported range
+        for (uint32_t n = (1u << 31) - 4096; n < (1u << 31); ++n)
+            if (fdiv(n, f) != n / d) ++bad;
+    }
+    return bad;
+}
+
+}  // extern "C"

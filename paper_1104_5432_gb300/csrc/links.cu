@@ -1,0 +1,140 @@
+// links.cu -- start configurations, conversion between the device layout
+// and the canonical host layout double[V][4][4] ([lex][mu][a0..a3]), and
+// the random gauge transformation used to check gauge invariance.
+//
+// Hot start: "random SU(2) matrix initialization" (Sec. 2.1), read as
+// Haar-distributed links: four normals from one Philox block (tag 2,
+// counter (lex*4+mu, 0, 2<<24, 0)), normalised onto S^3.
+#include "su2_internal.h"
+#include "su2_links.cuh"
+
+namespace su2 {
+
+// one lattice, one thread per site; also clears the lattice's counters
+template <typename T>
+__global__ void __launch_bounds__(TPB) init_kernel(Ctx ctx, int l, int hot, uint64_t seed)
+{
+    LatDesc* Dw = ctx.desc + l;
+    const LatDesc& D = *Dw;
+    const uint32_t lex = blockIdx.x * TPB + threadIdx.x;
+    if (lex == 0) {
+        Dw->sweep = 0;
+        Dw->trials = Dw->updates = Dw->caps = 0;
+    }
+    if (lex >= D.V) return;
+    const Links<T> U(ctx.links, D);
+    int p;
+    EoSite::from_lex(D, lex, &p);
+    for (int mu = 0; mu < 4; ++mu) {
+        Quat<T> a = {T(1), T(0), T(0), T(0)};
+        if (hot) {
+            const Stream st{(uint32_t)seed, (uint32_t)(seed >> 32), lex * 4u + (uint32_t)mu, 0u, 0u};
+            a = haar_from<T>(st.draw(TAG_HOT, 0));
+        }
+        U.store(mu, p, lex >> 1, a);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB)
+to_canonical_kernel(Ctx ctx, int l, uint32_t lex0, uint32_t nsite, double* __restrict__ dst)
+{
+    const LatDesc& D = ctx.desc[l];
+    const uint32_t k = blockIdx.x * TPB + threadIdx.x;
+    if (k >= nsite) return;
+    const uint32_t lex = lex0 + k;
+    const Links<T> U(ctx.links, D);
+    int p;
+    EoSite::from_lex(D, lex, &p);
+    double* o = dst + (size_t)k * 16;
+    for (int mu = 0; mu < 4; ++mu) {
+        const Quat<T> a = U.load_rw(mu, p, lex >> 1);
+        o[mu * 4 + 0] = (double)a.a0;
+        o[mu * 4 + 1] = (double)a.a1;
+        o[mu * 4 + 2] = (double)a.a2;
+        o[mu * 4 + 3] = (double)a.a3;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB)
+from_canonical_kernel(Ctx ctx, int l, uint32_t lex0, uint32_t nsite, const double* __restrict__ src)
+{
+    const LatDesc& D = ctx.desc[l];
+    const uint32_t k = blockIdx.x * TPB + threadIdx.x;
+    if (k >= nsite) return;
+    const uint32_t lex = lex0 + k;
+    const Links<T> U(ctx.links, D);
+    int p;
+    EoSite::from_lex(D, lex, &p);
+    const double* in = src + (size_t)k * 16;
+    for (int mu = 0; mu < 4; ++mu) {
+        const Quat<T> a = {(T)in[mu * 4 + 0], (T)in[mu * 4 + 1], (T)in[mu * 4 + 2],
+                           (T)in[mu * 4 + 3]};
+        U.store(mu, p, lex >> 1, a);
+    }
+}
+
+// U_mu(x) -> g(x) U_mu(x) g(x+mu)^dagger, g Haar from Philox tag 3 with
+// counter (lex*4, 0, 3<<24, 0).  In place: each thread reads and writes
+// only the four links leaving its site; g is recomputed where needed.
+template <typename T>
+__global__ void __launch_bounds__(TPB) gauge_kernel(Ctx ctx, int l, uint64_t seed)
+{
+    const LatDesc& D = ctx.desc[l];
+    const uint32_t lex = blockIdx.x * TPB + threadIdx.x;
+    if (lex >= D.V) return;
+    const Links<T> U(ctx.links, D);
+    int p;
+    const EoSite s = EoSite::from_lex(D, lex, &p);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const Quat<T> g = haar_from<T>(Stream{k0, k1, lex * 4u, 0u, 0u}.draw(TAG_GAUGE, 0));
+    for (int mu = 0; mu < 4; ++mu) {
+        // lex of x + mu
+        int c[4] = {s.c[0], s.c[1], s.c[2], s.c[3]};
+        c[mu] = (c[mu] + 1) % (mu == 3 ? D.Nt : D.Ns);
+        const uint32_t lex_n =
+            (uint32_t)c[0] + (uint32_t)D.Ns * ((uint32_t)c[1] + (uint32_t)D.Ns *
+                                               ((uint32_t)c[2] + (uint32_t)D.Ns * (uint32_t)c[3]));
+        const Quat<T> gn = haar_from<T>(Stream{k0, k1, lex_n * 4u, 0u, 0u}.draw(TAG_GAUGE, 0));
+        const Quat<T> u = U.load_rw(mu, p, lex >> 1);
+        U.store(mu, p, lex >> 1, qmul_nd(qmul(g, u), gn));
+    }
+}
+
+static unsigned nblk(uint32_t n) { return (n + TPB - 1) / TPB; }
+
+cudaError_t launch_init(const Ctx& c, int dtype, int l, uint32_t V, int hot, uint64_t seed,
+                        cudaStream_t s)
+{
+    if (dtype == 0) init_kernel<float><<<nblk(V), TPB, 0, s>>>(c, l, hot, seed);
+    else init_kernel<double><<<nblk(V), TPB, 0, s>>>(c, l, hot, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_links_to_canonical(const Ctx& c, int dtype, int l, uint32_t lex0,
+                                      uint32_t nsite, double* dst, cudaStream_t s)
+{
+    if (dtype == 0) to_canonical_kernel<float><<<nblk(nsite), TPB, 0, s>>>(c, l, lex0, nsite, dst);
+    else to_canonical_kernel<double><<<nblk(nsite), TPB, 0, s>>>(c, l, lex0, nsite, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_links_from_canonical(const Ctx& c, int dtype, int l, uint32_t lex0,
+                                        uint32_t nsite, const double* src, cudaStream_t s)
+{
+    if (dtype == 0)
+        from_canonical_kernel<float><<<nblk(nsite), TPB, 0, s>>>(c, l, lex0, nsite, src);
+    else
+        from_canonical_kernel<double><<<nblk(nsite), TPB, 0, s>>>(c, l, lex0, nsite, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauge(const Ctx& c, int dtype, int l, uint32_t V, uint64_t seed, cudaStream_t s)
+{
+    if (dtype == 0) gauge_kernel<float><<<nblk(V), TPB, 0, s>>>(c, l, seed);
+    else gauge_kernel<double><<<nblk(V), TPB, 0, s>>>(c, l, seed);
+    return cudaGetLastError();
+}
+
+}  // namespace su2

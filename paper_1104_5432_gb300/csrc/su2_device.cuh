@@ -1,0 +1,205 @@
+// su2_device.cuh -- device building blocks of the SU(2) heat-bath library:
+// quaternion algebra, the Philox4x32-10 counter generator, exact fast
+// division by run-time constants and the even/odd site geometry.
+//
+// Conventions (the paper leaves them to its companion paper; they are fixed
+// once for the whole library):
+//   * a link is a unit quaternion (a0,a1,a2,a3) for U = a0 + i a.sigma,
+//     1/2 Tr U = a0, det U = |a|^2;
+//   * site (x,y,z,t), extents (Ns,Ns,Ns,Nt), lex = x + Ns(y + Ns(z + Ns t)),
+//     parity (x+y+z+t) & 1, index inside one parity eo = lex >> 1;
+//   * the random stream of link (lex, mu) in sweep s is Philox4x32-10 with
+//     key (seed lo, seed hi) and counter (lex*4+mu, s lo, tag<<24 | trial,
+//     s hi); tag 0 = Kennedy-Pendleton trial, 1 = direction / Haar draw,
+//     2 = hot start, 3 = random gauge transformation.  The stream therefore
+//     never depends on launch shape, batch position or graph replay.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace su2 {
+
+// --------------------------------------------------------------------------
+// quaternions
+// --------------------------------------------------------------------------
+template <typename T>
+struct Quat {
+    T a0, a1, a2, a3;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ Quat<T> qadd(const Quat<T>& p, const Quat<T>& q)
+{
+    return {p.a0 + q.a0, p.a1 + q.a1, p.a2 + q.a2, p.a3 + q.a3};
+}
+
+// p q  for U = a0 + i a.sigma:  (p0 q0 - p.q,  p0 q + q0 p - p x q)
+template <typename T>
+__host__ __device__ __forceinline__ Quat<T> qmul(const Quat<T>& p, const Quat<T>& q)
+{
+    Quat<T> r;
+    r.a0 = p.a0 * q.a0 - p.a1 * q.a1 - p.a2 * q.a2 - p.a3 * q.a3;
+    r.a1 = p.a0 * q.a1 + q.a0 * p.a1 - (p.a2 * q.a3 - p.a3 * q.a2);
+    r.a2 = p.a0 * q.a2 + q.a0 * p.a2 - (p.a3 * q.a1 - p.a1 * q.a3);
+    r.a3 = p.a0 * q.a3 + q.a0 * p.a3 - (p.a1 * q.a2 - p.a2 * q.a1);
+    return r;
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ Quat<T> qdag(const Quat<T>& p)
+{
+    return {p.a0, -p.a1, -p.a2, -p.a3};
+}
+
+// p q^dagger
+template <typename T>
+__host__ __device__ __forceinline__ Quat<T> qmul_nd(const Quat<T>& p, const Quat<T>& q)
+{
+    return qmul(p, qdag(q));
+}
+
+// p^dagger q^dagger = (q p)^dagger
+template <typename T>
+__host__ __device__ __forceinline__ Quat<T> qmul_dd(const Quat<T>& p, const Quat<T>& q)
+{
+    return qdag(qmul(q, p));
+}
+
+// 1/2 Re Tr (p q) = p0 q0 - p.q
+template <typename T>
+__host__ __device__ __forceinline__ T qretr(const Quat<T>& p, const Quat<T>& q)
+{
+    return p.a0 * q.a0 - p.a1 * q.a1 - p.a2 * q.a2 - p.a3 * q.a3;
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ T qnorm2(const Quat<T>& p)
+{
+    return p.a0 * p.a0 + p.a1 * p.a1 + p.a2 * p.a2 + p.a3 * p.a3;
+}
+
+__device__ __forceinline__ float rsqrt_t(float x) { return 1.0f / sqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ Quat<T> qnormalise(const Quat<T>& p)
+{
+    T s = rsqrt_t(qnorm2(p));
+    return {p.a0 * s, p.a1 * s, p.a2 * s, p.a3 * s};
+}
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11)
+// --------------------------------------------------------------------------
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+enum : uint32_t { TAG_TRIAL = 0u, TAG_DIRECTION = 1u, TAG_HOT = 2u, TAG_GAUGE = 3u };
+
+struct Stream {
+    uint32_t k0, k1;     // key
+    uint32_t link;       // lex*4 + mu
+    uint32_t s_lo, s_hi; // sweep
+    __device__ __forceinline__ U4 draw(uint32_t tag, uint32_t trial) const
+    {
+        return philox4x32_10(U4{link, s_lo, (tag << 24) | trial, s_hi}, k0, k1);
+    }
+};
+
+// uniform in (0,1): ((w >> 9) + 0.5) 2^-23, exact in float and double
+__device__ __forceinline__ float u01f(uint32_t w)
+{
+    return __fmul_rn(__uint2float_rn(w >> 9) + 0.5f, 1.1920928955078125e-7f);
+}
+__device__ __forceinline__ double u01d(uint32_t w)
+{
+    return (double)(w >> 9) * 1.1920928955078125e-7 + 5.9604644775390625e-8;
+}
+template <typename T> __device__ __forceinline__ T u01(uint32_t w);
+template <> __device__ __forceinline__ float u01<float>(uint32_t w) { return u01f(w); }
+template <> __device__ __forceinline__ double u01<double>(uint32_t w) { return u01d(w); }
+
+// math wrappers with one spelling for both precisions
+__device__ __forceinline__ float log_t(float x) { return logf(x); }
+__device__ __forceinline__ double log_t(double x) { return log(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+__device__ __forceinline__ float cospi_t(float x) { return cospif(x); }
+__device__ __forceinline__ double cospi_t(double x) { return cospi(x); }
+__device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// Haar element of SU(2) from one Philox block: Box-Muller on (w0,w1) and
+// (w2,w3) gives four normals, normalised onto S^3.
+template <typename T>
+__device__ __forceinline__ Quat<T> haar_from(U4 w)
+{
+    T u0 = u01<T>(w.x), u1 = u01<T>(w.y), u2 = u01<T>(w.z), u3 = u01<T>(w.w);
+    T r0 = sqrt_t(T(-2) * log_t(u0));
+    T r1 = sqrt_t(T(-2) * log_t(u2));
+    T s0, c0, s1, c1;
+    sincospi_t(T(2) * u1, &s0, &c0);
+    sincospi_t(T(2) * u3, &s1, &c1);
+    return qnormalise(Quat<T>{r0 * c0, r0 * s0, r1 * c1, r1 * s1});
+}
+
+// --------------------------------------------------------------------------
+// exact division of 0 <= n < 2^31 by a run-time constant d >= 1
+// (multiply-high with a rounded-up reciprocal: Granlund & Montgomery 1994)
+// --------------------------------------------------------------------------
+struct FastDiv {
+    uint32_t d, m, s;
+};
+
+__host__ __device__ __forceinline__ uint32_t umulhi32(uint32_t a, uint32_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    FastDiv f;
+    f.d = d;
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    f.s = s;
+    // m = floor(2^32 (2^s - d) / d) + 1
+    f.m = (uint32_t)((((1ull << s) - d) << 32) / d + 1);
+    return f;
+}
+
+__host__ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f)
+{
+    return (umulhi32(n, f.m) + n) >> f.s;
+}
+
+// --------------------------------------------------------------------------
+// even/odd geometry of one lattice
+// --------------------------------------------------------------------------
+struct Site {
+    int c[4];      // x, y, z, t
+    uint32_t r;    // row = y + Ns (z + Ns t)
+    uint32_t lex;
+};
+
+}  // namespace su2

@@ -1,0 +1,100 @@
+// su2_internal.h -- data structures shared by the kernels and the C-ABI
+// layer of the SU(2) heat-bath library.
+//
+// Memory model: the caller owns two device buffers and binds them to a
+// handle.  The LINK buffer holds every lattice of the handle; the WORK
+// buffer holds the per-lattice descriptors, reduction partials, the
+// per-sweep plaquette ring, the Polyakov field and a staging area for host
+// copies.  The library never allocates device memory.
+//
+// Link layout of one lattice (V sites, Vh = V/2):
+//   FP32: float4   U[mu][parity][eo]              (16 B per link)
+//   FP64: double2  U[mu][parity][plane][eo]       plane 0 = (a0,a1), 1 = (a2,a3)
+// so a warp touching 32 consecutive eo reads 512 contiguous bytes per access.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "su2_device.cuh"
+
+namespace su2 {
+
+constexpr int TPB = 256;            // threads per block of every lattice kernel
+constexpr int KP_CAP = 4096;        // Kennedy-Pendleton trial cap
+constexpr int PLAQ_RING = 4096;     // per-lattice plaquette slots for host output
+constexpr size_t STAGE_BYTES = size_t(32) << 20;
+constexpr uint32_t STATUS_CAP_HIT = 1u;
+
+// One per lattice, resident in the work buffer.  The first block is fixed
+// at bind time; the second is written by the parameter kernel at every
+// heat-bath call; the counters are advanced by the kernels.
+struct LatDesc {
+    int32_t Ns, Nt, Nh, Vs;
+    uint32_t V, Vh;
+    FastDiv div_nh, div_ns;
+    uint64_t link_off;      // byte offset of this lattice in the link buffer
+    uint64_t field_off;     // double offset of its Polyakov field
+    // per call
+    double beta;
+    uint64_t seed;
+    uint64_t sweep_base;    // sweep index stored at plaq_out[0]
+    double* plaq_out;       // device, nullable
+    // advanced by the kernels
+    uint64_t sweep;         // cumulative sweep counter
+    unsigned long long trials, updates, caps;
+};
+
+// Everything a kernel needs, passed by value.
+struct Ctx {
+    void* links;
+    LatDesc* desc;
+    const uint32_t* phase_start;   // [n+1] first block of each lattice, V/2 links
+    const uint32_t* site_start;    // [n+1] ... V sites
+    const uint32_t* spat_start;    // [n+1] ... Ns^3 spatial sites
+    double* plaq_partial;          // [3][phase blocks]
+    double* obs_partial;           // [obs_rows][max(site, spat) blocks]
+    double* field;                 // Polyakov fields
+    double* ring;                  // [n][PLAQ_RING]
+    uint32_t* status;
+    int n;
+    uint32_t phase_blocks, site_blocks, spat_blocks;
+};
+
+// lattice owning grid block b: largest l with start[l] <= b
+__device__ __forceinline__ int lattice_of_block(const uint32_t* start, int n, uint32_t b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ----- launchers (defined in the .cu files, called by the C-ABI layer) -----
+constexpr int PARAM_CHUNK = 64;
+struct ParamChunk {
+    int first, count;
+    double beta[PARAM_CHUNK];
+    uint64_t seed[PARAM_CHUNK];
+    double* plaq_out[PARAM_CHUNK];
+};
+cudaError_t launch_set_params(const Ctx& c, const ParamChunk& pc, cudaStream_t s);
+cudaError_t launch_phase(const Ctx& c, int dtype, int mu, int parity, bool plaq,
+                         int32_t* dbg_trials, cudaStream_t s);
+cudaError_t launch_sweep_end(const Ctx& c, bool plaq, cudaStream_t s);
+cudaError_t launch_init(const Ctx& c, int dtype, int l, uint32_t V, int hot, uint64_t seed,
+                        cudaStream_t s);
+cudaError_t launch_links_to_canonical(const Ctx& c, int dtype, int l, uint32_t lex0,
+                                      uint32_t nsite, double* dst, cudaStream_t s);
+cudaError_t launch_links_from_canonical(const Ctx& c, int dtype, int l, uint32_t lex0,
+                                        uint32_t nsite, const double* src, cudaStream_t s);
+cudaError_t launch_gauge(const Ctx& c, int dtype, int l, uint32_t V, uint64_t seed, cudaStream_t s);
+cudaError_t launch_plaquette(const Ctx& c, int dtype, double* out_dev, cudaStream_t s);
+cudaError_t launch_polyakov(const Ctx& c, int dtype, double* out_signed_dev,
+                            double* out_abs_dev, cudaStream_t s);
+cudaError_t launch_correlator(const Ctx& c, int rmax, double* out_dev, int accumulate,
+                              cudaStream_t s);
+
+}  // namespace su2

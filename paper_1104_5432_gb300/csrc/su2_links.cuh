@@ -1,0 +1,135 @@
+// su2_links.cuh -- typed access to one lattice's links in the even/odd
+// structure-of-arrays layout, and the decomposition of an even/odd index
+// into coordinates and neighbours.
+#pragma once
+#include "su2_internal.h"
+
+namespace su2 {
+
+template <typename T> struct Links;
+
+// FP32: float4 U[mu][parity][eo]
+template <> struct Links<float> {
+    float4* base;
+    uint32_t Vh;
+    __device__ __forceinline__ Links(void* links, const LatDesc& d)
+        : base(reinterpret_cast<float4*>(static_cast<char*>(links) + d.link_off)), Vh(d.Vh) {}
+    __device__ __forceinline__ size_t idx(int mu, int p, uint32_t eo) const
+    {
+        return size_t(mu * 2 + p) * Vh + eo;
+    }
+    __device__ __forceinline__ Quat<float> load(int mu, int p, uint32_t eo) const
+    {
+        const float4 v = __ldg(base + idx(mu, p, eo));
+        return {v.x, v.y, v.z, v.w};
+    }
+    __device__ __forceinline__ Quat<float> load_rw(int mu, int p, uint32_t eo) const
+    {
+        const float4 v = base[idx(mu, p, eo)];
+        return {v.x, v.y, v.z, v.w};
+    }
+    __device__ __forceinline__ void store(int mu, int p, uint32_t eo, const Quat<float>& q) const
+    {
+        base[idx(mu, p, eo)] = make_float4(q.a0, q.a1, q.a2, q.a3);
+    }
+};
+
+// FP64: double2 U[mu][parity][plane][eo]
+template <> struct Links<double> {
+    double2* base;
+    uint32_t Vh;
+    __device__ __forceinline__ Links(void* links, const LatDesc& d)
+        : base(reinterpret_cast<double2*>(static_cast<char*>(links) + d.link_off)), Vh(d.Vh) {}
+    __device__ __forceinline__ size_t idx(int mu, int p, int plane, uint32_t eo) const
+    {
+        return size_t((mu * 2 + p) * 2 + plane) * Vh + eo;
+    }
+    __device__ __forceinline__ Quat<double> load(int mu, int p, uint32_t eo) const
+    {
+        const double2 lo = __ldg(base + idx(mu, p, 0, eo));
+        const double2 hi = __ldg(base + idx(mu, p, 1, eo));
+        return {lo.x, lo.y, hi.x, hi.y};
+    }
+    __device__ __forceinline__ Quat<double> load_rw(int mu, int p, uint32_t eo) const
+    {
+        const double2 lo = base[idx(mu, p, 0, eo)];
+        const double2 hi = base[idx(mu, p, 1, eo)];
+        return {lo.x, lo.y, hi.x, hi.y};
+    }
+    __device__ __forceinline__ void store(int mu, int p, uint32_t eo, const Quat<double>& q) const
+    {
+        base[idx(mu, p, 0, eo)] = make_double2(q.a0, q.a1);
+        base[idx(mu, p, 1, eo)] = make_double2(q.a2, q.a3);
+    }
+};
+
+// Coordinates of the site with index eo inside parity p.
+struct EoSite {
+    int c[4];        // x, y, z, t
+    int Ns, Nt;
+    uint32_t Nh;
+    uint32_t r;      // row = y + Ns (z + Ns t);  eo = x/2 + Nh r;  lex = x + Ns r
+
+    __device__ __forceinline__ EoSite(const LatDesc& d, uint32_t eo, int p)
+    {
+        Ns = d.Ns;
+        Nt = d.Nt;
+        Nh = (uint32_t)d.Nh;
+        r = fdiv(eo, d.div_nh);
+        const uint32_t xh = eo - r * Nh;
+        const uint32_t q = fdiv(r, d.div_ns);
+        const uint32_t y = r - q * (uint32_t)Ns;
+        const uint32_t t = fdiv(q, d.div_ns);
+        const uint32_t z = q - t * (uint32_t)Ns;
+        c[1] = (int)y;
+        c[2] = (int)z;
+        c[3] = (int)t;
+        c[0] = (int)(2 * xh) + ((p + c[1] + c[2] + c[3]) & 1);
+    }
+
+    // the site with lexicographic index lex (any parity); *parity gets its parity
+    __device__ __forceinline__ static EoSite from_lex(const LatDesc& d, uint32_t lex, int* parity)
+    {
+        const uint32_t r = fdiv(lex, d.div_ns);
+        const uint32_t x = lex - r * (uint32_t)d.Ns;
+        const uint32_t q = fdiv(r, d.div_ns);
+        const uint32_t y = r - q * (uint32_t)d.Ns;
+        const uint32_t t = fdiv(q, d.div_ns);
+        const uint32_t z = q - t * (uint32_t)d.Ns;
+        const int p = (int)((x + y + z + t) & 1u);
+        *parity = p;
+        return EoSite(d, lex >> 1, p);
+    }
+
+    __device__ __forceinline__ uint32_t lex() const { return (uint32_t)c[0] + (uint32_t)Ns * r; }
+
+    __device__ __forceinline__ int extent(int d) const { return d == 3 ? Nt : Ns; }
+
+    // row stride of direction d (d >= 1)
+    __device__ __forceinline__ uint32_t rstride(int d) const
+    {
+        return d == 1 ? 1u : (d == 2 ? (uint32_t)Ns : (uint32_t)Ns * (uint32_t)Ns);
+    }
+
+    // even/odd index of x + s1 e_d1 + s2 e_d2 (s = -1, 0, +1; d1 != d2)
+    __device__ __forceinline__ uint32_t nb(int d1, int s1, int d2 = 0, int s2 = 0) const
+    {
+        int x = c[0];
+        int rr = (int)r;
+        auto step = [&](int d, int s) {
+            if (s == 0) return;
+            const int L = extent(d);
+            int v = c[d] + s;
+            int delta = s;
+            if (v == L) delta = s - L;
+            else if (v < 0) delta = s + L;
+            if (d == 0) x += delta;
+            else rr += delta * (int)rstride(d);
+        };
+        step(d1, s1);
+        step(d2, s2);
+        return (uint32_t)(x >> 1) + Nh * (uint32_t)rr;
+    }
+};
+
+}  // namespace su2

@@ -1,0 +1,251 @@
+"""Thin Python binding of the C ABI in ``include/su2.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library ``libsu2gb300.so``.  PyTorch supplies the two device buffers a
+handle needs (caching allocator) and the current CUDA stream.  There is no
+CPU fallback: if the library cannot be built or loaded, this module raises.
+
+Names follow the C ABI without the ``su2_`` prefix.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+SU2_OK = 0
+SU2_E_INVAL = -1
+SU2_E_NOMEM = -2
+SU2_E_CUDA = -3
+SU2_E_TRIALS = -4
+
+F32, F64 = 0, 1
+COLD, HOT = 0, 1
+KP_CAP = 4096
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SU2Error(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"su2 error {code}: {msg}")
+        self.code = code
+
+
+def load(build_if_needed: bool = True):
+    """Load (building first if needed) the CUDA library and declare its ABI."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_needed else _build.LIB
+        if not os.path.exists(path):
+            raise SU2Error(SU2_E_CUDA, f"CUDA library missing: {path}")
+        L = C.CDLL(path)
+        i, d, u64, sz, P = C.c_int, C.c_double, C.c_uint64, C.c_size_t, C.c_void_p
+        pp = C.POINTER(C.c_void_p)
+        sig = {
+            "su2_lattice_create": (i, [i, i, i, pp]),
+            "su2_batch_create": (i, [i, P, P, i, pp]),
+            "su2_lattice_destroy": (i, [P]),
+            "su2_lattice_count": (i, [P, P]),
+            "su2_lattice_volume": (i, [P, i, P]),
+            "su2_memory_requirements": (i, [P, P, P]),
+            "su2_bind_memory": (i, [P, P, sz, P, sz]),
+            "su2_set_stream": (i, [P, P]),
+            "su2_init": (i, [P, i, u64]),
+            "su2_batch_init": (i, [P, i, P]),
+            "su2_heatbath": (i, [P, d, i, u64, P]),
+            "su2_batch_heatbath": (i, [P, P, i, P, P]),
+            "su2_heatbath_phase": (i, [P, d, i, i, u64, P]),
+            "su2_plaquette": (i, [P, P]),
+            "su2_polyakov_loop": (i, [P, P, P]),
+            "su2_polyakov_correlator": (i, [P, i, P, i]),
+            "su2_get_links": (i, [P, i, P]),
+            "su2_set_links": (i, [P, i, P]),
+            "su2_gauge_transform": (i, [P, i, u64]),
+            "su2_stats": (i, [P, i, P]),
+            "su2_get_sweep": (i, [P, i, P]),
+            "su2_set_sweep": (i, [P, i, u64]),
+            "su2_sync": (i, [P]),
+            "su2_last_error": (C.c_char_p, []),
+            "su2_selftest_fastdiv": (u64, [C.c_uint32, C.c_uint32]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(rc: int) -> int:
+    if rc != SU2_OK:
+        raise SU2Error(rc, load().su2_last_error().decode())
+    return rc
+
+
+def _ptr(x) -> Optional[int]:
+    """Address of a numpy array or torch tensor (None passes through)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _u64_array(vals) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray([int(v) & 0xFFFFFFFFFFFFFFFF for v in vals],
+                                           dtype=np.uint64))
+
+
+class Lattice:
+    """n >= 1 SU(2) lattices Ns^3 x Nt of one precision on the current CUDA
+    device, with device memory from PyTorch's caching allocator."""
+
+    def __init__(self, Ns, Nt=None, dtype: int = F32, *, stream=None):
+        import torch
+
+        lib = load()
+        if isinstance(Ns, (list, tuple, np.ndarray)):
+            shapes = [(int(a), int(b)) for a, b in zip(Ns, Nt)]
+        else:
+            shapes = [(int(Ns), int(Nt))]
+        self.shapes = shapes
+        self.n = len(shapes)
+        self.dtype = dtype
+        h = C.c_void_p()
+        ns = np.array([s[0] for s in shapes], np.int32)
+        nt = np.array([s[1] for s in shapes], np.int32)
+        _check(lib.su2_batch_create(self.n, ns.ctypes.data, nt.ctypes.data, dtype, C.byref(h)))
+        self._h = h
+        lb, wb = C.c_size_t(), C.c_size_t()
+        _check(lib.su2_memory_requirements(h, C.byref(lb), C.byref(wb)))
+        self.link_bytes, self.work_bytes = lb.value, wb.value
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.links_buf = torch.empty(self.link_bytes, dtype=torch.uint8, device=dev)
+        self.work_buf = torch.empty(self.work_bytes, dtype=torch.uint8, device=dev)
+        _check(lib.su2_bind_memory(h, self.links_buf.data_ptr(), self.link_bytes,
+                                   self.work_buf.data_ptr(), self.work_bytes))
+        self.set_stream(stream if stream is not None else torch.cuda.current_stream())
+
+    # -- handle ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().su2_lattice_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+        self.stream = stream
+        _check(load().su2_set_stream(self._h, raw))
+
+    def volume(self, l: int = 0) -> int:
+        v = C.c_uint64()
+        _check(load().su2_lattice_volume(self._h, l, C.byref(v)))
+        return v.value
+
+    # -- the method ---------------------------------------------------------
+    def init(self, start: int, seed: int):
+        _check(load().su2_init(self._h, int(start), int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+    def batch_init(self, start: int, seeds: Sequence[int]):
+        s = _u64_array(seeds)
+        _check(load().su2_batch_init(self._h, int(start), s.ctypes.data))
+
+    def heatbath(self, beta: float, nsweeps: int, seed: int, plaq=True):
+        """plaq: True -> returns numpy [n, nsweeps] (host output), a numpy /
+        torch float64 buffer of n*nsweeps -> filled in place, None/False ->
+        no plaquette."""
+        out = None
+        if plaq is True:
+            out = np.zeros((self.n, nsweeps), np.float64)
+        elif plaq is not None and plaq is not False:
+            out = plaq
+        _check(load().su2_heatbath(self._h, float(beta), int(nsweeps),
+                                   int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out)))
+        return out
+
+    def batch_heatbath(self, betas: Sequence[float], nsweeps: int, seeds: Sequence[int],
+                       plaq=True):
+        b = np.ascontiguousarray(np.asarray(betas, np.float64))
+        s = _u64_array(seeds)
+        out = None
+        if plaq is True:
+            out = np.zeros((self.n, nsweeps), np.float64)
+        elif plaq is not None and plaq is not False:
+            out = plaq
+        _check(load().su2_batch_heatbath(self._h, b.ctypes.data, int(nsweeps), s.ctypes.data,
+                                         _ptr(out)))
+        return out
+
+    def heatbath_phase(self, beta: float, mu: int, parity: int, seed: int, trials=None):
+        _check(load().su2_heatbath_phase(self._h, float(beta), int(mu), int(parity),
+                                         int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(trials)))
+
+    def plaquette(self, out=None):
+        o = np.zeros(self.n, np.float64) if out is None else out
+        _check(load().su2_plaquette(self._h, _ptr(o)))
+        return o
+
+    def polyakov_loop(self):
+        s = np.zeros(self.n, np.float64)
+        a = np.zeros(self.n, np.float64)
+        _check(load().su2_polyakov_loop(self._h, _ptr(s), _ptr(a)))
+        return s, a
+
+    def polyakov_correlator(self, rmax: int, out=None, accumulate: bool = False):
+        o = np.zeros((self.n, rmax + 1), np.float64) if out is None else out
+        _check(load().su2_polyakov_correlator(self._h, int(rmax), _ptr(o), 1 if accumulate else 0))
+        return o
+
+    # -- state ---------------------------------------------------------------
+    def get_links(self, l: int = 0, out=None):
+        V = self.volume(l)
+        o = np.empty((V, 4, 4), np.float64) if out is None else out
+        _check(load().su2_get_links(self._h, l, _ptr(o)))
+        return o
+
+    def set_links(self, links, l: int = 0):
+        if isinstance(links, np.ndarray):
+            links = np.ascontiguousarray(links, np.float64)
+            if links.size != self.volume(l) * 16:
+                raise ValueError("links has the wrong size")
+        _check(load().su2_set_links(self._h, l, _ptr(links)))
+
+    def gauge_transform(self, seed: int, l: int = 0):
+        _check(load().su2_gauge_transform(self._h, l, int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+    def stats(self, l: int = 0):
+        o = np.zeros(3, np.uint64)
+        _check(load().su2_stats(self._h, l, o.ctypes.data))
+        return {"trials": int(o[0]), "updates": int(o[1]), "cap_hits": int(o[2])}
+
+    def get_sweep(self, l: int = 0) -> int:
+        v = C.c_uint64()
+        _check(load().su2_get_sweep(self._h, l, C.byref(v)))
+        return v.value
+
+    def set_sweep(self, sweep: int, l: int = 0):
+        _check(load().su2_set_sweep(self._h, l, int(sweep)))
+
+    def sync(self):
+        _check(load().su2_sync(self._h))

@@ -1,0 +1,354 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances:
+  FP64 links, one phase or sweep   max |diff| <= 1e-12, identical trial counts
+  FP32 links, one phase             max |diff| <= 2e-5 on links whose accept
+                                    decisions agree; flipped decisions < 1e-4
+  FP64 reductions                   <= 1e-13 (relative for P, absolute for L, C)
+  FP32 reductions                   <= 1e-6 absolute (FP32 products, FP64 sums)
+FP32 comparisons feed the oracle the GPU's own FP32 links widened to FP64,
+one phase at a time, so an input rounding difference never propagates.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1104_5432_gb300 import inputs, su2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PHASES = [(mu, p) for mu in range(4) for p in range(2)]
+
+
+def lattice(Ns, Nt, dtype):
+    return su2.Lattice(Ns, Nt, dtype)
+
+
+def parity_mask(Ns, Nt):
+    t, z, y, x = np.meshgrid(range(Nt), range(Ns), range(Ns), range(Ns), indexing="ij")
+    return ((x + y + z + t) % 2).reshape(-1)
+
+
+# ----------------------------------------------------------------------------
+# start configurations, layout round trip
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype,tol", [(su2.F64, 1e-14), (su2.F32, 1e-6)])
+@pytest.mark.parametrize("Ns,Nt", [(4, 4), (6, 4), (10, 6)])
+def test_init_parity(dtype, tol, Ns, Nt):
+    lat = lattice(Ns, Nt, dtype)
+    lat.init(su2.COLD, 0)
+    np.testing.assert_array_equal(lat.get_links(), O.init(Ns, Nt, False, 0))
+    lat.init(su2.HOT, 77)
+    g = lat.get_links()
+    assert np.max(np.abs(g - O.init(Ns, Nt, True, 77))) <= tol
+    assert lat.get_sweep() == 0
+
+
+@pytest.mark.parametrize("dtype", [su2.F64, su2.F32])
+def test_links_round_trip(dtype):
+    Ns, Nt = 6, 4
+    src = inputs.random_links(Ns, Nt, 3)
+    lat = lattice(Ns, Nt, dtype)
+    lat.set_links(src)
+    got = lat.get_links()
+    if dtype == su2.F64:
+        np.testing.assert_array_equal(got, src)
+    else:
+        np.testing.assert_array_equal(got, src.astype(np.float32).astype(np.float64))
+    # device-pointer path of the same calls
+    dev = torch.from_numpy(src).cuda()
+    lat.set_links(dev)
+    out = torch.empty_like(dev)
+    lat.get_links(out=out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), got)
+
+
+# ----------------------------------------------------------------------------
+# observables
+# ----------------------------------------------------------------------------
+def thermalised(Ns, Nt, seed=5, beta=2.3, sweeps=3):
+    links = O.init(Ns, Nt, True, seed)
+    links, _, _ = O.heatbath(Ns, Nt, links, beta, sweeps, seed)
+    return links
+
+
+@pytest.mark.parametrize("Ns,Nt", [(4, 4), (6, 2), (8, 4), (10, 6)])
+def test_observables_fp64(Ns, Nt):
+    links = thermalised(Ns, Nt)
+    lat = lattice(Ns, Nt, su2.F64)
+    lat.set_links(links)
+    P = lat.plaquette()[0]
+    Po = O.plaquette(Ns, Nt, links)
+    assert abs(P - Po) <= 1e-13 * abs(Po)
+    s, a = lat.polyakov_loop()
+    so, ao, _ = O.polyakov(Ns, Nt, links)
+    assert abs(s[0] - so) <= 1e-13 and abs(a[0] - ao) <= 1e-13
+    rmax = Ns // 2
+    C = lat.polyakov_correlator(rmax)[0]
+    np.testing.assert_allclose(C, O.correlator(Ns, Nt, links, rmax), rtol=0, atol=1e-13)
+    # device outputs and accumulation
+    acc = torch.zeros(rmax + 1, dtype=torch.float64, device="cuda")
+    lat.polyakov_correlator(rmax, out=acc, accumulate=True)
+    lat.polyakov_correlator(rmax, out=acc, accumulate=True)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(acc.cpu().numpy(), 2 * C, rtol=0, atol=1e-13)
+    host_acc = np.ones((1, rmax + 1))
+    lat.polyakov_correlator(rmax, out=host_acc, accumulate=True)
+    np.testing.assert_allclose(host_acc[0], 1 + C, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("Ns,Nt", [(6, 4), (8, 8)])
+def test_observables_fp32(Ns, Nt):
+    lat = lattice(Ns, Nt, su2.F32)
+    lat.set_links(thermalised(Ns, Nt))
+    links = lat.get_links()  # the FP32 links, widened exactly
+    assert abs(lat.plaquette()[0] - O.plaquette(Ns, Nt, links)) <= 1e-6
+    s, _ = lat.polyakov_loop()
+    assert abs(s[0] - O.polyakov(Ns, Nt, links)[0]) <= 1e-6
+    np.testing.assert_allclose(lat.polyakov_correlator(Ns // 2)[0],
+                               O.correlator(Ns, Nt, links, Ns // 2), rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("dtype,tol", [(su2.F64, 1e-13), (su2.F32, 2e-6)])
+def test_gauge_invariance_gpu(dtype, tol):
+    Ns, Nt = 6, 4
+    lat = lattice(Ns, Nt, dtype)
+    lat.set_links(thermalised(Ns, Nt))
+    before = lat.get_links()
+    P0, (L0, _), C0 = lat.plaquette()[0], lat.polyakov_loop(), lat.polyakov_correlator(3)[0]
+    lat.gauge_transform(1234)
+    after = lat.get_links()
+    assert np.max(np.abs(after - before)) > 0.1
+    ref = O.gauge_transform(Ns, Nt, before, 1234)
+    assert np.max(np.abs(after - ref)) <= (1e-14 if dtype == su2.F64 else 1e-6)
+    assert abs(lat.plaquette()[0] - P0) <= tol
+    assert abs(lat.polyakov_loop()[0][0] - L0[0]) <= tol
+    np.testing.assert_allclose(lat.polyakov_correlator(3)[0], C0, rtol=0, atol=tol)
+
+
+# ----------------------------------------------------------------------------
+# heat-bath phases and sweeps
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("Ns,Nt", [(4, 4), (6, 4), (10, 6), (2, 2)])
+def test_phase_parity_fp64(Ns, Nt):
+    """Every phase from the GPU state before it: links to 1e-12, identical
+    per-link trial counts, nothing outside the phase touched."""
+    V = Ns ** 3 * Nt
+    par = parity_mask(Ns, Nt)
+    lat = lattice(Ns, Nt, su2.F64)
+    lat.init(su2.HOT, 11)
+    lat.set_sweep(5)
+    beta, seed = 2.3, 21
+    for mu, p in PHASES:
+        before = lat.get_links()
+        trials = torch.full((V,), -2, dtype=torch.int32, device="cuda")
+        lat.heatbath_phase(beta, mu, p, seed, trials)
+        after = lat.get_links()
+        ref, rt, _ = O.heatbath_phase(Ns, Nt, before, beta, mu, p, seed, 5)
+        assert np.max(np.abs(after - ref)) <= 1e-12, (mu, p)
+        gt = trials.cpu().numpy()
+        np.testing.assert_array_equal(gt[par == p], rt[par == p, mu])
+        assert np.all(gt[par != p] == -2)
+    assert lat.get_sweep() == 5
+
+
+@pytest.mark.parametrize("Ns,Nt", [(12, 12), (10, 6)])
+def test_phase_parity_fp32(Ns, Nt):
+    V = Ns ** 3 * Nt
+    par = parity_mask(Ns, Nt)
+    lat = lattice(Ns, Nt, su2.F32)
+    lat.init(su2.HOT, 12)
+    lat.heatbath(2.4, 2, 3, plaq=None)
+    beta, seed = 2.4, 31
+    sweep = lat.get_sweep()
+    flips = n = 0
+    worst = 0.0
+    for mu, p in PHASES:
+        before = lat.get_links()
+        trials = torch.full((V,), -2, dtype=torch.int32, device="cuda")
+        lat.heatbath_phase(beta, mu, p, seed, trials)
+        after = lat.get_links()
+        ref, rt, _ = O.heatbath_phase(Ns, Nt, before, beta, mu, p, seed, sweep)
+        gt = trials.cpu().numpy()
+        same = gt[par == p] == rt[par == p, mu]
+        flips += int((~same).sum())
+        n += int(same.size)
+        diff = np.max(np.abs(after[par == p, mu] - ref[par == p, mu]), axis=1)
+        worst = max(worst, float(diff[same].max()))
+        # links outside the phase are untouched
+        other = np.ones((V, 4), bool)
+        other[par == p, mu] = False
+        np.testing.assert_array_equal(after[other], before[other])
+    assert worst <= 2e-5, worst
+    assert flips < 1e-4 * n, (flips, n)
+
+
+@pytest.mark.parametrize("Ns,Nt,beta", [(8, 8, 2.3), (6, 4, 6.0), (4, 8, 0.7)])
+def test_sweeps_parity_fp64(Ns, Nt, beta):
+    """Two full sweeps (graph-replayed phases + fused plaquette) against the
+    oracle's sweeps: links, per-sweep plaquettes and counters."""
+    lat = lattice(Ns, Nt, su2.F64)
+    lat.init(su2.HOT, 1)
+    plaq = lat.heatbath(beta, 2, 1)
+    ref, rplaq, cnt = O.heatbath(Ns, Nt, O.init(Ns, Nt, True, 1), beta, 2, 1)
+    assert np.max(np.abs(lat.get_links() - ref)) <= 1e-12
+    np.testing.assert_allclose(plaq[0], rplaq, rtol=1e-13, atol=0)
+    st = lat.stats()
+    assert (st["trials"], st["updates"], st["cap_hits"]) == tuple(int(c) for c in cnt)
+    assert lat.get_sweep() == 2
+    # the fused per-sweep plaquette equals the stand-alone kernel
+    assert abs(plaq[0, -1] - lat.plaquette()[0]) <= 1e-13 * abs(plaq[0, -1])
+
+
+def test_fused_plaquette_fp32_and_device_output():
+    Ns, Nt = 8, 8
+    lat = lattice(Ns, Nt, su2.F32)
+    lat.init(su2.HOT, 2)
+    dev = torch.zeros(5, dtype=torch.float64, device="cuda")
+    lat.heatbath(2.5, 5, 2, plaq=dev)
+    torch.cuda.synchronize()
+    fused = dev.cpu().numpy()
+    links = lat.get_links()
+    assert abs(fused[-1] - O.plaquette(Ns, Nt, links)) <= 1e-6
+    assert abs(fused[-1] - lat.plaquette()[0]) <= 1e-6
+    assert np.all(np.diff(fused) != 0)
+
+
+@pytest.mark.parametrize("dtype", [su2.F32, su2.F64])
+def test_composition_and_checkpoint_resume(dtype):
+    Ns, Nt = 6, 4
+    a = lattice(Ns, Nt, dtype)
+    a.init(su2.HOT, 9)
+    pa = a.heatbath(2.2, 5, 4)
+    b = lattice(Ns, Nt, dtype)
+    b.init(su2.HOT, 9)
+    pb1 = b.heatbath(2.2, 2, 4)
+    ck_links, ck_sweep = b.get_links(), b.get_sweep()
+    c = lattice(Ns, Nt, dtype)
+    c.set_links(ck_links)
+    c.set_sweep(ck_sweep)
+    pb2 = c.heatbath(2.2, 3, 4)
+    np.testing.assert_array_equal(c.get_links(), a.get_links())
+    np.testing.assert_array_equal(np.concatenate([pb1[0], pb2[0]]), pa[0])
+    assert c.get_sweep() == 5
+
+
+@pytest.mark.parametrize("dtype", [su2.F32, su2.F64])
+def test_batch_equals_single(dtype):
+    """Every lattice of a batch (uneven shapes, own beta and seed) evolves
+    bit-identically to the same lattice run alone."""
+    shapes = [(4, 4), (6, 2), (8, 6), (4, 8), (2, 2)]
+    betas = [2.2, 2.6, 2.4, 0.9, 3.0]
+    seeds = [101, 202, 303, 404, 505]
+    B = su2.Lattice([s[0] for s in shapes], [s[1] for s in shapes], dtype)
+    B.batch_init(su2.HOT, seeds)
+    pb = B.batch_heatbath(betas, 3, seeds)
+    Pb = B.plaquette()
+    Lb, _ = B.polyakov_loop()
+    for l, (Ns, Nt) in enumerate(shapes):
+        s = lattice(Ns, Nt, dtype)
+        s.init(su2.HOT, seeds[l])
+        ps = s.heatbath(betas[l], 3, seeds[l])
+        np.testing.assert_array_equal(B.get_links(l), s.get_links())
+        np.testing.assert_array_equal(pb[l], ps[0])
+        assert Pb[l] == s.plaquette()[0]
+        assert Lb[l] == s.polyakov_loop()[0][0]
+        assert B.get_sweep(l) == 3
+        assert B.stats(l) == s.stats()
+
+
+def test_cap_hit_reported_and_links_kept():
+    Ns, Nt = 4, 4
+    lat = lattice(Ns, Nt, su2.F64)
+    lat.init(su2.HOT, 3)
+    before = lat.get_links()
+    lat.heatbath(1e-9, 1, 3, plaq=None)
+    with pytest.raises(su2.SU2Error) as e:
+        lat.sync()
+    assert e.value.code == su2.SU2_E_TRIALS
+    lat.sync()  # reported once
+    np.testing.assert_array_equal(lat.get_links(), before)
+    st = lat.stats()
+    V = Ns ** 3 * Nt
+    assert st["cap_hits"] == 4 * V and st["trials"] == su2.KP_CAP * 4 * V
+    # with host plaquette output the same call reports it directly
+    with pytest.raises(su2.SU2Error):
+        lat.heatbath(1e-9, 1, 3)
+
+
+def test_beta_zero_and_zero_staple_take_haar_branch():
+    Ns, Nt = 2, 2
+    V = Ns ** 3 * Nt
+    lat = lattice(Ns, Nt, su2.F64)
+    links = O.init(Ns, Nt, False, 0)
+    s = np.sqrt(3.0) / 2
+    for d, q in zip((1, 2, 4), ([1, 0, 0, 0], [-0.5, s, 0, 0], [-0.5, -s, 0, 0])):
+        links[d, 0] = q
+    lat.set_links(links)
+    trials = torch.full((V,), -2, dtype=torch.int32, device="cuda")
+    lat.heatbath_phase(2.3, 0, 0, 1, trials)
+    ref, rt, _ = O.heatbath_phase(Ns, Nt, links, 2.3, 0, 0, 1, 0)
+    assert trials[0].item() == 0 and rt[0, 0] == 0
+    assert np.max(np.abs(lat.get_links() - ref)) <= 1e-13
+    # beta = 0: every link a Haar draw, zero trials
+    lat.init(su2.HOT, 4)
+    lat.heatbath(0.0, 1, 8, plaq=None)
+    lat.sync()
+    assert lat.stats()["trials"] == 0 and lat.stats()["updates"] == 4 * V
+
+
+def test_invalid_arguments_leave_state():
+    lat = lattice(4, 4, su2.F32)
+    lat.init(su2.HOT, 1)
+    before = lat.get_links()
+    for call in (lambda: lat.heatbath(-1.0, 1, 1), lambda: lat.heatbath(float("nan"), 1, 1),
+                 lambda: lat.heatbath(2.0, -1, 1), lambda: lat.heatbath_phase(2.0, 4, 0, 1),
+                 lambda: lat.heatbath_phase(2.0, 0, 2, 1), lambda: lat.init(5, 1),
+                 lambda: lat.polyakov_correlator(3), lambda: lat.get_links(1)):
+        with pytest.raises((su2.SU2Error, ValueError)) as e:
+            call()
+    np.testing.assert_array_equal(lat.get_links(), before)
+    assert lat.heatbath(2.0, 0, 1).shape == (1, 0)
+    assert lat.get_sweep() == 0
+
+
+# ----------------------------------------------------------------------------
+# full size, in the launch configuration the benchmark times
+# ----------------------------------------------------------------------------
+def test_full_size_64_sampled():
+    """64^4 FP32 (1 GiB of links), hot start seed 3, one graph-replayed sweep
+    at beta = 2.5: U_0 on even sites comes from the first phase only, so a
+    sample of them is checked link by link against the oracle from the start
+    configuration; properties that hold at any size are checked in full."""
+    Ns = Nt = 64
+    V = Ns ** 4
+    lat = lattice(Ns, Nt, su2.F32)
+    lat.init(su2.HOT, 3)
+    start = lat.get_links()
+    plaq = lat.heatbath(2.5, 1, 3)
+    after = lat.get_links()
+    st = lat.stats()
+    assert st["updates"] == 4 * V and st["cap_hits"] == 0
+    norms = np.linalg.norm(after, axis=2)
+    assert np.max(np.abs(norms - 1.0)) <= 5e-7
+    assert abs(plaq[0, 0] - lat.plaquette()[0]) <= 1e-6
+    rng = np.random.default_rng(0)
+    par = None
+    checked = flips = 0
+    worst = 0.0
+    for lex in rng.choice(V, size=3000, replace=False):
+        x, y, z, t = lex % Ns, (lex // Ns) % Ns, (lex // Ns ** 2) % Ns, lex // Ns ** 3
+        if (x + y + z + t) % 2:
+            continue
+        u, tr = O.heatbath_link(Ns, Nt, start, 2.5, 0, int(lex), 3, 0)
+        d = np.max(np.abs(after[lex, 0] - u))
+        if d > 2e-5:
+            flips += 1
+        else:
+            worst = max(worst, d)
+        checked += 1
+    assert checked > 1000
+    assert flips <= 1, flips
+    assert worst <= 2e-5

@@ -404,3 +404,16 @@ def test_weak_coupling_limit():
     W = np.diag(ws)
     coef = np.linalg.solve(A.T @ W @ A, A.T @ W @ np.array(ys))
     assert abs(coef[0] - 0.75) < 0.02, coef
+
+
+def test_single_link_entry_matches_phase():
+    """The single-link entry point draws what the phase draws."""
+    Ns, Nt = 4, 4
+    links = inputs.random_links(Ns, Nt, 41)
+    new, trials, _ = O.heatbath_phase(Ns, Nt, links, 2.1, 2, 1, seed=6, sweep=3)
+    for lex in (1, 2, 77, 254):
+        par = sum(int(v) for v in np.unravel_index(lex, (Nt, Ns, Ns, Ns))) % 2
+        u, t = O.heatbath_link(Ns, Nt, links, 2.1, 2, lex, seed=6, sweep=3)
+        if par == 1:
+            np.testing.assert_array_equal(u, new[lex, 2])
+            assert t == trials[lex, 2]

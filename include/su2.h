@@ -190,6 +190,37 @@ int su2_sync(su2_lattice* lat);
 /* Message of the last failing call on this thread ("" if none). */
 const char* su2_last_error(void);
 
+/* ------------------------------------------------------------------ */
+/* allocation-free measurement                                          */
+/* ------------------------------------------------------------------ */
+
+/* Largest lattice (sites) su2_plaquette_static accepts. */
+#define SU2_STATIC_MAX_SITES 16777216
+
+/* The mean plaquette of one lattice, computed without any device
+ * allocation and without a caller work buffer.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory,
+ * such as code running inside a host framework that owns the whole device
+ * pool (its own cudaMalloc would fail or break the framework's budget), or
+ * code that must avoid the device-wide synchronisation that cudaMalloc and
+ * cudaFree can cause.
+ * links: device memory of the CURRENT device holding one lattice in the
+ *   library's link layout -- the link buffer of a single-lattice handle
+ *   (FP32: float4 U[mu][parity][eo]; FP64: double2 U[mu][parity][plane][eo],
+ *   plane 0 = (a0,a1), plane 1 = (a2,a3); eo = lex >> 1).
+ * Ns, Nt: even, >= 2, Ns^3 Nt <= SU2_STATIC_MAX_SITES (else SU2_E_INVAL).
+ * out: host or device double; a host output makes the call synchronous.
+ * stream: cudaStream_t (as void*), 0 = legacy default stream.
+ * Scratch: a fixed 512 KiB array in the library's static device memory,
+ * held by every GPU that loads the library until the process exits.  The
+ * first call on each device looks up that array's device address (with
+ * cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents: calls
+ * whose work overlaps on the GPU (other streams or host threads) race on
+ * it and must be ordered by the caller.  Allocates nothing. */
+int su2_plaquette_static(const void* links, int Ns, int Nt, int dtype, double* out,
+                         void* stream);
+
 /* Self-test of the host-side exact division used for site indexing:
  * returns the number of n in [0, limit) and divisors 1..dmax for which
  * it differs from n / d. */

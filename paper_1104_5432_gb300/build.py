@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsu2gb300.so")
-SOURCES = ["heatbath.cu", "observables.cu", "links.cu", "api.cu"]
+SOURCES = ["heatbath.cu", "observables.cu", "links.cu", "api.cu", "plaquette_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -327,6 +327,8 @@ int finish_output(su2_lattice* L, double* out, const double* dev_src, size_t cou
 
 }  // namespace
 
+void su2::record_error(const char* msg) { g_err = msg; }
+
 // --------------------------------------------------------------------------
 // exported
 // --------------------------------------------------------------------------

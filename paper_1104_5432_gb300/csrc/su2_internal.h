@@ -97,4 +97,7 @@ cudaError_t launch_polyakov(const Ctx& c, int dtype, double* out_signed_dev,
 cudaError_t launch_correlator(const Ctx& c, int rmax, double* out_dev, int accumulate,
                               cudaStream_t s);
 
+// sets the message returned by su2_last_error() for the calling thread
+void record_error(const char* msg);
+
 }  // namespace su2

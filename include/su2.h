@@ -221,6 +221,14 @@ const char* su2_last_error(void);
 int su2_plaquette_static(const void* links, int Ns, int Nt, int dtype, double* out,
                          void* stream);
 
+/* Test hook: exhaustive check, over every uniform grid point
+ * u = (k + 1/2) 2^-23, of the FP32 forms the heat-bath draw uses against
+ * FP64 references.  out: device double[4] receiving the maximum relative
+ * error of ln u, the maximum absolute error of cos^2(2 pi u), of
+ * sin/cos(2 pi u), and the maximum relative error of sqrt(u).  Asynchronous
+ * on `stream`. */
+int su2_selftest_math(void* out, void* stream);
+
 /* Self-test of the host-side exact division used for site indexing:
  * returns the number of n in [0, limit) and divisors 1..dmax for which
  * it differs from n / d. */

@@ -73,6 +73,8 @@ struct su2_lattice {
     size_t link_bytes = 0, work_bytes = 0;
     size_t off_status = 0, off_desc = 0, off_pstart = 0, off_sstart = 0, off_spstart = 0;
     size_t off_plaq = 0, off_obs = 0, off_field = 0, off_ring = 0, off_res = 0, off_stage = 0;
+    size_t off_chunks = 0, off_tickets = 0;
+    uint32_t max_chunks = 1;
     size_t res_doubles = 0;
     // bound state
     void* links = nullptr;
@@ -151,6 +153,11 @@ int layout(su2_lattice* L)
         rlim = std::min(rlim, L->Ns[l] / 2);
     }
     L->phase_blocks = L->phase_start[n];
+    L->max_chunks = 1;
+    for (int l = 0; l < n; ++l) {
+        const uint32_t nb = L->phase_start[l + 1] - L->phase_start[l];
+        L->max_chunks = std::max<uint32_t>(L->max_chunks, (3 * nb + SWEEP_CHUNK - 1) / SWEEP_CHUNK);
+    }
     L->site_blocks = L->site_start[n];
     L->spat_blocks = L->spat_start[n];
     L->rmax_limit = rlim;
@@ -173,6 +180,8 @@ int layout(su2_lattice* L)
     L->off_obs = take(8 * obs_rows);
     L->off_field = take(8 * fo);
     L->off_ring = take(8 * (size_t)PLAQ_RING * n);
+    L->off_chunks = take(8 * (size_t)L->max_chunks * n);
+    L->off_tickets = take(4 * (size_t)n);
     L->res_doubles = (size_t)n * (rlim + 1) + 2 * (size_t)n;
     L->off_res = take(8 * L->res_doubles);
     L->off_stage = take(STAGE_BYTES);
@@ -424,6 +433,7 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
     SU2_CUDA(cudaMemcpy(w + lat->off_spstart, lat->spat_start.data(), 4 * (lat->n + 1),
                         cudaMemcpyHostToDevice));
     SU2_CUDA(cudaMemset(w + lat->off_ring, 0, 8 * (size_t)PLAQ_RING * lat->n));
+    SU2_CUDA(cudaMemset(w + lat->off_tickets, 0, 4 * (size_t)lat->n));
 
     Ctx& c = lat->ctx;
     c.links = links;
@@ -435,6 +445,9 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
     c.obs_partial = reinterpret_cast<double*>(w + lat->off_obs);
     c.field = reinterpret_cast<double*>(w + lat->off_field);
     c.ring = reinterpret_cast<double*>(w + lat->off_ring);
+    c.chunk_partial = reinterpret_cast<double*>(w + lat->off_chunks);
+    c.chunk_count = reinterpret_cast<uint32_t*>(w + lat->off_tickets);
+    c.max_chunks = lat->max_chunks;
     c.status = reinterpret_cast<uint32_t*>(w + lat->off_status);
     c.n = lat->n;
     c.phase_blocks = lat->phase_blocks;

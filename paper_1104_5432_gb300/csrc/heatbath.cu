@@ -21,6 +21,7 @@
 // at no extra memory traffic.
 #include "su2_internal.h"
 #include "su2_links.cuh"
+#include "su2_math.cuh"
 #include "su2_reduce.cuh"
 
 namespace su2 {
@@ -29,23 +30,34 @@ template <typename T> __device__ __forceinline__ T alpha_haar();
 template <> __device__ __forceinline__ float alpha_haar<float>() { return 1e-12f; }
 template <> __device__ __forceinline__ double alpha_haar<double>() { return 1e-12; }
 
+// warp partial sum in the link precision (fixed butterfly order)
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <typename T, int MU, bool PLAQ, bool DBG>
-__global__ void __launch_bounds__(TPB)
+__global__ void __launch_bounds__(TPB, HB_MIN_BLOCKS)
 hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 {
-    __shared__ double sred[TPB / 32];
-    __shared__ uint32_t ured[TPB / 32];
+    __shared__ uint32_t s_trials[TPB / 32];
+    __shared__ T s_plaq[TPB / 32];
 
     const int l = lattice_of_block(ctx.phase_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
     const uint32_t Vh = D.Vh;
-    const uint32_t i = (blockIdx.x - __ldg(ctx.phase_start + l)) * TPB + threadIdx.x;
+    const uint32_t blk0 = __ldg(ctx.phase_start + l);
+    const uint32_t i = (blockIdx.x - blk0) * TPB + threadIdx.x;
     const bool active = i < Vh;
     const Links<T> U(ctx.links, D);
     const int q = p ^ 1;
 
     T plaq = T(0);
-    uint32_t ntrial = 0, ncap = 0;
+    uint32_t ntrial = 0;
+    int ncap = 0;
 
     if (active) {
         const EoSite s(D, i, p);
@@ -72,8 +84,11 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             if (PLAQ && nu < MU) Sp[nu < MU ? nu : 0] = S;
         }
 
-        const T k = sqrt_t(qnorm2(A));
-        const T alpha = T(D.beta) * k;
+        // alpha = beta k and 1/(2 alpha) from one reciprocal square root of k^2
+        const T k2 = qnorm2(A);
+        const T rk = Math<T>::rsqrt(k2);
+        const T beta = T(D.beta);
+        const T alpha = beta * k2 * rk;
         const uint64_t sw = D.sweep;
         const Stream st{(uint32_t)D.seed, (uint32_t)(D.seed >> 32), s.lex() * 4u + MU,
                         (uint32_t)sw, (uint32_t)(sw >> 32)};
@@ -81,18 +96,18 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
         Quat<T> un;
         int32_t tr;
         if (!(alpha >= alpha_haar<T>())) {
-            // alpha -> 0 limit of the conditional law: a Haar draw
+            // alpha -> 0 limit of the conditional law (zero staple or beta = 0)
             un = haar_from<T>(st.draw(TAG_DIRECTION, 0));
             tr = 0;
         } else {
-            const T inv2a = T(0.5) / alpha;
+            const T inv2a = T(0.5) * rk / beta;
             T delta = T(0);
             tr = -1;
             for (int t = 0; t < KP_CAP; ++t) {
                 const U4 w = st.draw(TAG_TRIAL, (uint32_t)t);
                 const T r1 = u01<T>(w.x), r2 = u01<T>(w.y), r3 = u01<T>(w.z), r4 = u01<T>(w.w);
-                const T cs = cospi_t(T(2) * r2);
-                const T lam2 = -(log_t(r1) + cs * cs * log_t(r3)) * inv2a;
+                const T lam2 = -(Math<T>::ln_u01(r1) + Math<T>::cos2pi_sq(r2) *
+                                 Math<T>::ln_u01(r3)) * inv2a;
                 if (r4 * r4 <= T(1) - lam2) {
                     delta = T(2) * lam2;
                     tr = t + 1;
@@ -102,10 +117,10 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             if (tr > 0) {
                 const U4 w = st.draw(TAG_DIRECTION, 0);
                 const T cth = T(2) * u01<T>(w.x) - T(1);
-                const T sth = sqrt_t((T(1) - cth) * (T(1) + cth));
+                const T sth = Math<T>::sqrt_pos((T(1) - cth) * (T(1) + cth));
                 T sph, cph;
-                sincospi_t(T(2) * u01<T>(w.y), &sph, &cph);
-                const T vl = sqrt_t(delta * (T(2) - delta));
+                Math<T>::sincos2pi(u01<T>(w.y), &sph, &cph);
+                const T vl = Math<T>::sqrt_pos(delta * (T(2) - delta));
                 const Quat<T> X = {T(1) - delta, vl * sth * cph, vl * sth * sph, vl * cth};
                 un = qnormalise(qmul_nd(X, A));
             }
@@ -125,19 +140,31 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
         }
     }
 
-    // block totals: integer counters by atomics (exact), plaquette partial
-    // per block (summed later in a fixed order)
-    const uint32_t bt = block_sum<TPB>(ntrial, ured);
-    const uint32_t bc = block_sum<TPB>(ncap, ured);
-    const uint32_t bu = block_sum<TPB>(active ? 1u : 0u, ured);
-    if (PLAQ) {
-        const double bp = block_sum<TPB>((double)plaq, sred);
-        if (threadIdx.x == 0) ctx.plaq_partial[(size_t)(MU - 1) * ctx.phase_blocks + blockIdx.x] = bp;
+    // One barrier for every block total: warp partials to shared memory,
+    // cap hits counted by the barrier itself.  Trial counts are exact
+    // integers (atomics); the plaquette partial is written per block and
+    // summed later in a fixed order.
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t wt = __reduce_add_sync(0xffffffffu, ntrial);
+    T wp = T(0);
+    if (PLAQ) wp = warp_sum_t(plaq);
+    if (lane == 0) {
+        s_trials[w] = wt;
+        if (PLAQ) s_plaq[w] = wp;
     }
+    const int bc = __syncthreads_count(ncap);
     if (threadIdx.x == 0) {
+        unsigned long long bt = 0;
+        double bp = 0.0;
+#pragma unroll
+        for (int k = 0; k < TPB / 32; ++k) {
+            bt += s_trials[k];
+            if (PLAQ) bp += (double)s_plaq[k];
+        }
+        if (PLAQ) ctx.plaq_partial[(size_t)(MU - 1) * ctx.phase_blocks + blockIdx.x] = bp;
         LatDesc* Dw = ctx.desc + l;
-        atomicAdd(&Dw->trials, (unsigned long long)bt);
-        atomicAdd(&Dw->updates, (unsigned long long)bu);
+        atomicAdd(&Dw->trials, bt);
+        if (blockIdx.x == blk0) atomicAdd(&Dw->updates, (unsigned long long)Vh);
         if (bc) {
             atomicAdd(&Dw->caps, (unsigned long long)bc);
             atomicOr(ctx.status, STATUS_CAP_HIT);
@@ -145,29 +172,56 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     }
 }
 
-// One block per lattice: finishes the sweep (fixed-order plaquette sum of
-// the three fused phases) and advances the lattice's sweep counter.
+// Finishes a sweep: the fixed-order sum of the fused plaquette partials and
+// the lattice's sweep counter.  Grid (chunks, lattices); each block sums
+// SWEEP_CHUNK partials of its lattice, the last block of a lattice to finish
+// (ticket counter) adds the chunk sums in chunk order.
 template <bool PLAQ>
 __global__ void __launch_bounds__(TPB) sweep_end_kernel(Ctx ctx)
 {
     __shared__ double sred[TPB / 32];
-    const int l = blockIdx.x;
+    __shared__ int s_last;
+    const int l = blockIdx.y;
     LatDesc* D = ctx.desc + l;
-    if (PLAQ) {
-        const uint32_t b0 = ctx.phase_start[l], b1 = ctx.phase_start[l + 1];
-        double acc = 0.0;
-        for (int slot = 0; slot < 3; ++slot)
-            for (uint32_t b = b0 + threadIdx.x; b < b1; b += TPB)
-                acc += ctx.plaq_partial[(size_t)slot * ctx.phase_blocks + b];
-        const double tot = block_sum<TPB>(acc, sred);
-        if (threadIdx.x == 0) {
-            const double P = tot / (6.0 * (double)D->V);
-            const uint64_t k = D->sweep - D->sweep_base;
-            ctx.ring[(size_t)l * PLAQ_RING + (k % PLAQ_RING)] = P;
-            if (D->plaq_out) D->plaq_out[k] = P;
-        }
+    if (!PLAQ) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) D->sweep += 1;
+        return;
     }
-    if (threadIdx.x == 0) D->sweep += 1;
+    const uint32_t b0 = ctx.phase_start[l];
+    const uint32_t nb = ctx.phase_start[l + 1] - b0;
+    const uint32_t total = 3 * nb;
+    const uint32_t nchunk = (total + SWEEP_CHUNK - 1) / SWEEP_CHUNK;
+    if (blockIdx.x >= nchunk) return;
+
+    const uint32_t e0 = blockIdx.x * SWEEP_CHUNK;
+    const uint32_t e1 = min(e0 + (uint32_t)SWEEP_CHUNK, total);
+    double acc = 0.0;
+    for (uint32_t e = e0 + threadIdx.x; e < e1; e += TPB) {
+        const uint32_t slot = (e >= nb) + (e >= 2 * nb);
+        acc += ctx.plaq_partial[(size_t)slot * ctx.phase_blocks + b0 + (e - slot * nb)];
+    }
+    const double part = block_sum<TPB>(acc, sred);
+    double* chunks = ctx.chunk_partial + (size_t)l * ctx.max_chunks;
+    if (threadIdx.x == 0) {
+        chunks[blockIdx.x] = part;
+        __threadfence();
+        const uint32_t ticket = atomicAdd(ctx.chunk_count + l, 1u);
+        s_last = ticket == nchunk - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double c = 0.0;
+    for (uint32_t k = threadIdx.x; k < nchunk; k += TPB) c += __ldcg(chunks + k);
+    const double tot = block_sum<TPB>(c, sred);
+    if (threadIdx.x == 0) {
+        ctx.chunk_count[l] = 0;
+        const double P = tot / (6.0 * (double)D->V);
+        const uint64_t k = D->sweep - D->sweep_base;
+        ctx.ring[(size_t)l * PLAQ_RING + (k % PLAQ_RING)] = P;
+        if (D->plaq_out) D->plaq_out[k] = P;
+        D->sweep += 1;
+    }
 }
 
 // Per-call parameters go in by value (no host-to-device copy); the
@@ -221,8 +275,8 @@ cudaError_t launch_phase(const Ctx& c, int dtype, int mu, int parity, bool plaq,
 
 cudaError_t launch_sweep_end(const Ctx& c, bool plaq, cudaStream_t s)
 {
-    if (plaq) sweep_end_kernel<true><<<c.n, TPB, 0, s>>>(c);
-    else sweep_end_kernel<false><<<c.n, TPB, 0, s>>>(c);
+    if (plaq) sweep_end_kernel<true><<<dim3(c.max_chunks, c.n), TPB, 0, s>>>(c);
+    else sweep_end_kernel<false><<<dim3(1, c.n), 32, 0, s>>>(c);
     return cudaGetLastError();
 }
 

@@ -78,7 +78,7 @@ __host__ __device__ __forceinline__ T qnorm2(const Quat<T>& p)
     return p.a0 * p.a0 + p.a1 * p.a1 + p.a2 * p.a2 + p.a3 * p.a3;
 }
 
-__device__ __forceinline__ float rsqrt_t(float x) { return 1.0f / sqrtf(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
 
 template <typename T>
@@ -122,10 +122,12 @@ struct Stream {
     }
 };
 
-// uniform in (0,1): ((w >> 9) + 0.5) 2^-23, exact in float and double
+// uniform in (0,1): ((w >> 9) + 0.5) 2^-23, exact in float and double.
+// FP32: the top 23 bits as the mantissa of a float in [1,2) give
+// 1 + k 2^-23; subtracting 1 - 2^-24 leaves (2k + 1) 2^-24 exactly.
 __device__ __forceinline__ float u01f(uint32_t w)
 {
-    return __fmul_rn(__uint2float_rn(w >> 9) + 0.5f, 1.1920928955078125e-7f);
+    return __int_as_float((int)((w >> 9) | 0x3F800000u)) - 0.99999994039535522f;
 }
 __device__ __forceinline__ double u01d(uint32_t w)
 {
@@ -192,14 +194,5 @@ __host__ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f)
 {
     return (umulhi32(n, f.m) + n) >> f.s;
 }
-
-// --------------------------------------------------------------------------
-// even/odd geometry of one lattice
-// --------------------------------------------------------------------------
-struct Site {
-    int c[4];      // x, y, z, t
-    uint32_t r;    // row = y + Ns (z + Ns t)
-    uint32_t lex;
-};
 
 }  // namespace su2

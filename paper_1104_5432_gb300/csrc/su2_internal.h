@@ -19,11 +19,19 @@
 
 namespace su2 {
 
-constexpr int TPB = 256;            // threads per block of every lattice kernel
+#ifndef SU2_TPB
+#define SU2_TPB 256
+#endif
+#ifndef SU2_HB_MIN_BLOCKS
+#define SU2_HB_MIN_BLOCKS 4
+#endif
+constexpr int TPB = SU2_TPB;        // threads per block of every lattice kernel
+constexpr int HB_MIN_BLOCKS = SU2_HB_MIN_BLOCKS;  // phase-kernel residency hint
 constexpr int KP_CAP = 4096;        // Kennedy-Pendleton trial cap
 constexpr int PLAQ_RING = 4096;     // per-lattice plaquette slots for host output
 constexpr size_t STAGE_BYTES = size_t(32) << 20;
 constexpr uint32_t STATUS_CAP_HIT = 1u;
+constexpr int SWEEP_CHUNK = TPB * 8;   // plaquette partials summed per sweep_end block
 
 // One per lattice, resident in the work buffer.  The first block is fixed
 // at bind time; the second is written by the parameter kernel at every
@@ -55,9 +63,12 @@ struct Ctx {
     double* obs_partial;           // [obs_rows][max(site, spat) blocks]
     double* field;                 // Polyakov fields
     double* ring;                  // [n][PLAQ_RING]
+    double* chunk_partial;         // [n][max_chunks] sweep_end chunk sums
+    uint32_t* chunk_count;         // [n] sweep_end tickets (zero between sweeps)
     uint32_t* status;
     int n;
     uint32_t phase_blocks, site_blocks, spat_blocks;
+    uint32_t max_chunks;
 };
 
 // lattice owning grid block b: largest l with start[l] <= b

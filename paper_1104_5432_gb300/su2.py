@@ -77,6 +77,7 @@ def load(build_if_needed: bool = True):
             "su2_last_error": (C.c_char_p, []),
             "su2_selftest_fastdiv": (u64, [C.c_uint32, C.c_uint32]),
             "su2_plaquette_static": (i, [P, i, i, i, P, P]),
+            "su2_selftest_math": (i, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

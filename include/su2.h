@@ -135,6 +135,19 @@ int su2_heatbath(su2_lattice* lat, double beta, int nsweeps, uint64_t seed, doub
 int su2_batch_heatbath(su2_lattice* lat, const double* betas, int nsweeps,
                        const uint64_t* seeds, double* plaq);
 
+/* As su2_batch_heatbath, and after EVERY sweep the Polyakov loop (Sec. 2.2,
+ * Eq. 1) and the Polyakov-loop correlator C(r), r = 0..rmax (Sec. 2.2,
+ * Eq. 3), of every lattice are measured and summed in FP64 over the call's
+ * sweeps: the finite-temperature scan of Sec. 2.2 (thermalise with
+ * su2_batch_heatbath, then measure with this call).
+ * poly_sum: host or device double[2n]: [0,n) sums of the signed spatial
+ *   means of L, [n,2n) sums of their moduli.
+ * corr_sum: host or device double[n][rmax+1]: sums of C(r).
+ * Divide by nsweeps for the ensemble averages.  rmax <= min(Ns/2, 128). */
+int su2_batch_heatbath_measure(su2_lattice* lat, const double* betas, int nsweeps,
+                               const uint64_t* seeds, double* plaq, int rmax, double* poly_sum,
+                               double* corr_sum);
+
 /* One checkerboard phase (mu in 0..3, parity 0/1) of every lattice at the
  * current sweep counter, which does NOT advance (the unit the sweep is
  * made of; for testing).  trials (nullable, device int32[V], n == 1
@@ -154,7 +167,8 @@ int su2_polyakov_loop(su2_lattice* lat, double* out_signed, double* out_abs);
 
 /* Polyakov-loop correlator (Sec. 2.2, Eq. 3; for SU(2) the traces are
  * real): C(r) = (1/(3 Ns^3)) sum_x sum_{i=x,y,z} L(x) L(x + r e_i),
- * r = 0..rmax, periodic, rmax <= Ns/2 of every lattice.  Measures L first.
+ * r = 0..rmax, periodic, rmax <= min(Ns/2, 128) over the lattices.
+ * Measures L first.
  * out: host or device double[n][rmax+1]; accumulate != 0 adds to out
  * (running sums over measured sweeps) instead of overwriting it. */
 int su2_polyakov_correlator(su2_lattice* lat, int rmax, double* out, int accumulate);

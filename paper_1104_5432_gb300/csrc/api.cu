@@ -73,7 +73,7 @@ struct su2_lattice {
     size_t link_bytes = 0, work_bytes = 0;
     size_t off_status = 0, off_desc = 0, off_pstart = 0, off_sstart = 0, off_spstart = 0;
     size_t off_plaq = 0, off_obs = 0, off_field = 0, off_ring = 0, off_res = 0, off_stage = 0;
-    size_t off_chunks = 0, off_tickets = 0;
+    size_t off_chunks = 0, off_tickets = 0, off_acc = 0;
     uint32_t max_chunks = 1;
     size_t res_doubles = 0;
     // bound state
@@ -83,6 +83,8 @@ struct su2_lattice {
     cudaStream_t stream = 0;
     cudaStream_t capture = nullptr;
     cudaGraphExec_t sweep_graph[2] = {nullptr, nullptr};
+    int measure_rmax = -1;                  // rmax baked into measure_graph
+    cudaGraphExec_t measure_graph[2] = {nullptr, nullptr};
     Ctx ctx{};
 
     bool bound() const { return links != nullptr && work != nullptr; }
@@ -95,13 +97,17 @@ struct su2_lattice {
     double* ring_dev() const { return reinterpret_cast<double*>(work + off_ring); }
     double* stage_dev() const { return reinterpret_cast<double*>(work + off_stage); }
 
+    double* acc_dev() const { return reinterpret_cast<double*>(work + off_acc); }
+
     void drop_graphs()
     {
-        for (auto& g : sweep_graph)
-            if (g) {
-                cudaGraphExecDestroy(g);
-                g = nullptr;
-            }
+        for (auto* gs : {sweep_graph, measure_graph})
+            for (int k = 0; k < 2; ++k)
+                if (gs[k]) {
+                    cudaGraphExecDestroy(gs[k]);
+                    gs[k] = nullptr;
+                }
+        measure_rmax = -1;
     }
 };
 
@@ -160,7 +166,7 @@ int layout(su2_lattice* L)
     }
     L->site_blocks = L->site_start[n];
     L->spat_blocks = L->spat_start[n];
-    L->rmax_limit = rlim;
+    L->rmax_limit = std::min(rlim, MAX_RMAX);
     L->link_bytes = lb;
 
     size_t w = 0;
@@ -176,13 +182,14 @@ int layout(su2_lattice* L)
     L->off_spstart = take(4 * (n + 1));
     L->off_plaq = take(8 * 3 * (size_t)L->phase_blocks);
     const size_t obs_rows = std::max<size_t>(L->site_blocks,
-                                             (size_t)L->spat_blocks * (size_t)(rlim + 1));
+                                             (size_t)L->spat_blocks * (size_t)(L->rmax_limit + 1));
     L->off_obs = take(8 * obs_rows);
     L->off_field = take(8 * fo);
     L->off_ring = take(8 * (size_t)PLAQ_RING * n);
     L->off_chunks = take(8 * (size_t)L->max_chunks * n);
     L->off_tickets = take(4 * (size_t)n);
-    L->res_doubles = (size_t)n * (rlim + 1) + 2 * (size_t)n;
+    L->res_doubles = (size_t)n * (L->rmax_limit + 1) + 2 * (size_t)n;
+    L->off_acc = take(8 * L->res_doubles);
     L->off_res = take(8 * L->res_doubles);
     L->off_stage = take(STAGE_BYTES);
     L->work_bytes = w;
@@ -234,22 +241,37 @@ int set_params(su2_lattice* L, const double* betas, double beta, const uint64_t*
     return SU2_OK;
 }
 
-int record_sweep(su2_lattice* L, bool plaq, cudaStream_t s)
+// one sweep: 8 phases + sweep end; with rmax >= 0 also the Polyakov loop
+// and the correlator, added into the handle's accumulators
+int record_sweep(su2_lattice* L, bool plaq, int rmax, cudaStream_t s)
 {
     for (int mu = 0; mu < 4; ++mu)
         for (int p = 0; p < 2; ++p) SU2_CUDA(launch_phase(L->ctx, L->dtype, mu, p, plaq, nullptr, s));
     SU2_CUDA(launch_sweep_end(L->ctx, plaq, s));
+    if (rmax >= 0) {
+        double* acc = L->acc_dev();
+        SU2_CUDA(launch_polyakov(L->ctx, L->dtype, acc, acc + L->n, 1, s));
+        SU2_CUDA(launch_correlator(L->ctx, L->dtype, rmax, acc + 2 * L->n, 1, s));
+    }
     return SU2_OK;
 }
 
-// one sweep as a graph of 9 kernels, built once per handle and binding
-int sweep_graph(su2_lattice* L, bool plaq, cudaGraphExec_t* exec)
+// one sweep as a graph of kernels, built once per handle, binding and rmax
+int sweep_graph(su2_lattice* L, bool plaq, int rmax, cudaGraphExec_t* exec)
 {
-    cudaGraphExec_t& g = L->sweep_graph[plaq ? 1 : 0];
+    if (rmax >= 0 && rmax != L->measure_rmax) {
+        for (auto& gm : L->measure_graph)
+            if (gm) {
+                cudaGraphExecDestroy(gm);
+                gm = nullptr;
+            }
+        L->measure_rmax = rmax;
+    }
+    cudaGraphExec_t& g = rmax >= 0 ? L->measure_graph[plaq ? 1 : 0] : L->sweep_graph[plaq ? 1 : 0];
     if (!g) {
         if (!L->capture) SU2_CUDA(cudaStreamCreateWithFlags(&L->capture, cudaStreamNonBlocking));
         SU2_CUDA(cudaStreamBeginCapture(L->capture, cudaStreamCaptureModeThreadLocal));
-        const int rc = record_sweep(L, plaq, L->capture);
+        const int rc = record_sweep(L, plaq, rmax, L->capture);
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(L->capture, &graph);
         if (rc != SU2_OK) {
@@ -283,10 +305,16 @@ int sync_status(su2_lattice* L)
 }
 
 int heatbath_impl(su2_lattice* L, const double* betas, double beta, int nsweeps,
-                  const uint64_t* seeds, uint64_t seed, double* plaq)
+                  const uint64_t* seeds, uint64_t seed, double* plaq, int rmax = -1,
+                  double* poly_sum = nullptr, double* corr_sum = nullptr)
 {
     if (int rc = check_handle(L)) return rc;
     if (nsweeps < 0) return fail(SU2_E_INVAL, "nsweeps < 0");
+    if (rmax >= 0) {
+        if (rmax > L->rmax_limit)
+            return fail(SU2_E_INVAL, "rmax %d outside 0..%d", rmax, L->rmax_limit);
+        if (!poly_sum || !corr_sum) return fail(SU2_E_INVAL, "null measurement output");
+    }
     for (int l = 0; l < L->n; ++l) {
         const double b = betas ? betas[l] : beta;
         if (!(b >= 0.0) || !std::isfinite(b)) return fail(SU2_E_INVAL, "beta must be finite and >= 0");
@@ -295,7 +323,10 @@ int heatbath_impl(su2_lattice* L, const double* betas, double beta, int nsweeps,
     const bool want = plaq != nullptr;
     const bool dev_out = want && is_device_ptr(plaq);
     cudaGraphExec_t g = nullptr;
-    if (int rc = sweep_graph(L, want, &g)) return rc;
+    if (int rc = sweep_graph(L, want, rmax, &g)) return rc;
+    const size_t acc_count = rmax >= 0 ? 2 * (size_t)L->n + (size_t)L->n * (rmax + 1) : 0;
+    if (rmax >= 0)
+        SU2_CUDA(cudaMemsetAsync(L->acc_dev(), 0, sizeof(double) * acc_count, L->stream));
     int done = 0;
     while (done < nsweeps) {
         const int chunk = (want && !dev_out) ? std::min(PLAQ_RING, nsweeps - done) : nsweeps;
@@ -309,6 +340,18 @@ int heatbath_impl(su2_lattice* L, const double* betas, double beta, int nsweeps,
                                          sizeof(double) * chunk, cudaMemcpyDeviceToHost, L->stream));
         }
         done += chunk;
+    }
+    if (rmax >= 0) {
+        const bool pdev = is_device_ptr(poly_sum), cdev = is_device_ptr(corr_sum);
+        const double* acc = L->acc_dev();
+        SU2_CUDA(cudaMemcpyAsync(poly_sum, acc, sizeof(double) * 2 * L->n,
+                                 pdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 L->stream));
+        SU2_CUDA(cudaMemcpyAsync(corr_sum, acc + 2 * L->n,
+                                 sizeof(double) * (size_t)L->n * (rmax + 1),
+                                 cdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 L->stream));
+        if (!pdev || !cdev) return sync_status(L);
     }
     if (want && !dev_out) return sync_status(L);
     SU2_CUDA(cudaGetLastError());
@@ -486,6 +529,15 @@ int su2_batch_heatbath(su2_lattice* lat, const double* betas, int nsweeps, const
     return heatbath_impl(lat, betas, 0.0, nsweeps, seeds, 0, plaq);
 }
 
+int su2_batch_heatbath_measure(su2_lattice* lat, const double* betas, int nsweeps,
+                               const uint64_t* seeds, double* plaq, int rmax, double* poly_sum,
+                               double* corr_sum)
+{
+    if (!betas || !seeds) return fail(SU2_E_INVAL, "null betas or seeds");
+    if (rmax < 0) return fail(SU2_E_INVAL, "rmax < 0");
+    return heatbath_impl(lat, betas, 0.0, nsweeps, seeds, 0, plaq, rmax, poly_sum, corr_sum);
+}
+
 int su2_heatbath_phase(su2_lattice* lat, double beta, int mu, int parity, uint64_t seed,
                        int32_t* trials)
 {
@@ -523,7 +575,7 @@ int su2_polyakov_loop(su2_lattice* lat, double* out_signed, double* out_abs)
         return fail(SU2_E_INVAL, "out_signed and out_abs must both be host or both device");
     double* ts = dev ? out_signed : lat->res_dev();
     double* ta = out_abs ? (dev ? out_abs : lat->res_dev() + lat->n) : nullptr;
-    SU2_CUDA(launch_polyakov(lat->ctx, lat->dtype, ts, ta, lat->stream));
+    SU2_CUDA(launch_polyakov(lat->ctx, lat->dtype, ts, ta, 0, lat->stream));
     if (!dev) {
         SU2_CUDA(cudaMemcpyAsync(out_signed, ts, sizeof(double) * lat->n, cudaMemcpyDeviceToHost,
                                  lat->stream));
@@ -546,11 +598,11 @@ int su2_polyakov_correlator(su2_lattice* lat, int rmax, double* out, int accumul
     const size_t cnt = (size_t)lat->n * (rmax + 1);
     double* scratch = lat->res_dev();  // [2n] Polyakov means, then correlator rows
     double* tgt = dev ? out : scratch + 2 * lat->n;
-    SU2_CUDA(launch_polyakov(lat->ctx, lat->dtype, scratch, scratch + lat->n, lat->stream));
+    SU2_CUDA(launch_polyakov(lat->ctx, lat->dtype, scratch, scratch + lat->n, 0, lat->stream));
     if (!dev && accumulate)
         SU2_CUDA(cudaMemcpyAsync(tgt, out, sizeof(double) * cnt, cudaMemcpyHostToDevice,
                                  lat->stream));
-    SU2_CUDA(launch_correlator(lat->ctx, rmax, tgt, accumulate, lat->stream));
+    SU2_CUDA(launch_correlator(lat->ctx, lat->dtype, rmax, tgt, accumulate, lat->stream));
     if (!dev) return finish_output(lat, out, tgt, cnt);
     return SU2_OK;
 }

@@ -5,8 +5,9 @@
 //   C(r) = <L(x) L(x + r e_i)> over x and the three spatial axes
 //   (Sec. 2.2, Eq. 3: for SU(2) the traces are real, so 1/4 Tr L Tr L^+ is
 //   the product of the normalised loops).
-// Products are taken in the link precision, every sum in FP64 and in a
-// fixed order: per-block partials, then one block per (lattice, row).
+// Products and warp partial sums are taken in the link precision; block,
+// lattice and over-sweep sums in FP64, each in a fixed order (per-block
+// partials, then one block per (lattice, row)).
 #include "su2_internal.h"
 #include "su2_links.cuh"
 #include "su2_reduce.cuh"
@@ -14,9 +15,33 @@
 namespace su2 {
 
 template <typename T>
+__device__ __forceinline__ T warp_total(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block total of one value per thread: warp sums in T, block sum in FP64
+// (valid in thread 0)
+template <typename T>
+__device__ __forceinline__ double block_total(T v, T* s_warp)
+{
+    v = warp_total(v);
+    if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 0; w < TPB / 32; ++w) s += (double)s_warp[w];
+    }
+    return s;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(TPB) plaquette_kernel(Ctx ctx)
 {
-    __shared__ double sred[TPB / 32];
+    __shared__ T s_warp[TPB / 32];
     const int l = lattice_of_block(ctx.site_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
     const uint32_t lex = (blockIdx.x - __ldg(ctx.site_start + l)) * TPB + threadIdx.x;
@@ -40,18 +65,20 @@ __global__ void __launch_bounds__(TPB) plaquette_kernel(Ctx ctx)
             }
         }
     }
-    const double b = block_sum<TPB>((double)acc, sred);
+    const double b = block_total(acc, s_warp);
     if (threadIdx.x == 0) ctx.obs_partial[blockIdx.x] = b;
 }
 
+// L(x) for every spatial site into the field (link precision) and the
+// per-block partial sums of L
 template <typename T>
 __global__ void __launch_bounds__(TPB) polyakov_kernel(Ctx ctx)
 {
-    __shared__ double sred[TPB / 32];
+    __shared__ T s_warp[TPB / 32];
     const int l = lattice_of_block(ctx.spat_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
     const uint32_t sidx = (blockIdx.x - __ldg(ctx.spat_start + l)) * TPB + threadIdx.x;
-    double L = 0.0;
+    T L = T(0);
     if (sidx < (uint32_t)D.Vs) {
         const Links<T> U(ctx.links, D);
         const uint32_t r = fdiv(sidx, D.div_ns);
@@ -64,25 +91,26 @@ __global__ void __launch_bounds__(TPB) polyakov_kernel(Ctx ctx)
             const int p = (int)((x + y + z + (uint32_t)t) & 1u);
             P = qmul(P, U.load(3, p, lex >> 1));
         }
-        L = (double)P.a0;
-        ctx.field[D.field_off + sidx] = L;
+        L = P.a0;
+        reinterpret_cast<T*>(ctx.field)[D.field_off + sidx] = L;
     }
-    const double b = block_sum<TPB>(L, sred);
+    const double b = block_total(L, s_warp);
     if (threadIdx.x == 0) ctx.obs_partial[blockIdx.x] = b;
 }
 
 // rows r = 0..rmax of partials, from the Polyakov field of the last
-// polyakov_kernel launch
+// polyakov_kernel launch; one barrier for all rows
+template <typename T>
 __global__ void __launch_bounds__(TPB) correlator_kernel(Ctx ctx, int rmax)
 {
-    __shared__ double sred[TPB / 32];
+    __shared__ T s_rows[MAX_RMAX + 1][TPB / 32];
     const int l = lattice_of_block(ctx.spat_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
     const uint32_t sidx = (blockIdx.x - __ldg(ctx.spat_start + l)) * TPB + threadIdx.x;
     const bool act = sidx < (uint32_t)D.Vs;
-    const double* F = ctx.field + D.field_off;
+    const T* F = reinterpret_cast<const T*>(ctx.field) + D.field_off;
     uint32_t x = 0, y = 0, z = 0;
-    double L0 = 0.0;
+    T L0 = T(0);
     const uint32_t Ns = (uint32_t)D.Ns;
     if (act) {
         const uint32_t r = fdiv(sidx, D.div_ns);
@@ -91,15 +119,26 @@ __global__ void __launch_bounds__(TPB) correlator_kernel(Ctx ctx, int rmax)
         y = r - z * Ns;
         L0 = F[sidx];
     }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t xr = x, yr = y, zr = z;
     for (int r = 0; r <= rmax; ++r) {
-        double v = 0.0;
+        T v = T(0);
         if (act) {
-            const uint32_t xr = (x + r) % Ns, yr = (y + r) % Ns, zr = (z + r) % Ns;
             v = L0 * (F[xr + Ns * (y + Ns * z)] + F[x + Ns * (yr + Ns * z)]
                       + F[x + Ns * (y + Ns * zr)]);
         }
-        const double b = block_sum<TPB>(v, sred);
-        if (threadIdx.x == 0) ctx.obs_partial[(size_t)r * ctx.spat_blocks + blockIdx.x] = b;
+        v = warp_total(v);
+        if (lane == 0) s_rows[r][w] = v;
+        xr = xr + 1 == Ns ? 0 : xr + 1;
+        yr = yr + 1 == Ns ? 0 : yr + 1;
+        zr = zr + 1 == Ns ? 0 : zr + 1;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x <= rmax) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < TPB / 32; ++k) s += (double)s_rows[threadIdx.x][k];
+        ctx.obs_partial[(size_t)threadIdx.x * ctx.spat_blocks + blockIdx.x] = s;
     }
 }
 
@@ -142,19 +181,20 @@ cudaError_t launch_plaquette(const Ctx& c, int dtype, double* out_dev, cudaStrea
 }
 
 cudaError_t launch_polyakov(const Ctx& c, int dtype, double* out_signed_dev, double* out_abs_dev,
-                            cudaStream_t s)
+                            int accumulate, cudaStream_t s)
 {
     if (dtype == 0) polyakov_kernel<float><<<c.spat_blocks, TPB, 0, s>>>(c);
     else polyakov_kernel<double><<<c.spat_blocks, TPB, 0, s>>>(c);
     finalize_kernel<<<dim3(c.n, 1), TPB, 0, s>>>(c, c.spat_start, c.spat_blocks, 1, 1,
-                                                 out_signed_dev, out_abs_dev, 0);
+                                                 out_signed_dev, out_abs_dev, accumulate);
     return cudaGetLastError();
 }
 
-cudaError_t launch_correlator(const Ctx& c, int rmax, double* out_dev, int accumulate,
+cudaError_t launch_correlator(const Ctx& c, int dtype, int rmax, double* out_dev, int accumulate,
                               cudaStream_t s)
 {
-    correlator_kernel<<<c.spat_blocks, TPB, 0, s>>>(c, rmax);
+    if (dtype == 0) correlator_kernel<float><<<c.spat_blocks, TPB, 0, s>>>(c, rmax);
+    else correlator_kernel<double><<<c.spat_blocks, TPB, 0, s>>>(c, rmax);
     finalize_kernel<<<dim3(c.n, rmax + 1), TPB, 0, s>>>(c, c.spat_start, c.spat_blocks, rmax + 1,
                                                         2, out_dev, nullptr, accumulate);
     return cudaGetLastError();

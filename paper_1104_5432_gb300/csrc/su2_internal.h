@@ -32,6 +32,7 @@ constexpr int PLAQ_RING = 4096;     // per-lattice plaquette slots for host outp
 constexpr size_t STAGE_BYTES = size_t(32) << 20;
 constexpr uint32_t STATUS_CAP_HIT = 1u;
 constexpr int SWEEP_CHUNK = TPB * 8;   // plaquette partials summed per sweep_end block
+constexpr int MAX_RMAX = 128;          // largest correlator separation
 
 // One per lattice, resident in the work buffer.  The first block is fixed
 // at bind time; the second is written by the parameter kernel at every
@@ -104,8 +105,8 @@ cudaError_t launch_links_from_canonical(const Ctx& c, int dtype, int l, uint32_t
 cudaError_t launch_gauge(const Ctx& c, int dtype, int l, uint32_t V, uint64_t seed, cudaStream_t s);
 cudaError_t launch_plaquette(const Ctx& c, int dtype, double* out_dev, cudaStream_t s);
 cudaError_t launch_polyakov(const Ctx& c, int dtype, double* out_signed_dev,
-                            double* out_abs_dev, cudaStream_t s);
-cudaError_t launch_correlator(const Ctx& c, int rmax, double* out_dev, int accumulate,
+                            double* out_abs_dev, int accumulate, cudaStream_t s);
+cudaError_t launch_correlator(const Ctx& c, int dtype, int rmax, double* out_dev, int accumulate,
                               cudaStream_t s);
 
 // sets the message returned by su2_last_error() for the calling thread

@@ -64,6 +64,7 @@ def load(build_if_needed: bool = True):
             "su2_heatbath": (i, [P, d, i, u64, P]),
             "su2_batch_heatbath": (i, [P, P, i, P, P]),
             "su2_heatbath_phase": (i, [P, d, i, i, u64, P]),
+            "su2_batch_heatbath_measure": (i, [P, P, i, P, P, i, P, P]),
             "su2_plaquette": (i, [P, P]),
             "su2_polyakov_loop": (i, [P, P, P]),
             "su2_polyakov_correlator": (i, [P, i, P, i]),
@@ -198,6 +199,25 @@ class Lattice:
         _check(load().su2_batch_heatbath(self._h, b.ctypes.data, int(nsweeps), s.ctypes.data,
                                          _ptr(out)))
         return out
+
+    def batch_heatbath_measure(self, betas: Sequence[float], nsweeps: int, seeds: Sequence[int],
+                               rmax: int, plaq=True, poly_sum=None, corr_sum=None):
+        """Sweeps with the Polyakov loop and correlator measured after each;
+        returns (plaq [n, nsweeps] or the given buffer, poly_sum [2, n],
+        corr_sum [n, rmax+1]) -- sums over the call's sweeps."""
+        b = np.ascontiguousarray(np.asarray(betas, np.float64))
+        s = _u64_array(seeds)
+        out = None
+        if plaq is True:
+            out = np.zeros((self.n, nsweeps), np.float64)
+        elif plaq is not None and plaq is not False:
+            out = plaq
+        ps = np.zeros((2, self.n), np.float64) if poly_sum is None else poly_sum
+        cs = np.zeros((self.n, rmax + 1), np.float64) if corr_sum is None else corr_sum
+        _check(load().su2_batch_heatbath_measure(self._h, b.ctypes.data, int(nsweeps),
+                                                 s.ctypes.data, _ptr(out), int(rmax), _ptr(ps),
+                                                 _ptr(cs)))
+        return out, ps, cs
 
     def heatbath_phase(self, beta: float, mu: int, parity: int, seed: int, trials=None):
         _check(load().su2_heatbath_phase(self._h, float(beta), int(mu), int(parity),

@@ -1,0 +1,126 @@
+"""Physics and statistics of the CUDA path.
+
+* The fused per-sweep Polyakov loop / correlator measurement (the
+  finite-temperature scan of Sec. 2.2) equals the stand-alone measurements
+  after each sweep, and the FP64 oracle's chain.
+* Long runs: GPU FP64, GPU FP32 and the oracle give ensemble means of the
+  plaquette that agree within 3 sigma (binned jackknife), on the 8^4,
+  beta = 2.3 workload of the paper's benchmark shape.
+* Strong coupling <P>(beta = 0.5) = I2(beta)/I1(beta) and weak coupling
+  beta (1 - <P>) -> 3/4, through the GPU path in both precisions.
+"""
+import numpy as np
+import pytest
+from scipy import special
+
+from oracle import oracle as O
+from paper_1104_5432_gb300 import su2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def jackknife_mean(x, bin_size):
+    """Mean and binned-jackknife error of a Monte Carlo series."""
+    nb = len(x) // bin_size
+    b = np.asarray(x[:nb * bin_size]).reshape(nb, bin_size).mean(1)
+    tot = b.sum()
+    jk = (tot - b) / (nb - 1)
+    err = np.sqrt((nb - 1) / nb * np.sum((jk - jk.mean()) ** 2))
+    return b.mean(), err
+
+
+@pytest.mark.parametrize("dtype,tol", [(su2.F64, 1e-12), (su2.F32, 1e-6)])
+def test_fused_measurement_equals_per_sweep(dtype, tol):
+    shapes = [(4, 4), (6, 4), (8, 2)]
+    betas = [2.2, 2.3, 2.4]
+    seeds = [11, 12, 13]
+    rmax = 2
+    nsw = 3
+    B = su2.Lattice([s[0] for s in shapes], [s[1] for s in shapes], dtype)
+    B.batch_init(su2.HOT, seeds)
+    plaq, ps, cs = B.batch_heatbath_measure(betas, nsw, seeds, rmax)
+    ref = su2.Lattice([s[0] for s in shapes], [s[1] for s in shapes], dtype)
+    ref.batch_init(su2.HOT, seeds)
+    ps_r = np.zeros((2, 3))
+    cs_r = np.zeros((3, rmax + 1))
+    for k in range(nsw):
+        pk = ref.batch_heatbath(betas, 1, seeds)
+        np.testing.assert_array_equal(pk[:, 0], plaq[:, k])
+        s, a = ref.polyakov_loop()
+        ps_r[0] += s
+        ps_r[1] += a
+        cs_r += ref.polyakov_correlator(rmax)
+    np.testing.assert_allclose(ps, ps_r, rtol=0, atol=tol * nsw)
+    np.testing.assert_allclose(cs, cs_r, rtol=0, atol=tol * nsw)
+    if dtype == su2.F64:
+        # and the oracle's own chain, measured after every sweep
+        for l, (Ns, Nt) in enumerate(shapes):
+            links = O.init(Ns, Nt, True, seeds[l])
+            so = ao = 0.0
+            co = np.zeros(rmax + 1)
+            for k in range(nsw):
+                links, _, _ = O.heatbath(Ns, Nt, links, betas[l], 1, seeds[l], sweep0=k)
+                m, a, _ = O.polyakov(Ns, Nt, links)
+                so += m
+                ao += a
+                co += O.correlator(Ns, Nt, links, rmax)
+            assert abs(ps[0, l] - so) <= 1e-11 and abs(ps[1, l] - ao) <= 1e-11
+            np.testing.assert_allclose(cs[l], co, rtol=0, atol=1e-11)
+    # device accumulators
+    dps = torch.zeros(6, dtype=torch.float64, device="cuda")
+    dcs = torch.zeros(3 * (rmax + 1), dtype=torch.float64, device="cuda")
+    B.batch_heatbath_measure(betas, 2, seeds, rmax, plaq=None, poly_sum=dps, corr_sum=dcs)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(dps.cpu().numpy())) and dcs.cpu().numpy()[0] > 0
+    with pytest.raises(su2.SU2Error):
+        B.batch_heatbath_measure(betas, 1, seeds, 3)  # rmax beyond Ns/2 of a 4^4 lattice
+
+
+def test_long_run_ensembles_agree():
+    """8^4, beta = 2.3, hot start: GPU FP64, GPU FP32 and the CPU oracle
+    (independent seeds) agree on <P> within 3 sigma (binned jackknife)."""
+    Ns = Nt = 8
+    beta, therm = 2.3, 100
+    series = {}
+    for name, dtype, seed, n in (("gpu_f64", su2.F64, 21, 3000), ("gpu_f32", su2.F32, 22, 3000)):
+        lat = su2.Lattice(Ns, Nt, dtype)
+        lat.init(su2.HOT, seed)
+        series[name] = lat.heatbath(beta, therm + n, seed)[0][therm:]
+    links = O.init(Ns, Nt, True, 23)
+    series["oracle"] = O.heatbath(Ns, Nt, links, beta, therm + 700, 23)[1][therm:]
+    stats = {k: jackknife_mean(v, 20) for k, v in series.items()}
+    names = list(stats)
+    for i in range(3):
+        for j in range(i + 1, 3):
+            (m1, e1), (m2, e2) = stats[names[i]], stats[names[j]]
+            assert abs(m1 - m2) < 3 * np.hypot(e1, e2), (names[i], names[j], stats)
+    for m, e in stats.values():
+        assert 0.55 < m < 0.65 and e < 2e-3
+
+
+@pytest.mark.parametrize("dtype", [su2.F32, su2.F64])
+def test_strong_coupling_gpu(dtype):
+    lat = su2.Lattice(12, 12, dtype)
+    lat.init(su2.HOT, 5)
+    p = lat.heatbath(0.5, 420, 5)[0][20:]
+    m, e = jackknife_mean(p, 20)
+    u = special.ive(2, 0.5) / special.ive(1, 0.5)
+    assert abs(m - u) < 3 * e + 2e-4, (m, u, e)
+
+
+@pytest.mark.parametrize("dtype", [su2.F32, su2.F64])
+def test_weak_coupling_gpu(dtype):
+    xs, ys, ws = [], [], []
+    for beta in (10.0, 20.0, 40.0):
+        lat = su2.Lattice(8, 8, dtype)
+        lat.init(su2.COLD, 0)
+        p = lat.heatbath(beta, 600, int(beta))[0][100:]
+        m, e = jackknife_mean(p, 25)
+        xs.append(1 / beta)
+        ys.append(beta * (1 - m))
+        ws.append(1 / (beta * e) ** 2)
+    A = np.vstack([np.ones(3), xs]).T
+    W = np.diag(ws)
+    coef = np.linalg.solve(A.T @ W @ A, A.T @ W @ np.array(ys))
+    assert abs(coef[0] - 0.75) < 0.02, coef

@@ -143,7 +143,7 @@ def gpu_arm(args, rank, world, local):
     import torch
     import torch.distributed as dist
 
-    from paper_1104_5432_gb300 import inputs, su2
+    from paper_1104_5432_gb300 import inputs, shard, su2
 
     torch.cuda.set_device(local)
     w = WORKLOAD
@@ -297,7 +297,10 @@ def gpu_arm(args, rank, world, local):
         B.close()
         torch.cuda.empty_cache()
         # ---- FP32 finite-temperature scan (Sec. 2.2) ------------------------------
-        scan = inputs.temperature_scan(21, 48, 4)
+        full_scan = inputs.temperature_scan(21, 48, 4)
+        # independent lattices: each rank takes its share, no exchange
+        share = shard.partition([e["Ns"] ** 3 * e["Nt"] for e in full_scan], world)[rank]
+        scan = [full_scan[i] for i in share] or full_scan[:1]
         S = su2.Lattice([e["Ns"] for e in scan], [e["Nt"] for e in scan], su2.F32)
         sb = [e["beta"] for e in scan]
         ss = [e["seed"] + 1000003 * rank for e in scan]
@@ -305,7 +308,7 @@ def gpu_arm(args, rank, world, local):
         pls = torch.zeros(len(scan) * n_meas, dtype=torch.float64, device="cuda")
         ps_dev = torch.zeros(2 * len(scan), dtype=torch.float64, device="cuda")
         cs_dev = torch.zeros(len(scan) * (rmax + 1), dtype=torch.float64, device="cuda")
-        Vs_tot = sum(e["Ns"] ** 3 * e["Nt"] for e in scan)
+        Vs_tot = sum(e["Ns"] ** 3 * e["Nt"] for e in full_scan)
 
         def step_scan():
             S.batch_init(su2.HOT, ss)
@@ -317,14 +320,15 @@ def gpu_arm(args, rank, world, local):
         S.sync()
         absL = (ps_dev.cpu().numpy()[len(scan):] / n_meas).tolist()
         arms["fp32_temperature_scan"] = {
-            "value": world * 4 * Vs_tot * (n_therm + n_meas) / tsc, "unit": UNIT,
+            "value": 4 * Vs_tot * (n_therm + n_meas) / tsc, "unit": UNIT,
             "workload": "21 lattices 48^3x4, beta = 2.20..2.40 step 0.01, hot start, "
                         f"{n_therm} + {n_meas} sweeps (the scan's 500 + 2000 reduced 10x), "
                         "Polyakov loop and correlator r = 0..24 measured after every measured "
                         "sweep and summed in FP64, FP32 links",
             "ms_per_sweep": tsc / (n_therm + n_meas) * 1e3,
             "mean_abs_polyakov_short_run": {f"{b:.2f}": round(a, 4) for b, a in zip(sb, absL)
-                                  if round(b * 100) % 5 == 0}}
+                                            if round(b * 100) % 5 == 0},
+            "lattices_per_rank": len(share)}
         S.close()
         torch.cuda.empty_cache()
         if "fp64_plain" in arms:

@@ -124,3 +124,20 @@ def test_weak_coupling_gpu(dtype):
     W = np.diag(ws)
     coef = np.linalg.solve(A.T @ W @ A, A.T @ W @ np.array(ys))
     assert abs(coef[0] - 0.75) < 0.02, coef
+
+
+def test_scan_worker_single_process():
+    """The scan worker used for sharded runs (here without a process group:
+    every item runs locally) returns per-lattice averages consistent with a
+    direct batched measurement."""
+    from paper_1104_5432_gb300 import shard
+    items = [dict(Ns=4, Nt=4, beta=2.2, seed=31), dict(Ns=6, Nt=2, beta=2.5, seed=32)]
+    res = shard.sharded_run(items, [256, 432], shard.gpu_scan_worker(2, 3, 2, su2.F64))
+    B = su2.Lattice([4, 6], [4, 2], su2.F64)
+    B.batch_init(su2.HOT, [31, 32])
+    B.batch_heatbath([2.2, 2.5], 2, [31, 32], plaq=None)
+    plaq, ps, cs = B.batch_heatbath_measure([2.2, 2.5], 3, [31, 32], 2)
+    for l, r in enumerate(res):
+        assert r["plaquette"] == plaq[l].mean()
+        assert r["abs_polyakov"] == ps[1, l] / 3
+        np.testing.assert_array_equal(r["correlator"], cs[l] / 3)

@@ -183,6 +183,7 @@ def gpu_arm(args, rank, world, local):
 
     # ---- main arm: FP32, inputs resident in HBM --------------------------------
     lat = su2.Lattice(Ns, Nt, su2.F32)
+    tuned = {"fp32": lat.autotune()}  # launch shape chosen by measurement
     plaq_dev = torch.zeros(sweeps, dtype=torch.float64, device="cuda")
 
     def step_f32():
@@ -257,6 +258,7 @@ def gpu_arm(args, rank, world, local):
     if not args.no_arms:
         # ---- FP64 plain: same lattice, FP64 throughout ---------------------------
         lat64 = su2.Lattice(Ns, Nt, su2.F64)
+        tuned["fp64"] = lat64.autotune()
         sw64 = 10
         pl64 = torch.zeros(sw64, dtype=torch.float64, device="cuda")
 
@@ -276,6 +278,7 @@ def gpu_arm(args, rank, world, local):
         # ---- FP32 batched ensemble -------------------------------------------------
         ens = inputs.batched_ensemble(64, 5)
         B = su2.Lattice([e["Ns"] for e in ens], [e["Nt"] for e in ens], su2.F32)
+        tuned["fp32_batched"] = B.autotune()
         betas = [e["beta"] for e in ens]
         seeds = [e["seed"] + 1000003 * rank for e in ens]
         swb = 200
@@ -334,7 +337,9 @@ def gpu_arm(args, rank, world, local):
         if "fp64_plain" in arms:
             arms["fp32_over_fp64_plain"] = value / arms["fp64_plain"]["value"]
 
+    from paper_1104_5432_gb300.csrc_info import launch_shapes
     return dict(t_main=t_main, value=value, clocks=clocks, roofline=roofline, e2e=e2e,
+                tuned={k: launch_shapes(k.startswith("fp64"))[v] for k, v in tuned.items()},
                 arms=arms, launches=launches_per_step * args.steps, step_gbs=step_gbs,
                 phase_s=phase_s)
 
@@ -435,7 +440,8 @@ def main():
                            "parallelism": f"{world} independent lattice(s), one per GPU"},
                 "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
                 "gpu_launches": r["launches"], "clocks": r["clocks"],
-                "step_effective_gbs": round(r["step_gbs"], 1), "arms": r["arms"]}
+                "step_effective_gbs": round(r["step_gbs"], 1), "arms": r["arms"],
+                "launch_shapes": r["tuned"]}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -197,6 +197,39 @@ int su2_stats(su2_lattice* lat, int l, uint64_t out[3]);
 int su2_get_sweep(su2_lattice* lat, int l, uint64_t* sweep);
 int su2_set_sweep(su2_lattice* lat, int l, uint64_t sweep);
 
+/* ------------------------------------------------------------------ */
+/* launch-shape autotuning                                             */
+/* ------------------------------------------------------------------ */
+
+/* Number of launch shapes (threads per block, minimum resident blocks per
+ * SM) compiled for the phase kernel; shape 0 is the default.  Results never
+ * depend on the shape (the random streams are keyed by link and sweep). */
+#define SU2_NUM_LAUNCH_CONFIGS 4
+
+/* Times every launch shape on this handle's lattices (whole sweeps with the
+ * fused plaquette, replayed as in su2_heatbath, ~20 ms per shape in each of
+ * three interleaved rounds, best round kept) and keeps the fastest.
+ * OVERWRITES the links: on return every lattice holds the hot start of
+ * su2_init(SU2_HOT, 0x5EED) with zeroed counters; call it before su2_init
+ * or su2_set_links.  If the environment variable SU2_AUTOTUNE_CACHE names
+ * a file, the choice is appended there under a key made of the GPU name,
+ * the precision and the lattice shapes, and su2_bind_memory of any later
+ * handle with the same key starts with the cached shape.
+ * chosen (nullable): the index picked.  Synchronous. */
+int su2_autotune(su2_lattice* lat, int* chosen);
+
+/* Select a launch shape by index (0 .. SU2_NUM_LAUNCH_CONFIGS-1) / read
+ * the current one with its threads per block and minimum blocks per SM. */
+int su2_set_launch_config(su2_lattice* lat, int cfg);
+int su2_get_launch_config(const su2_lattice* lat, int* cfg, int* threads, int* min_blocks);
+
+/* Test hooks of the tuning cache: the handle's key (GPU name|precision|
+ * shapes), and a lookup (returns 1 if found, 0 if not) and append on a
+ * cache file. */
+int su2_tune_key(const su2_lattice* lat, char* buf, size_t len);
+int su2_tune_cache_lookup(const char* path, const char* key, int* cfg);
+int su2_tune_cache_store(const char* path, const char* key, int cfg, double ms);
+
 /* Waits for the handle's stream; returns SU2_E_TRIALS (once) if a cap hit
  * occurred since the previous synchronising call. */
 int su2_sync(su2_lattice* lat);

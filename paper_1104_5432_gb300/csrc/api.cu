@@ -1,7 +1,9 @@
 // api.cu -- the C ABI (include/su2.h): handles, binding of caller-owned
 // device memory, sweep orchestration through a replayed CUDA graph, host /
 // device output handling, checkpoints and statistics.
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -67,11 +69,20 @@ struct su2_lattice {
     int dtype = 0;
     std::vector<int> Ns, Nt;
     std::vector<uint64_t> V, Vs, link_off, field_off;
-    std::vector<uint32_t> phase_start, site_start, spat_start;
-    uint32_t phase_blocks = 0, site_blocks = 0, spat_blocks = 0;
+    std::vector<uint32_t> site_start, spat_start;
+    uint32_t site_blocks = 0, spat_blocks = 0;
+    // per launch shape of the phase kernel: first block of each lattice,
+    // total blocks, sweep-end chunks
+    std::vector<uint32_t> phase_start[NUM_LAUNCH_CFG];
+    uint32_t phase_blocks[NUM_LAUNCH_CFG] = {};
+    uint32_t cfg_chunks[NUM_LAUNCH_CFG] = {};
+    size_t off_pstart_cfg[NUM_LAUNCH_CFG] = {};
+    uint32_t max_phase_blocks = 0;
+    int cfg = 0;                    // active launch shape
+    std::string tune_key;
     int rmax_limit = 0;             // rmax <= min_l Ns_l / 2
     size_t link_bytes = 0, work_bytes = 0;
-    size_t off_status = 0, off_desc = 0, off_pstart = 0, off_sstart = 0, off_spstart = 0;
+    size_t off_status = 0, off_desc = 0, off_sstart = 0, off_spstart = 0;
     size_t off_plaq = 0, off_obs = 0, off_field = 0, off_ring = 0, off_res = 0, off_stage = 0;
     size_t off_chunks = 0, off_tickets = 0, off_acc = 0;
     uint32_t max_chunks = 1;
@@ -82,10 +93,12 @@ struct su2_lattice {
     int device = -1;
     cudaStream_t stream = 0;
     cudaStream_t capture = nullptr;
-    cudaGraphExec_t sweep_graph[2] = {nullptr, nullptr};
+    // replayable sweeps per launch shape and fused-plaquette flag
+    cudaGraphExec_t sweep_graph[NUM_LAUNCH_CFG][2] = {};
     int measure_rmax = -1;                  // rmax baked into measure_graph
-    cudaGraphExec_t measure_graph[2] = {nullptr, nullptr};
-    Ctx ctx{};
+    cudaGraphExec_t measure_graph[NUM_LAUNCH_CFG][2] = {};
+    Ctx ctx{};                      // non-phase kernels
+    Ctx cfg_ctx[NUM_LAUNCH_CFG]{};  // phase kernels and sweep end, per launch shape
 
     bool bound() const { return links != nullptr && work != nullptr; }
     LatDesc* desc_dev(int l) const
@@ -99,14 +112,20 @@ struct su2_lattice {
 
     double* acc_dev() const { return reinterpret_cast<double*>(work + off_acc); }
 
+    static void drop(cudaGraphExec_t (&gs)[NUM_LAUNCH_CFG][2])
+    {
+        for (auto& row : gs)
+            for (auto& g : row)
+                if (g) {
+                    cudaGraphExecDestroy(g);
+                    g = nullptr;
+                }
+    }
+
     void drop_graphs()
     {
-        for (auto* gs : {sweep_graph, measure_graph})
-            for (int k = 0; k < 2; ++k)
-                if (gs[k]) {
-                    cudaGraphExecDestroy(gs[k]);
-                    gs[k] = nullptr;
-                }
+        drop(sweep_graph);
+        drop(measure_graph);
         measure_rmax = -1;
     }
 };
@@ -138,7 +157,7 @@ int layout(su2_lattice* L)
     L->Vs.resize(n);
     L->link_off.resize(n);
     L->field_off.resize(n);
-    L->phase_start.assign(n + 1, 0);
+    for (int k = 0; k < NUM_LAUNCH_CFG; ++k) L->phase_start[k].assign(n + 1, 0);
     L->site_start.assign(n + 1, 0);
     L->spat_start.assign(n + 1, 0);
     size_t lb = 0;
@@ -153,16 +172,25 @@ int layout(su2_lattice* L)
         lb += align256(4 * L->V[l] * link_size);
         L->field_off[l] = fo;
         fo += (L->Vs[l] + 31) & ~uint64_t(31);
-        L->phase_start[l + 1] = L->phase_start[l] + blocks_of(L->V[l] / 2);
+        for (int k = 0; k < NUM_LAUNCH_CFG; ++k) {
+            const uint64_t nt = (uint64_t)LAUNCH_CFG[L->dtype][k].threads;
+            L->phase_start[k][l + 1] = L->phase_start[k][l] + (uint32_t)((L->V[l] / 2 + nt - 1) / nt);
+        }
         L->site_start[l + 1] = L->site_start[l] + blocks_of(L->V[l]);
         L->spat_start[l + 1] = L->spat_start[l] + blocks_of(L->Vs[l]);
         rlim = std::min(rlim, L->Ns[l] / 2);
     }
-    L->phase_blocks = L->phase_start[n];
     L->max_chunks = 1;
-    for (int l = 0; l < n; ++l) {
-        const uint32_t nb = L->phase_start[l + 1] - L->phase_start[l];
-        L->max_chunks = std::max<uint32_t>(L->max_chunks, (3 * nb + SWEEP_CHUNK - 1) / SWEEP_CHUNK);
+    L->max_phase_blocks = 0;
+    for (int k = 0; k < NUM_LAUNCH_CFG; ++k) {
+        L->phase_blocks[k] = L->phase_start[k][n];
+        L->max_phase_blocks = std::max(L->max_phase_blocks, L->phase_blocks[k]);
+        L->cfg_chunks[k] = 1;
+        for (int l = 0; l < n; ++l) {
+            const uint32_t nb = L->phase_start[k][l + 1] - L->phase_start[k][l];
+            L->cfg_chunks[k] = std::max<uint32_t>(L->cfg_chunks[k], (3 * nb + SWEEP_CHUNK - 1) / SWEEP_CHUNK);
+        }
+        L->max_chunks = std::max(L->max_chunks, L->cfg_chunks[k]);
     }
     L->site_blocks = L->site_start[n];
     L->spat_blocks = L->spat_start[n];
@@ -177,10 +205,10 @@ int layout(su2_lattice* L)
     };
     L->off_status = take(256);
     L->off_desc = take(sizeof(LatDesc) * n);
-    L->off_pstart = take(4 * (n + 1));
+    for (int k = 0; k < NUM_LAUNCH_CFG; ++k) L->off_pstart_cfg[k] = take(4 * (n + 1));
     L->off_sstart = take(4 * (n + 1));
     L->off_spstart = take(4 * (n + 1));
-    L->off_plaq = take(8 * 3 * (size_t)L->phase_blocks);
+    L->off_plaq = take(8 * 3 * (size_t)L->max_phase_blocks);
     const size_t obs_rows = std::max<size_t>(L->site_blocks,
                                              (size_t)L->spat_blocks * (size_t)(L->rmax_limit + 1));
     L->off_obs = take(8 * obs_rows);
@@ -246,8 +274,9 @@ int set_params(su2_lattice* L, const double* betas, double beta, const uint64_t*
 int record_sweep(su2_lattice* L, bool plaq, int rmax, cudaStream_t s)
 {
     for (int mu = 0; mu < 4; ++mu)
-        for (int p = 0; p < 2; ++p) SU2_CUDA(launch_phase(L->ctx, L->dtype, mu, p, plaq, nullptr, s));
-    SU2_CUDA(launch_sweep_end(L->ctx, plaq, s));
+        for (int p = 0; p < 2; ++p)
+            SU2_CUDA(launch_phase(L->cfg_ctx[L->cfg], L->dtype, L->cfg, mu, p, plaq, nullptr, s));
+    SU2_CUDA(launch_sweep_end(L->cfg_ctx[L->cfg], plaq, s));
     if (rmax >= 0) {
         double* acc = L->acc_dev();
         SU2_CUDA(launch_polyakov(L->ctx, L->dtype, acc, acc + L->n, 1, s));
@@ -260,14 +289,11 @@ int record_sweep(su2_lattice* L, bool plaq, int rmax, cudaStream_t s)
 int sweep_graph(su2_lattice* L, bool plaq, int rmax, cudaGraphExec_t* exec)
 {
     if (rmax >= 0 && rmax != L->measure_rmax) {
-        for (auto& gm : L->measure_graph)
-            if (gm) {
-                cudaGraphExecDestroy(gm);
-                gm = nullptr;
-            }
+        su2_lattice::drop(L->measure_graph);
         L->measure_rmax = rmax;
     }
-    cudaGraphExec_t& g = rmax >= 0 ? L->measure_graph[plaq ? 1 : 0] : L->sweep_graph[plaq ? 1 : 0];
+    cudaGraphExec_t& g = rmax >= 0 ? L->measure_graph[L->cfg][plaq ? 1 : 0]
+                                   : L->sweep_graph[L->cfg][plaq ? 1 : 0];
     if (!g) {
         if (!L->capture) SU2_CUDA(cudaStreamCreateWithFlags(&L->capture, cudaStreamNonBlocking));
         SU2_CUDA(cudaStreamBeginCapture(L->capture, cudaStreamCaptureModeThreadLocal));
@@ -379,6 +405,66 @@ int finish_output(su2_lattice* L, double* out, const double* dev_src, size_t cou
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// launch-shape autotuning: key, cache file, measurement
+// ---------------------------------------------------------------------------
+namespace {
+
+// FNV-1a over the lattice shapes, with the GPU name and precision in clear
+std::string tune_key(const su2_lattice* L, int dev)
+{
+    cudaDeviceProp prop;
+    std::string name = "unknown-gpu";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    else cudaGetLastError();
+    for (auto& ch : name)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    uint64_t h = 1469598103934665603ull;
+    for (int l = 0; l < L->n; ++l)
+        for (int v : {L->Ns[l], L->Nt[l]}) {
+            h ^= (uint64_t)v;
+            h *= 1099511628211ull;
+        }
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|%s|n%d|V%llu|%016llx", name.c_str(), L->dtype ? "f64" : "f32",
+             L->n, (unsigned long long)[&] {
+                 uint64_t t = 0;
+                 for (uint64_t v : L->V) t += v;
+                 return t;
+             }(), (unsigned long long)h);
+    return buf;
+}
+
+// Cache file: one line per key, "key cfg ms_per_phase"; later lines win.
+bool cache_lookup(const char* path, const std::string& key, int* cfg)
+{
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        char k[400];
+        int c = -1;
+        double ms = 0;
+        if (sscanf(line, "%399s %d %lf", k, &c, &ms) >= 2 && key == k) {
+            *cfg = c;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+bool cache_store(const char* path, const std::string& key, int cfg, double ms)
+{
+    FILE* f = fopen(path, "a");
+    if (!f) return false;
+    const bool ok = fprintf(f, "%s %d %.6f\n", key.c_str(), cfg, ms) > 0;
+    return fclose(f) == 0 && ok;
+}
+
+}  // namespace
+
 void su2::record_error(const char* msg) { g_err = msg; }
 
 // --------------------------------------------------------------------------
@@ -469,8 +555,9 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
     SU2_CUDA(cudaMemset(w + lat->off_status, 0, 256));
     SU2_CUDA(cudaMemcpy(w + lat->off_desc, d.data(), sizeof(LatDesc) * lat->n,
                         cudaMemcpyHostToDevice));
-    SU2_CUDA(cudaMemcpy(w + lat->off_pstart, lat->phase_start.data(), 4 * (lat->n + 1),
-                        cudaMemcpyHostToDevice));
+    for (int k = 0; k < NUM_LAUNCH_CFG; ++k)
+        SU2_CUDA(cudaMemcpy(w + lat->off_pstart_cfg[k], lat->phase_start[k].data(),
+                            4 * (lat->n + 1), cudaMemcpyHostToDevice));
     SU2_CUDA(cudaMemcpy(w + lat->off_sstart, lat->site_start.data(), 4 * (lat->n + 1),
                         cudaMemcpyHostToDevice));
     SU2_CUDA(cudaMemcpy(w + lat->off_spstart, lat->spat_start.data(), 4 * (lat->n + 1),
@@ -481,7 +568,7 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
     Ctx& c = lat->ctx;
     c.links = links;
     c.desc = reinterpret_cast<LatDesc*>(w + lat->off_desc);
-    c.phase_start = reinterpret_cast<const uint32_t*>(w + lat->off_pstart);
+    c.phase_start = reinterpret_cast<const uint32_t*>(w + lat->off_pstart_cfg[0]);
     c.site_start = reinterpret_cast<const uint32_t*>(w + lat->off_sstart);
     c.spat_start = reinterpret_cast<const uint32_t*>(w + lat->off_spstart);
     c.plaq_partial = reinterpret_cast<double*>(w + lat->off_plaq);
@@ -490,12 +577,26 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
     c.ring = reinterpret_cast<double*>(w + lat->off_ring);
     c.chunk_partial = reinterpret_cast<double*>(w + lat->off_chunks);
     c.chunk_count = reinterpret_cast<uint32_t*>(w + lat->off_tickets);
-    c.max_chunks = lat->max_chunks;
+    c.max_chunks = lat->cfg_chunks[0];
     c.status = reinterpret_cast<uint32_t*>(w + lat->off_status);
     c.n = lat->n;
-    c.phase_blocks = lat->phase_blocks;
+    c.phase_blocks = lat->phase_blocks[0];
     c.site_blocks = lat->site_blocks;
     c.spat_blocks = lat->spat_blocks;
+    for (int k = 0; k < NUM_LAUNCH_CFG; ++k) {
+        lat->cfg_ctx[k] = c;
+        lat->cfg_ctx[k].phase_start = reinterpret_cast<const uint32_t*>(w + lat->off_pstart_cfg[k]);
+        lat->cfg_ctx[k].phase_blocks = lat->phase_blocks[k];
+        lat->cfg_ctx[k].max_chunks = lat->cfg_chunks[k];
+    }
+    // a launch shape tuned earlier for these shapes on this GPU, if cached
+    lat->tune_key = tune_key(lat, dev);
+    lat->cfg = 0;
+    if (const char* path = getenv("SU2_AUTOTUNE_CACHE")) {
+        int cached = -1;
+        if (cache_lookup(path, lat->tune_key, &cached) && cached >= 0 && cached < NUM_LAUNCH_CFG)
+            lat->cfg = cached;
+    }
     return SU2_OK;
 }
 
@@ -549,7 +650,8 @@ int su2_heatbath_phase(su2_lattice* lat, double beta, int mu, int parity, uint64
     if (trials && !is_device_ptr(trials)) return fail(SU2_E_INVAL, "trials must be device memory");
     DeviceGuard dg(lat->device);
     if (int rc = set_params(lat, nullptr, beta, nullptr, seed, nullptr, 0)) return rc;
-    SU2_CUDA(launch_phase(lat->ctx, lat->dtype, mu, parity, false, trials, lat->stream));
+    SU2_CUDA(launch_phase(lat->cfg_ctx[lat->cfg], lat->dtype, lat->cfg, mu, parity, false, trials,
+                          lat->stream));
     return SU2_OK;
 }
 
@@ -699,6 +801,114 @@ int su2_sync(su2_lattice* lat)
     if (int rc = check_handle(lat)) return rc;
     DeviceGuard dg(lat->device);
     return sync_status(lat);
+}
+
+int su2_autotune(su2_lattice* lat, int* chosen)
+{
+    if (int rc = check_handle(lat)) return rc;
+    DeviceGuard dg(lat->device);
+    cudaStream_t s = lat->stream;
+    const uint64_t tune_seed = 0x5EEDull;
+    for (int l = 0; l < lat->n; ++l)
+        SU2_CUDA(launch_init(lat->ctx, lat->dtype, l, (uint32_t)lat->V[l], SU2_HOT, tune_seed + l, s));
+    if (int rc = set_params(lat, nullptr, 2.4, nullptr, tune_seed, nullptr, 0)) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SU2_CUDA(cudaEventCreate(&e0));
+    SU2_CUDA(cudaEventCreate(&e1));
+    const int saved = lat->cfg;
+    double best_ms[NUM_LAUNCH_CFG];
+    int reps[NUM_LAUNCH_CFG];
+    int rc = SU2_OK;
+    // Time what production runs: whole sweeps (graph replay, fused
+    // plaquette), shapes interleaved over three rounds, best round kept.
+    auto time_sweeps = [&](int k, int n, float* ms) -> int {
+        lat->cfg = k;
+        cudaGraphExec_t g = nullptr;
+        if (int r = sweep_graph(lat, true, -1, &g)) return r;
+        cudaError_t e = cudaEventRecord(e0, s);
+        for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaGraphLaunch(g, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        return e == cudaSuccess ? SU2_OK : cuda_fail(e, "autotune timing");
+    };
+    for (int k = 0; k < NUM_LAUNCH_CFG && rc == SU2_OK; ++k) {
+        float ms = 0.f;
+        rc = time_sweeps(k, 1, &ms);  // builds the graph, warms up
+        if (rc == SU2_OK) rc = time_sweeps(k, 1, &ms);
+        // about 20 ms of sweeps per round, between 1 and 50
+        reps[k] = std::max(1, std::min(50, (int)(20.0 / std::max(ms, 1e-3f))));
+        best_ms[k] = 1e300;
+    }
+    for (int round = 0; round < 3 && rc == SU2_OK; ++round)
+        for (int k = 0; k < NUM_LAUNCH_CFG && rc == SU2_OK; ++k) {
+            float ms = 0.f;
+            rc = time_sweeps(k, reps[k], &ms);
+            best_ms[k] = std::min(best_ms[k], (double)ms / reps[k]);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lat->cfg = saved;
+    if (rc != SU2_OK) return rc;
+    int best = 0;
+    for (int k = 1; k < NUM_LAUNCH_CFG; ++k)
+        if (best_ms[k] < best_ms[best]) best = k;
+    // leave the handle as su2_init(SU2_HOT) with the tuning seed would
+    for (int l = 0; l < lat->n; ++l)
+        SU2_CUDA(launch_init(lat->ctx, lat->dtype, l, (uint32_t)lat->V[l], SU2_HOT, tune_seed + l, s));
+    if (int r2 = sync_status(lat)) return r2;
+    lat->cfg = best;
+    if (const char* path = getenv("SU2_AUTOTUNE_CACHE"))
+        if (!cache_store(path, lat->tune_key, best, best_ms[best]))
+            return fail(SU2_E_INVAL, "cannot append to autotune cache %s", path);
+    if (chosen) *chosen = best;
+    return SU2_OK;
+}
+
+int su2_set_launch_config(su2_lattice* lat, int cfg)
+{
+    if (int rc = check_handle(lat, false)) return rc;
+    if (cfg < 0 || cfg >= NUM_LAUNCH_CFG)
+        return fail(SU2_E_INVAL, "launch config %d outside 0..%d", cfg, NUM_LAUNCH_CFG - 1);
+    lat->cfg = cfg;  // graphs are kept per launch shape
+    return SU2_OK;
+}
+
+int su2_get_launch_config(const su2_lattice* lat, int* cfg, int* threads, int* min_blocks)
+{
+    if (int rc = check_handle(lat, false)) return rc;
+    if (cfg) *cfg = lat->cfg;
+    if (threads) *threads = LAUNCH_CFG[lat->dtype][lat->cfg].threads;
+    if (min_blocks) *min_blocks = LAUNCH_CFG[lat->dtype][lat->cfg].min_blocks;
+    return SU2_OK;
+}
+
+int su2_tune_key(const su2_lattice* lat, char* buf, size_t len)
+{
+    if (int rc = check_handle(lat, false)) return rc;
+    if (!buf || len == 0) return fail(SU2_E_INVAL, "null buffer");
+    int dev = lat->device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    const std::string k = tune_key(lat, dev);
+    if (k.size() + 1 > len) return fail(SU2_E_INVAL, "buffer too small");
+    memcpy(buf, k.c_str(), k.size() + 1);
+    return SU2_OK;
+}
+
+int su2_tune_cache_lookup(const char* path, const char* key, int* cfg)
+{
+    if (!path || !key || !cfg) return fail(SU2_E_INVAL, "null argument");
+    return cache_lookup(path, key, cfg) ? 1 : 0;
+}
+
+int su2_tune_cache_store(const char* path, const char* key, int cfg, double ms)
+{
+    if (!path || !key) return fail(SU2_E_INVAL, "null argument");
+    if (cfg < 0 || cfg >= NUM_LAUNCH_CFG) return fail(SU2_E_INVAL, "bad config");
+    return cache_store(path, key, cfg, ms) ? SU2_OK : fail(SU2_E_INVAL, "cannot write %s", path);
 }
 
 const char* su2_last_error(void) { return g_err.c_str(); }

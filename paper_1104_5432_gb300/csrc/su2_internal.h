@@ -19,14 +19,20 @@
 
 namespace su2 {
 
-#ifndef SU2_TPB
-#define SU2_TPB 256
-#endif
-#ifndef SU2_HB_MIN_BLOCKS
-#define SU2_HB_MIN_BLOCKS 4
-#endif
-constexpr int TPB = SU2_TPB;        // threads per block of every lattice kernel
-constexpr int HB_MIN_BLOCKS = SU2_HB_MIN_BLOCKS;  // phase-kernel residency hint
+constexpr int TPB = 256;            // threads per block of the non-phase kernels
+
+// Launch shapes of the phase kernel the autotuner chooses from (threads per
+// block, minimum resident blocks per SM); entry 0 is the default.  Row 0:
+// FP32, row 1: FP64.
+struct LaunchCfg {
+    int threads, min_blocks;
+};
+constexpr int NUM_LAUNCH_CFG = 4;
+constexpr LaunchCfg LAUNCH_CFG[2][NUM_LAUNCH_CFG] = {
+    {{256, 4}, {256, 3}, {128, 8}, {512, 2}},
+    {{256, 1}, {256, 2}, {128, 4}, {128, 1}},
+};
+
 constexpr int KP_CAP = 4096;        // Kennedy-Pendleton trial cap
 constexpr int PLAQ_RING = 4096;     // per-lattice plaquette slots for host output
 constexpr size_t STAGE_BYTES = size_t(32) << 20;
@@ -93,7 +99,7 @@ struct ParamChunk {
     double* plaq_out[PARAM_CHUNK];
 };
 cudaError_t launch_set_params(const Ctx& c, const ParamChunk& pc, cudaStream_t s);
-cudaError_t launch_phase(const Ctx& c, int dtype, int mu, int parity, bool plaq,
+cudaError_t launch_phase(const Ctx& c, int dtype, int cfg, int mu, int parity, bool plaq,
                          int32_t* dbg_trials, cudaStream_t s);
 cudaError_t launch_sweep_end(const Ctx& c, bool plaq, cudaStream_t s);
 cudaError_t launch_init(const Ctx& c, int dtype, int l, uint32_t V, int hot, uint64_t seed,

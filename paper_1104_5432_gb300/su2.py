@@ -79,6 +79,12 @@ def load(build_if_needed: bool = True):
             "su2_selftest_fastdiv": (u64, [C.c_uint32, C.c_uint32]),
             "su2_plaquette_static": (i, [P, i, i, i, P, P]),
             "su2_selftest_math": (i, [P, P]),
+            "su2_autotune": (i, [P, P]),
+            "su2_set_launch_config": (i, [P, i]),
+            "su2_get_launch_config": (i, [P, P, P, P]),
+            "su2_tune_key": (i, [P, C.c_char_p, sz]),
+            "su2_tune_cache_lookup": (i, [C.c_char_p, C.c_char_p, P]),
+            "su2_tune_cache_store": (i, [C.c_char_p, C.c_char_p, i, d]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -268,6 +274,21 @@ class Lattice:
 
     def set_sweep(self, sweep: int, l: int = 0):
         _check(load().su2_set_sweep(self._h, l, int(sweep)))
+
+    # -- launch shape --------------------------------------------------------
+    def autotune(self) -> int:
+        """Pick the fastest launch shape (overwrites the links: call first)."""
+        c = C.c_int()
+        _check(load().su2_autotune(self._h, C.byref(c)))
+        return c.value
+
+    def set_launch_config(self, cfg: int):
+        _check(load().su2_set_launch_config(self._h, int(cfg)))
+
+    def launch_config(self):
+        c, t, m = C.c_int(), C.c_int(), C.c_int()
+        _check(load().su2_get_launch_config(self._h, C.byref(c), C.byref(t), C.byref(m)))
+        return c.value, t.value, m.value
 
     def sync(self):
         _check(load().su2_sync(self._h))

@@ -76,3 +76,54 @@ def test_batch_layout_sizes():
     lib.su2_lattice_destroy(h)
     assert lib.su2_batch_create(0, Ns.ctypes.data, Nt.ctypes.data, su2.F32, C.byref(h)) \
         == su2.SU2_E_INVAL
+
+
+def test_tune_cache_round_trip(tmp_path):
+    lib = su2.load()
+    path = str(tmp_path / "tune.txt").encode()
+    cfg = C.c_int(-1)
+    assert lib.su2_tune_cache_lookup(path, b"gpu|f32|n1|V256|00ff", C.byref(cfg)) == 0
+    assert lib.su2_tune_cache_store(path, b"gpu|f32|n1|V256|00ff", 2, 0.25) == 0
+    assert lib.su2_tune_cache_store(path, b"gpu|f64|n1|V256|00ff", 1, 0.5) == 0
+    assert lib.su2_tune_cache_lookup(path, b"gpu|f32|n1|V256|00ff", C.byref(cfg)) == 1
+    assert cfg.value == 2
+    # a later entry for the same key wins
+    assert lib.su2_tune_cache_store(path, b"gpu|f32|n1|V256|00ff", 3, 0.2) == 0
+    assert lib.su2_tune_cache_lookup(path, b"gpu|f32|n1|V256|00ff", C.byref(cfg)) == 1
+    assert cfg.value == 3
+    assert lib.su2_tune_cache_store(path, b"k", 9, 0.1) == su2.SU2_E_INVAL
+
+
+def test_tune_key_and_launch_config_host_side():
+    lib = su2.load()
+    h = C.c_void_p()
+    Ns = np.array([4, 6], np.int32)
+    Nt = np.array([4, 2], np.int32)
+    assert lib.su2_batch_create(2, Ns.ctypes.data, Nt.ctypes.data, su2.F32, C.byref(h)) == 0
+    buf = C.create_string_buffer(256)
+    assert lib.su2_tune_key(h, buf, 256) == 0
+    key = buf.value.decode()
+    parts = key.split("|")
+    assert parts[1] == "f32" and parts[2] == "n2" and parts[3] == "V%d" % (4 ** 4 + 6 ** 3 * 2)
+    cfg, thr, mb = C.c_int(), C.c_int(), C.c_int()
+    assert lib.su2_get_launch_config(h, C.byref(cfg), C.byref(thr), C.byref(mb)) == 0
+    assert (cfg.value, thr.value) == (0, 256)
+    assert lib.su2_set_launch_config(h, 2) == 0
+    assert lib.su2_get_launch_config(h, C.byref(cfg), C.byref(thr), C.byref(mb)) == 0
+    assert (cfg.value, thr.value, mb.value) == (2, 128, 8)
+    assert lib.su2_set_launch_config(h, 4) == su2.SU2_E_INVAL
+    lib.su2_lattice_destroy(h)
+
+
+def test_launch_shape_mirror_matches_library():
+    from paper_1104_5432_gb300.csrc_info import _F32, _F64
+    lib = su2.load()
+    for dtype, table in ((su2.F32, _F32), (su2.F64, _F64)):
+        h = C.c_void_p()
+        assert lib.su2_lattice_create(4, 4, dtype, C.byref(h)) == 0
+        for k, (t, m) in enumerate(table):
+            assert lib.su2_set_launch_config(h, k) == 0
+            cfg, thr, mb = C.c_int(), C.c_int(), C.c_int()
+            lib.su2_get_launch_config(h, C.byref(cfg), C.byref(thr), C.byref(mb))
+            assert (thr.value, mb.value) == (t, m)
+        lib.su2_lattice_destroy(h)

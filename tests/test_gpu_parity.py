@@ -367,3 +367,43 @@ def test_fp32_math_forms_exhaustive():
     assert cerr <= 1.5e-6, cerr
     assert serr <= 1e-6, serr
     assert qerr <= 3e-7, qerr
+
+
+@pytest.mark.parametrize("dtype", [su2.F32, su2.F64])
+def test_every_launch_shape_gives_identical_results(dtype):
+    """The random streams are keyed by link and sweep, never by thread: each
+    launch shape the autotuner may pick produces the same links bit for
+    bit (batch of uneven lattices, two sweeps)."""
+    shapes = [(6, 4), (8, 6), (4, 2)]
+    seeds, betas = [7, 8, 9], [2.3, 2.5, 1.9]
+    ref_links = ref_plaq = None
+    for cfg in range(4):
+        B = su2.Lattice([s[0] for s in shapes], [s[1] for s in shapes], dtype)
+        B.set_launch_config(cfg)
+        assert B.launch_config()[0] == cfg
+        B.batch_init(su2.HOT, seeds)
+        plaq = B.batch_heatbath(betas, 2, seeds)
+        links = [B.get_links(l) for l in range(3)]
+        if ref_links is None:
+            ref_links, ref_plaq = links, plaq
+            continue
+        for a, b in zip(links, ref_links):
+            np.testing.assert_array_equal(a, b)
+        np.testing.assert_allclose(plaq, ref_plaq, rtol=1e-13, atol=0)
+
+
+def test_autotune_and_cache(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("SU2_AUTOTUNE_CACHE", str(cache))
+    lat = su2.Lattice(16, 16, su2.F32)
+    chosen = lat.autotune()
+    assert 0 <= chosen < 4 and lat.launch_config()[0] == chosen
+    # the handle is left in the hot start of the tuning seed
+    assert lat.get_sweep() == 0 and lat.stats()["updates"] == 0
+    ref = su2.Lattice(16, 16, su2.F32)
+    ref.init(su2.HOT, 0x5EED)
+    np.testing.assert_array_equal(lat.get_links(), ref.get_links())
+    assert cache.exists() and len(cache.read_text().splitlines()) == 1
+    # a new handle of the same shape on this GPU starts with the cached shape
+    again = su2.Lattice(16, 16, su2.F32)
+    assert again.launch_config()[0] == chosen

@@ -84,7 +84,7 @@ struct su2_lattice {
     size_t link_bytes = 0, work_bytes = 0;
     size_t off_status = 0, off_desc = 0, off_sstart = 0, off_spstart = 0;
     size_t off_plaq = 0, off_obs = 0, off_field = 0, off_ring = 0, off_res = 0, off_stage = 0;
-    size_t off_chunks = 0, off_tickets = 0, off_acc = 0;
+    size_t off_chunks = 0, off_tickets = 0, off_acc = 0, off_tslots = 0;
     uint32_t max_chunks = 1;
     size_t res_doubles = 0;
     // bound state
@@ -184,10 +184,11 @@ int layout(su2_lattice* L)
     L->max_phase_blocks = 0;
     for (int k = 0; k < NUM_LAUNCH_CFG; ++k) {
         L->phase_blocks[k] = L->phase_start[k][n];
-        L->max_phase_blocks = std::max(L->max_phase_blocks, L->phase_blocks[k]);
+        const uint32_t wpb = (uint32_t)LAUNCH_CFG[L->dtype][k].threads / 32;
+        L->max_phase_blocks = std::max(L->max_phase_blocks, L->phase_blocks[k] * wpb);
         L->cfg_chunks[k] = 1;
         for (int l = 0; l < n; ++l) {
-            const uint32_t nb = L->phase_start[k][l + 1] - L->phase_start[k][l];
+            const uint32_t nb = (L->phase_start[k][l + 1] - L->phase_start[k][l]) * wpb;
             L->cfg_chunks[k] = std::max<uint32_t>(L->cfg_chunks[k], (3 * nb + SWEEP_CHUNK - 1) / SWEEP_CHUNK);
         }
         L->max_chunks = std::max(L->max_chunks, L->cfg_chunks[k]);
@@ -216,6 +217,7 @@ int layout(su2_lattice* L)
     L->off_ring = take(8 * (size_t)PLAQ_RING * n);
     L->off_chunks = take(8 * (size_t)L->max_chunks * n);
     L->off_tickets = take(4 * (size_t)n);
+    L->off_tslots = take(8 * (size_t)TRIAL_SLOTS * n);
     L->res_doubles = (size_t)n * (L->rmax_limit + 1) + 2 * (size_t)n;
     L->off_acc = take(8 * L->res_doubles);
     L->off_res = take(8 * L->res_doubles);
@@ -564,6 +566,7 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
                         cudaMemcpyHostToDevice));
     SU2_CUDA(cudaMemset(w + lat->off_ring, 0, 8 * (size_t)PLAQ_RING * lat->n));
     SU2_CUDA(cudaMemset(w + lat->off_tickets, 0, 4 * (size_t)lat->n));
+    SU2_CUDA(cudaMemset(w + lat->off_tslots, 0, 8 * (size_t)TRIAL_SLOTS * lat->n));
 
     Ctx& c = lat->ctx;
     c.links = links;
@@ -577,7 +580,9 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
     c.ring = reinterpret_cast<double*>(w + lat->off_ring);
     c.chunk_partial = reinterpret_cast<double*>(w + lat->off_chunks);
     c.chunk_count = reinterpret_cast<uint32_t*>(w + lat->off_tickets);
+    c.trial_slots = reinterpret_cast<unsigned long long*>(w + lat->off_tslots);
     c.max_chunks = lat->cfg_chunks[0];
+    c.phase_wpb = (uint32_t)LAUNCH_CFG[lat->dtype][0].threads / 32;
     c.status = reinterpret_cast<uint32_t*>(w + lat->off_status);
     c.n = lat->n;
     c.phase_blocks = lat->phase_blocks[0];
@@ -588,6 +593,7 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
         lat->cfg_ctx[k].phase_start = reinterpret_cast<const uint32_t*>(w + lat->off_pstart_cfg[k]);
         lat->cfg_ctx[k].phase_blocks = lat->phase_blocks[k];
         lat->cfg_ctx[k].max_chunks = lat->cfg_chunks[k];
+        lat->cfg_ctx[k].phase_wpb = (uint32_t)LAUNCH_CFG[lat->dtype][k].threads / 32;
     }
     // a launch shape tuned earlier for these shapes on this GPU, if cached
     lat->tune_key = tune_key(lat, dev);
@@ -770,7 +776,11 @@ int su2_stats(su2_lattice* lat, int l, uint64_t out[3])
     SU2_CUDA(cudaStreamSynchronize(lat->stream));
     LatDesc d;
     SU2_CUDA(cudaMemcpy(&d, lat->desc_dev(l), sizeof d, cudaMemcpyDeviceToHost));
+    unsigned long long slots[TRIAL_SLOTS];
+    SU2_CUDA(cudaMemcpy(slots, lat->ctx.trial_slots + (size_t)l * TRIAL_SLOTS, sizeof slots,
+                        cudaMemcpyDeviceToHost));
     out[0] = d.trials;
+    for (unsigned long long v : slots) out[0] += v;
     out[1] = d.updates;
     out[2] = d.caps;
     return SU2_OK;

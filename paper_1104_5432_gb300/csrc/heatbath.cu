@@ -22,8 +22,10 @@ __global__ void __launch_bounds__(TPB) sweep_end_kernel(Ctx ctx)
         if (blockIdx.x == 0 && threadIdx.x == 0) D->sweep += 1;
         return;
     }
-    const uint32_t b0 = ctx.phase_start[l];
-    const uint32_t nb = ctx.phase_start[l + 1] - b0;
+    // partials are per warp: lattice l owns warps [b0, b0 + nb) of each slot
+    const uint32_t b0 = ctx.phase_start[l] * ctx.phase_wpb;
+    const uint32_t nb = ctx.phase_start[l + 1] * ctx.phase_wpb - b0;
+    const uint32_t stride = ctx.phase_blocks * ctx.phase_wpb;
     const uint32_t total = 3 * nb;
     const uint32_t nchunk = (total + SWEEP_CHUNK - 1) / SWEEP_CHUNK;
     if (blockIdx.x >= nchunk) return;
@@ -33,7 +35,7 @@ __global__ void __launch_bounds__(TPB) sweep_end_kernel(Ctx ctx)
     double acc = 0.0;
     for (uint32_t e = e0 + threadIdx.x; e < e1; e += TPB) {
         const uint32_t slot = (e >= nb) + (e >= 2 * nb);
-        acc += ctx.plaq_partial[(size_t)slot * ctx.phase_blocks + b0 + (e - slot * nb)];
+        acc += ctx.plaq_partial[(size_t)slot * stride + b0 + (e - slot * nb)];
     }
     const double part = block_sum<TPB>(acc, sred);
     double* chunks = ctx.chunk_partial + (size_t)l * ctx.max_chunks;
@@ -67,6 +69,7 @@ __global__ void set_params_kernel(Ctx ctx, ParamChunk pc)
     if (j >= pc.count) return;
     LatDesc* D = ctx.desc + pc.first + j;
     D->beta = pc.beta[j];
+    D->beta_f = (float)pc.beta[j];
     D->seed = pc.seed[j];
     D->plaq_out = pc.plaq_out[j];
     D->sweep_base = D->sweep;

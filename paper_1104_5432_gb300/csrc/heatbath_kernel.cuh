@@ -35,6 +35,10 @@ template <typename T> __device__ __forceinline__ T alpha_haar();
 template <> __device__ __forceinline__ float alpha_haar<float>() { return 1e-12f; }
 template <> __device__ __forceinline__ double alpha_haar<double>() { return 1e-12; }
 
+template <typename T> __device__ __forceinline__ T beta_of(const LatDesc& D);
+template <> __device__ __forceinline__ float beta_of<float>(const LatDesc& D) { return D.beta_f; }
+template <> __device__ __forceinline__ double beta_of<double>(const LatDesc& D) { return D.beta; }
+
 // warp partial sum in the link precision (fixed butterfly order)
 template <typename T>
 __device__ __forceinline__ T warp_sum_t(T v)
@@ -48,9 +52,6 @@ template <typename T, int MU, bool PLAQ, bool DBG, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 {
-    __shared__ uint32_t s_trials[NT / 32];
-    __shared__ T s_plaq[NT / 32];
-
     const int l = lattice_of_block(ctx.phase_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
     const uint32_t Vh = D.Vh;
@@ -62,7 +63,7 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 
     T plaq = T(0);
     uint32_t ntrial = 0;
-    int ncap = 0;
+    bool ncap = false;
 
     if (active) {
         const EoSite s(D, i, p);
@@ -92,7 +93,7 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
         // alpha = beta k and 1/(2 alpha) from one reciprocal square root of k^2
         const T k2 = qnorm2(A);
         const T rk = Math<T>::rsqrt(k2);
-        const T beta = T(D.beta);
+        const T beta = beta_of<T>(D);
         const T alpha = beta * k2 * rk;
         const uint64_t sw = D.sweep;
         const Stream st{(uint32_t)D.seed, (uint32_t)(D.seed >> 32), s.lex() * 4u + MU,
@@ -133,7 +134,7 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
         if (tr >= 0) {
             U.store(MU, p, i, un);
         } else {
-            ncap = 1;
+            ncap = true;
             if (PLAQ) un = U.load_rw(MU, p, i);
         }
         ntrial = tr > 0 ? (uint32_t)tr : (tr < 0 ? (uint32_t)KP_CAP : 0u);
@@ -145,38 +146,29 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
         }
     }
 
-    // One barrier for every block total: warp partials to shared memory,
-    // cap hits counted by the barrier itself.  Trial counts are exact
-    // integers (atomics); the plaquette partial is written per block and
-    // summed later in a fixed order.
+    // Totals without any block barrier (a warp never waits for the
+    // block's slowest warp): trial counts go to spread per-lattice atomic
+    // slots (exact integers), cap hits to an atomic only when present, the
+    // plaquette to one partial per warp, summed later in a fixed order.
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t wt = __reduce_add_sync(0xffffffffu, ntrial);
+    const uint32_t capmask = __ballot_sync(0xffffffffu, ncap);
     T wp = T(0);
     if (PLAQ) wp = warp_sum_t(plaq);
     if (lane == 0) {
-        s_trials[w] = wt;
-        if (PLAQ) s_plaq[w] = wp;
-    }
-    const int bc = __syncthreads_count(ncap);
-    if (threadIdx.x == 0) {
-        unsigned long long bt = 0;
-        double bp = 0.0;
-#pragma unroll
-        for (int k = 0; k < NT / 32; ++k) {
-            bt += s_trials[k];
-            if (PLAQ) bp += (double)s_plaq[k];
-        }
-        if (PLAQ) ctx.plaq_partial[(size_t)(MU - 1) * ctx.phase_blocks + blockIdx.x] = bp;
+        const uint32_t gw = blockIdx.x * (NT / 32) + w;  // global warp index
+        if (PLAQ)
+            ctx.plaq_partial[(size_t)(MU - 1) * ctx.phase_blocks * (NT / 32) + gw] = (double)wp;
+        atomicAdd(ctx.trial_slots + (size_t)l * TRIAL_SLOTS + (gw % TRIAL_SLOTS),
+                  (unsigned long long)wt);
         LatDesc* Dw = ctx.desc + l;
-        atomicAdd(&Dw->trials, bt);
-        if (blockIdx.x == blk0) atomicAdd(&Dw->updates, (unsigned long long)Vh);
-        if (bc) {
-            atomicAdd(&Dw->caps, (unsigned long long)bc);
+        if (w == 0 && blockIdx.x == blk0) atomicAdd(&Dw->updates, (unsigned long long)Vh);
+        if (capmask) {
+            atomicAdd(&Dw->caps, (unsigned long long)__popc(capmask));
             atomicOr(ctx.status, STATUS_CAP_HIT);
         }
     }
 }
-
 
 // One launch shape (NT threads per block, at least MINB blocks per SM) of
 // the phase kernel; the grid covers ctx.phase_blocks blocks of NT links.

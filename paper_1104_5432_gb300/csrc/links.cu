@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(TPB) init_kernel(Ctx ctx, int l, int hot, uint
         Dw->sweep = 0;
         Dw->trials = Dw->updates = Dw->caps = 0;
     }
+    if (lex < TRIAL_SLOTS) ctx.trial_slots[(size_t)l * TRIAL_SLOTS + lex] = 0;
     if (lex >= D.V) return;
     const Links<T> U(ctx.links, D);
     int p;

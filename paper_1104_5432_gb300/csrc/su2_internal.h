@@ -39,6 +39,7 @@ constexpr size_t STAGE_BYTES = size_t(32) << 20;
 constexpr uint32_t STATUS_CAP_HIT = 1u;
 constexpr int SWEEP_CHUNK = TPB * 8;   // plaquette partials summed per sweep_end block
 constexpr int MAX_RMAX = 128;          // largest correlator separation
+constexpr int TRIAL_SLOTS = 64;        // per-lattice trial counters (spread atomics)
 
 // One per lattice, resident in the work buffer.  The first block is fixed
 // at bind time; the second is written by the parameter kernel at every
@@ -51,6 +52,7 @@ struct LatDesc {
     uint64_t field_off;     // double offset of its Polyakov field
     // per call
     double beta;
+    float beta_f;           // beta rounded once for the FP32 kernels
     uint64_t seed;
     uint64_t sweep_base;    // sweep index stored at plaq_out[0]
     double* plaq_out;       // device, nullable
@@ -66,16 +68,18 @@ struct Ctx {
     const uint32_t* phase_start;   // [n+1] first block of each lattice, V/2 links
     const uint32_t* site_start;    // [n+1] ... V sites
     const uint32_t* spat_start;    // [n+1] ... Ns^3 spatial sites
-    double* plaq_partial;          // [3][phase blocks]
+    double* plaq_partial;          // [3][phase blocks * warps per block], per warp
     double* obs_partial;           // [obs_rows][max(site, spat) blocks]
     double* field;                 // Polyakov fields
     double* ring;                  // [n][PLAQ_RING]
     double* chunk_partial;         // [n][max_chunks] sweep_end chunk sums
     uint32_t* chunk_count;         // [n] sweep_end tickets (zero between sweeps)
+    unsigned long long* trial_slots;  // [n][TRIAL_SLOTS] Kennedy-Pendleton trial counts
     uint32_t* status;
     int n;
     uint32_t phase_blocks, site_blocks, spat_blocks;
     uint32_t max_chunks;
+    uint32_t phase_wpb;            // warps per phase block of this launch shape
 };
 
 // lattice owning grid block b: largest l with start[l] <= b

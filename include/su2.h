@@ -19,7 +19,8 @@
  *     with the Kennedy-Pendleton method from its staple sum A = k Vhat,
  *     U = X Vhat^dagger, then renormalised;
  *   - all random numbers come from Philox4x32-10, key = seed, counter =
- *     (lex*4+mu, sweep, tag<<24 | trial, sweep>>32), so results are
+ *     (lex*4+mu, sweep, tag<<24 | trial, sweep>>32) (the direction of a new
+ *     link uses the spare low bits of its first trial's block), so results are
  *     independent of launch shape, batching and graph replay, and
  *     heatbath(n) followed by heatbath(m) equals heatbath(n+m).
  *

@@ -30,9 +30,12 @@
  *              new link U = X Vhat^dagger, Vhat = A/k, then normalised
  *   RNG        Philox4x32-10, key = (seed lo, seed hi), counter =
  *              (lex*4+mu, sweep lo, tag<<24 | trial, sweep hi);
- *              tag 0 = KP trial, 1 = direction (or Haar draw when alpha is
- *              negligible), 2 = hot start, 3 = random gauge transformation;
- *              uniform(w) = ((w >> 9) + 0.5) * 2^-23
+ *              tag 0 = KP trial, 1 = Haar draw when alpha is negligible,
+ *              2 = hot start, 3 = random gauge transformation;
+ *              uniform(w) = ((w >> 9) + 0.5) * 2^-23 from the top 23 bits;
+ *              the direction of the new link uses the 9 low bits of the
+ *              four words of the trial-0 block: u1 from words 0,1 and u2
+ *              from words 2,3, each ((hi9 << 9 | lo9) + 0.5) * 2^-18
  */
 #include <complex.h>
 #include <math.h>
@@ -77,14 +80,29 @@ double or_u01(uint32_t w)
     return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
-static void draw(uint64_t seed, uint32_t c0, uint64_t sweep, uint32_t tag,
-                 uint32_t trial, double u[4])
+static void draw_words(uint64_t seed, uint32_t c0, uint64_t sweep, uint32_t tag,
+                       uint32_t trial, uint32_t w[4])
 {
     uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
     uint32_t ctr[4] = { c0, (uint32_t)sweep, (tag << 24) | trial, (uint32_t)(sweep >> 32) };
-    uint32_t w[4];
     or_philox(ctr, key, w);
+}
+
+static void draw(uint64_t seed, uint32_t c0, uint64_t sweep, uint32_t tag,
+                 uint32_t trial, double u[4])
+{
+    uint32_t w[4];
+    draw_words(seed, c0, sweep, tag, trial, w);
     for (int i = 0; i < 4; ++i) u[i] = or_u01(w[i]);
+}
+
+/* the two direction uniforms from the low 9 bits of a block's words */
+static void spare_uniforms(const uint32_t w[4], double *u1, double *u2)
+{
+    uint32_t k1 = ((w[0] & 511u) << 9) | (w[1] & 511u);
+    uint32_t k2 = ((w[2] & 511u) << 9) | (w[3] & 511u);
+    *u1 = ((double)k1 + 0.5) / 262144.0;
+    *u2 = ((double)k2 + 0.5) / 262144.0;
 }
 
 /* Box-Muller: two uniforms -> two independent standard normals */
@@ -374,10 +392,13 @@ static int update_from_staple(const mat2 *A, double beta, uint64_t seed, uint32_
     int trials = kp_delta(alpha, seed, c0, sweep, &delta);
     if (trials < 0) return -1;
 
-    draw(seed, c0, sweep, 1, 0, u);
-    double cth = 2.0 * u[0] - 1.0;
+    uint32_t w0[4];
+    double u1, u2;
+    draw_words(seed, c0, sweep, 0, 0, w0);
+    spare_uniforms(w0, &u1, &u2);
+    double cth = 2.0 * u1 - 1.0;
     double sth = sqrt((1.0 - cth) * (1.0 + cth));
-    double phi = 2.0 * M_PI * u[1];
+    double phi = 2.0 * M_PI * u2;
     double vlen = sqrt(delta * (2.0 - delta));
     double xq[4] = { 1.0 - delta, vlen * sth * cos(phi), vlen * sth * sin(phi), vlen * cth };
 

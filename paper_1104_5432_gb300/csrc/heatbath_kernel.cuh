@@ -14,8 +14,9 @@
 // Per link: 18 neighbour loads (7 distinct links per update on average over
 // the phase: V/2 opposite-parity U_mu plus 3V other-direction links for V/2
 // updates), 12 quaternion products, the Kennedy-Pendleton draw of
-// delta = 1 - a0 (one Philox block per trial), the direction (one Philox
-// block), U = X A^dagger / k, renormalisation, one store.
+// delta = 1 - a0 (one Philox block per trial; the direction comes from the
+// 9 spare low bits of the four words of the first trial's block),
+// U = X A^dagger / k, renormalisation, one store.
 //
 // The mean plaquette after the sweep is fused in: in phase (mu, 1) with
 // mu >= 1 the plane-nu part S_nu of the staple (nu < mu) closes exactly the
@@ -67,16 +68,18 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 
     if (active) {
         const EoSite s(D, i, p);
-        const uint32_t e_pmu = s.nb(MU, +1);
+        int hp[4], hm[4];
+        s.hops(hp, hm);
+        const uint32_t e_pmu = i + hp[MU];
 
         Quat<T> A = {T(0), T(0), T(0), T(0)};
         Quat<T> Sp[MU > 0 ? MU : 1];
 #pragma unroll
         for (int nu = 0; nu < 4; ++nu) {
             if (nu == MU) continue;
-            const uint32_t e_pnu = s.nb(nu, +1);
-            const uint32_t e_mnu = s.nb(nu, -1);
-            const uint32_t e_pmu_mnu = s.nb(MU, +1, nu, -1);
+            const uint32_t e_pnu = i + hp[nu];
+            const uint32_t e_mnu = i + hm[nu];
+            const uint32_t e_pmu_mnu = i + hp[MU] + hm[nu];
             const Quat<T> a = U.load(nu, q, e_pmu);      // U_nu(x+mu)
             const Quat<T> b = U.load(MU, q, e_pnu);      // U_mu(x+nu)
             const Quat<T> c = U.load(nu, p, i);          // U_nu(x)
@@ -109,23 +112,32 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             const T inv2a = T(0.5) * rk / beta;
             T delta = T(0);
             tr = -1;
-            for (int t = 0; t < KP_CAP; ++t) {
-                const U4 w = st.draw(TAG_TRIAL, (uint32_t)t);
-                const T r1 = u01<T>(w.x), r2 = u01<T>(w.y), r3 = u01<T>(w.z), r4 = u01<T>(w.w);
+            // trial 0 also carries the direction in the low 9 bits of its words
+            U4 w = st.draw(TAG_TRIAL, 0u);
+            const uint32_t kd1 = ((w.x & 511u) << 9) | (w.y & 511u);
+            const uint32_t kd2 = ((w.z & 511u) << 9) | (w.w & 511u);
+            auto kp_try = [&](const U4& ww, T* d) -> bool {
+                const T r1 = u01<T>(ww.x), r2 = u01<T>(ww.y), r3 = u01<T>(ww.z), r4 = u01<T>(ww.w);
                 const T lam2 = -(Math<T>::ln_u01(r1) + Math<T>::cos2pi_sq(r2) *
                                  Math<T>::ln_u01(r3)) * inv2a;
-                if (r4 * r4 <= T(1) - lam2) {
-                    delta = T(2) * lam2;
-                    tr = t + 1;
-                    break;
+                *d = T(2) * lam2;
+                return r4 * r4 <= T(1) - lam2;
+            };
+            if (kp_try(w, &delta)) {
+                tr = 1;
+            } else {
+                for (int t = 1; t < KP_CAP; ++t) {
+                    if (kp_try(st.draw(TAG_TRIAL, (uint32_t)t), &delta)) {
+                        tr = t + 1;
+                        break;
+                    }
                 }
             }
             if (tr > 0) {
-                const U4 w = st.draw(TAG_DIRECTION, 0);
-                const T cth = T(2) * u01<T>(w.x) - T(1);
+                const T cth = T(2) * u18<T>(kd1) - T(1);
                 const T sth = Math<T>::sqrt_pos((T(1) - cth) * (T(1) + cth));
                 T sph, cph;
-                Math<T>::sincos2pi(u01<T>(w.y), &sph, &cph);
+                Math<T>::sincos2pi(u18<T>(kd2), &sph, &cph);
                 const T vl = Math<T>::sqrt_pos(delta * (T(2) - delta));
                 const Quat<T> X = {T(1) - delta, vl * sth * cph, vl * sth * sph, vl * cth};
                 un = qnormalise(qmul_nd(X, A));

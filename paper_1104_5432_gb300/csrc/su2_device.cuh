@@ -10,7 +10,8 @@
 //     parity (x+y+z+t) & 1, index inside one parity eo = lex >> 1;
 //   * the random stream of link (lex, mu) in sweep s is Philox4x32-10 with
 //     key (seed lo, seed hi) and counter (lex*4+mu, s lo, tag<<24 | trial,
-//     s hi); tag 0 = Kennedy-Pendleton trial, 1 = direction / Haar draw,
+//     s hi); tag 0 = Kennedy-Pendleton trial (its first block also feeds
+//     the direction through the 9 low bits of each word), 1 = Haar draw,
 //     2 = hot start, 3 = random gauge transformation.  The stream therefore
 //     never depends on launch shape, batch position or graph replay.
 #pragma once
@@ -133,6 +134,19 @@ __device__ __forceinline__ double u01d(uint32_t w)
 {
     return (double)(w >> 9) * 1.1920928955078125e-7 + 5.9604644775390625e-8;
 }
+// uniform in (0,1) from an 18-bit integer k: (k + 0.5) 2^-18, exact
+__device__ __forceinline__ float u18f(uint32_t k)
+{
+    return __int_as_float((int)(0x3F800000u | (k << 5))) - 0.9999980926513671875f;
+}
+__device__ __forceinline__ double u18d(uint32_t k)
+{
+    return (double)k * 3.814697265625e-6 + 1.9073486328125e-6;
+}
+template <typename T> __device__ __forceinline__ T u18(uint32_t k);
+template <> __device__ __forceinline__ float u18<float>(uint32_t k) { return u18f(k); }
+template <> __device__ __forceinline__ double u18<double>(uint32_t k) { return u18d(k); }
+
 template <typename T> __device__ __forceinline__ T u01(uint32_t w);
 template <> __device__ __forceinline__ float u01<float>(uint32_t w) { return u01f(w); }
 template <> __device__ __forceinline__ double u01<double>(uint32_t w) { return u01d(w); }

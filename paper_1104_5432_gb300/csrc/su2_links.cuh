@@ -101,6 +101,23 @@ struct EoSite {
         return EoSite(d, lex >> 1, p);
     }
 
+    // eo offsets of x + e_d (plus) and x - e_d (minus), wrap included
+    __device__ __forceinline__ void hops(int* plus, int* minus) const
+    {
+        const int b = c[0] & 1;
+        const int nh = (int)Nh;
+        plus[0] = b ? (c[0] == Ns - 1 ? 1 - nh : 1) : 0;
+        minus[0] = b ? 0 : (c[0] == 0 ? nh - 1 : -1);
+        int st = nh;
+#pragma unroll
+        for (int d = 1; d < 4; ++d) {
+            const int L = d == 3 ? Nt : Ns;
+            plus[d] = c[d] == L - 1 ? -(L - 1) * st : st;
+            minus[d] = c[d] == 0 ? (L - 1) * st : -st;
+            st *= Ns;
+        }
+    }
+
     __device__ __forceinline__ uint32_t lex() const { return (uint32_t)c[0] + (uint32_t)Ns * r; }
 
     __device__ __forceinline__ int extent(int d) const { return d == 3 ? Nt : Ns; }

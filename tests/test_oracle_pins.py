@@ -298,6 +298,10 @@ def test_update_from_staple_conditional_law():
     u = vec / np.linalg.norm(vec, axis=1, keepdims=True)
     assert np.all(np.abs(u.mean(0)) < 5 * np.sqrt(1 / 3 / n))
     assert np.all(np.abs((u ** 2).mean(0) - 1 / 3) < 5 * np.sqrt(4 / 45 / n))
+    # the direction is independent of a0 (it comes from other random bits)
+    for comp in (u, u ** 2):
+        for i in range(3):
+            assert abs(np.corrcoef(a0, comp[:, i])[0, 1]) < 5 / np.sqrt(n)
 
 
 def test_update_degenerate_cases():

@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-arms", action="store_true", help="skip the FP64 and batched arms")
+    ap.add_argument("--profile-case", choices=["f32_64", "f32_128", "f64_64"],
+                    help="run only a few sweeps of one lattice (for ncu captures) and exit")
+    ap.add_argument("--launch-shape", type=int, default=None,
+                    help="phase-kernel launch shape index instead of autotuning")
     return ap.parse_args()
 
 
@@ -122,6 +126,19 @@ def peaks():
         return 6800.0, "fallback"
 
 
+PHASE_SOURCES = ("heatbath_kernel.cuh", "su2_links.cuh", "su2_math.cuh", "su2_device.cuh",
+                 "su2_internal.h")
+
+
+def phase_kernel_hash():
+    """Hash of the sources the phase kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in PHASE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1104_5432_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def recorded_traffic(kernel_key):
     """DRAM bytes per launch from the committed ncu summary, or None when the
     kernel source changed since the counters were taken."""
@@ -131,8 +148,7 @@ def recorded_traffic(kernel_key):
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_1104_5432_gb300", "csrc", "heatbath.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = phase_kernel_hash()
     ent = rec.get(kernel_key)
     if not ent or ent.get("source_sha256_16") != h:
         return None
@@ -183,7 +199,11 @@ def gpu_arm(args, rank, world, local):
 
     # ---- main arm: FP32, inputs resident in HBM --------------------------------
     lat = su2.Lattice(Ns, Nt, su2.F32)
-    tuned = {"fp32": lat.autotune()}  # launch shape chosen by measurement
+    if args.launch_shape is None:
+        tuned = {"fp32": lat.autotune()}  # launch shape chosen by measurement
+    else:
+        lat.set_launch_config(args.launch_shape)
+        tuned = {"fp32": args.launch_shape}
     plaq_dev = torch.zeros(sweeps, dtype=torch.float64, device="cuda")
 
     def step_f32():
@@ -334,6 +354,24 @@ def gpu_arm(args, rank, world, local):
             "lattices_per_rank": len(share)}
         S.close()
         torch.cuda.empty_cache()
+        # ---- FP32 128^4 (16 GiB of links) -----------------------------------------
+        big = su2.Lattice(128, 128, su2.F32)
+        tuned["fp32_128^4"] = big.autotune()
+        sw_big = 5
+        pl_big = torch.zeros(sw_big, dtype=torch.float64, device="cuda")
+
+        def step_big():
+            big.init(su2.HOT, seed_init)
+            big.heatbath(w["beta"], sw_big, seed_hb, plaq=pl_big)
+
+        tbig = time_steps(step_big, 2, 1)
+        big.sync()
+        arms["fp32_128^4"] = {"value": world * 4 * 128 ** 4 * sw_big * 2 / tbig, "unit": UNIT,
+                              "workload": "SU(2) 128^4, beta=2.5, hot start, 5 sweeps + "
+                                          "plaquette per sweep per step, FP32 links (16 GiB)",
+                              "ms_per_sweep": tbig / (2 * sw_big) * 1e3}
+        big.close()
+        torch.cuda.empty_cache()
         if "fp64_plain" in arms:
             arms["fp32_over_fp64_plain"] = value / arms["fp64_plain"]["value"]
 
@@ -408,8 +446,30 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    """Init + 3 sweeps (fused plaquette) of one lattice, fixed launch shape:
+    the kernels the profiles/ summaries are captured on."""
+    import torch
+
+    from paper_1104_5432_gb300 import su2
+
+    Ns, dt = {"f32_64": (64, su2.F32), "f32_128": (128, su2.F32), "f64_64": (64, su2.F64)}[
+        args.profile_case]
+    lat = su2.Lattice(Ns, Ns, dt)
+    lat.set_launch_config(args.launch_shape or 0)
+    lat.init(su2.HOT, WORKLOAD["init_seed"])
+    pl = torch.zeros(3, dtype=torch.float64, device="cuda")
+    lat.heatbath(WORKLOAD["beta"], 3, WORKLOAD["hb_seed"], plaq=pl)
+    lat.sync()
+    print(json.dumps({"profile_case": args.profile_case, "launch_shape": lat.launch_config(),
+                      "plaquette": pl.cpu().tolist()}))
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args)
+        return
     rank, world, local = dist_env()
     if args.impl == "reference":
         reference_arm(args, rank, world)

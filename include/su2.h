@@ -203,9 +203,11 @@ int su2_set_sweep(su2_lattice* lat, int l, uint64_t sweep);
 /* ------------------------------------------------------------------ */
 
 /* Number of launch shapes (threads per block, minimum resident blocks per
- * SM) compiled for the phase kernel; shape 0 is the default.  Results never
- * depend on the shape (the random streams are keyed by link and sweep). */
-#define SU2_NUM_LAUNCH_CONFIGS 4
+ * SM, plain or y-slab traversal of the lattice) compiled for the phase
+ * kernel; shape 0 is the default, shapes 4..7 walk large FP32 lattices in
+ * y slabs so the +-t neighbours stay in L2.  Results never depend on the
+ * shape (the random streams are keyed by link and sweep). */
+#define SU2_NUM_LAUNCH_CONFIGS 8
 
 /* Times every launch shape on this handle's lattices (whole sweeps with the
  * fused plaquette, replayed as in su2_heatbath, ~20 ms per shape in each of
@@ -228,6 +230,11 @@ int su2_get_launch_config(const su2_lattice* lat, int* cfg, int* threads, int* m
  * shapes), and a lookup (returns 1 if found, 0 if not) and append on a
  * cache file. */
 int su2_tune_key(const su2_lattice* lat, char* buf, size_t len);
+
+/* Test hook: walk every lattice in S y-slabs under the slab launch shapes
+ * (S must divide every Ns; by default S is chosen from the lattice size).
+ * Synchronous. */
+int su2_set_slabs(su2_lattice* lat, int S);
 int su2_tune_cache_lookup(const char* path, const char* key, int* cfg);
 int su2_tune_cache_store(const char* path, const char* key, int cfg, double ms);
 

@@ -3,6 +3,7 @@
 // device output handling, checkpoints and statistics.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
@@ -80,6 +81,7 @@ struct su2_lattice {
     uint32_t max_phase_blocks = 0;
     int cfg = 0;                    // active launch shape
     std::string tune_key;
+    std::vector<int> ysplit;        // y slabs per lattice (slab launch shapes)
     int rmax_limit = 0;             // rmax <= min_l Ns_l / 2
     size_t link_bytes = 0, work_bytes = 0;
     size_t off_status = 0, off_desc = 0, off_sstart = 0, off_spstart = 0;
@@ -250,6 +252,29 @@ int create(int n, const int* Ns, const int* Nt, int dtype, su2_lattice** out)
     layout(L);
     *out = L;
     return SU2_OK;
+}
+
+// y slabs for the large-lattice traversal: the smallest power of two
+// dividing Ns that keeps the t-neighbour window Nh (Ns/S) Ns sites x 7 link
+// loads within SLAB_WINDOW_BYTES (FP32 only; 1 = plain order)
+int slab_rule(const su2_lattice* L, int l)
+{
+    if (L->dtype != SU2_F32) return 1;
+    const double link = 16.0;
+    const double Ns = L->Ns[l];
+    int S = 1;
+    while ((L->Ns[l] % (2 * S)) == 0 &&
+           (Ns / 2) * (Ns / S) * Ns * 7.0 * link > SLAB_WINDOW_BYTES)
+        S *= 2;
+    return S;
+}
+
+void set_slabs(LatDesc& D, int S)
+{
+    D.ysplit = S;
+    D.Ny = D.Ns / S;
+    D.div_ny = make_fastdiv((uint32_t)D.Ny);
+    D.div_nt = make_fastdiv((uint32_t)D.Nt);
 }
 
 // per-lattice parameters for the next sweeps; plaq_out[l] may be null
@@ -539,6 +564,7 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
     lat->device = dev;
 
     std::vector<LatDesc> d(lat->n);
+    lat->ysplit.assign(lat->n, 1);
     for (int l = 0; l < lat->n; ++l) {
         LatDesc& D = d[l];
         memset(&D, 0, sizeof D);
@@ -550,6 +576,8 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
         D.Vh = (uint32_t)(lat->V[l] / 2);
         D.div_nh = make_fastdiv((uint32_t)D.Nh);
         D.div_ns = make_fastdiv((uint32_t)D.Ns);
+        set_slabs(D, slab_rule(lat, l));
+        lat->ysplit[l] = D.ysplit;
         D.link_off = lat->link_off[l];
         D.field_off = lat->field_off[l];
     }
@@ -842,7 +870,11 @@ int su2_autotune(su2_lattice* lat, int* chosen)
         if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
         return e == cudaSuccess ? SU2_OK : cuda_fail(e, "autotune timing");
     };
-    for (int k = 0; k < NUM_LAUNCH_CFG && rc == SU2_OK; ++k) {
+    // slab shapes only matter when some lattice is walked in slabs
+    bool any_slab = false;
+    for (int l = 0; l < lat->n; ++l) any_slab = any_slab || lat->ysplit[l] > 1;
+    const int ncand = any_slab ? NUM_LAUNCH_CFG : NUM_LAUNCH_CFG / 2;
+    for (int k = 0; k < ncand && rc == SU2_OK; ++k) {
         float ms = 0.f;
         rc = time_sweeps(k, 1, &ms);  // builds the graph, warms up
         if (rc == SU2_OK) rc = time_sweeps(k, 1, &ms);
@@ -851,7 +883,7 @@ int su2_autotune(su2_lattice* lat, int* chosen)
         best_ms[k] = 1e300;
     }
     for (int round = 0; round < 3 && rc == SU2_OK; ++round)
-        for (int k = 0; k < NUM_LAUNCH_CFG && rc == SU2_OK; ++k) {
+        for (int k = 0; k < ncand && rc == SU2_OK; ++k) {
             float ms = 0.f;
             rc = time_sweeps(k, reps[k], &ms);
             best_ms[k] = std::min(best_ms[k], (double)ms / reps[k]);
@@ -861,7 +893,7 @@ int su2_autotune(su2_lattice* lat, int* chosen)
     lat->cfg = saved;
     if (rc != SU2_OK) return rc;
     int best = 0;
-    for (int k = 1; k < NUM_LAUNCH_CFG; ++k)
+    for (int k = 1; k < ncand; ++k)
         if (best_ms[k] < best_ms[best]) best = k;
     // leave the handle as su2_init(SU2_HOT) with the tuning seed would
     for (int l = 0; l < lat->n; ++l)
@@ -890,6 +922,28 @@ int su2_get_launch_config(const su2_lattice* lat, int* cfg, int* threads, int* m
     if (cfg) *cfg = lat->cfg;
     if (threads) *threads = LAUNCH_CFG[lat->dtype][lat->cfg].threads;
     if (min_blocks) *min_blocks = LAUNCH_CFG[lat->dtype][lat->cfg].min_blocks;
+    return SU2_OK;
+}
+
+int su2_set_slabs(su2_lattice* lat, int S)
+{
+    if (int rc = check_handle(lat)) return rc;
+    if (S < 1) return fail(SU2_E_INVAL, "slab count must be >= 1");
+    for (int l = 0; l < lat->n; ++l)
+        if (lat->Ns[l] % S) return fail(SU2_E_INVAL, "lattice %d: Ns=%d not divisible by %d", l,
+                                        lat->Ns[l], S);
+    DeviceGuard dg(lat->device);
+    SU2_CUDA(cudaStreamSynchronize(lat->stream));
+    for (int l = 0; l < lat->n; ++l) {
+        LatDesc D;
+        SU2_CUDA(cudaMemcpy(&D, lat->desc_dev(l), sizeof D, cudaMemcpyDeviceToHost));
+        set_slabs(D, S);
+        const size_t off = offsetof(LatDesc, ysplit);
+        const size_t len = offsetof(LatDesc, div_nt) + sizeof(FastDiv) - off;
+        SU2_CUDA(cudaMemcpy(reinterpret_cast<char*>(lat->desc_dev(l)) + off,
+                            reinterpret_cast<const char*>(&D) + off, len, cudaMemcpyHostToDevice));
+        lat->ysplit[l] = S;
+    }
     return SU2_OK;
 }
 

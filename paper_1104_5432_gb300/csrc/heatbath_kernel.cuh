@@ -49,7 +49,7 @@ __device__ __forceinline__ T warp_sum_t(T v)
     return v;
 }
 
-template <typename T, int MU, bool PLAQ, bool DBG, int NT, int MINB>
+template <typename T, int MU, bool PLAQ, bool DBG, int NT, int MINB, bool SLAB>
 __global__ void __launch_bounds__(NT, MINB)
 hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 {
@@ -57,8 +57,8 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const LatDesc& D = ctx.desc[l];
     const uint32_t Vh = D.Vh;
     const uint32_t blk0 = __ldg(ctx.phase_start + l);
-    const uint32_t i = (blockIdx.x - blk0) * NT + threadIdx.x;
-    const bool active = i < Vh;
+    const uint32_t j = (blockIdx.x - blk0) * NT + threadIdx.x;  // traversal position
+    const bool active = j < Vh;
     const Links<T> U(ctx.links, D);
     const int q = p ^ 1;
 
@@ -67,7 +67,8 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     bool ncap = false;
 
     if (active) {
-        const EoSite s(D, i, p);
+        uint32_t i = j;  // storage index of the site
+        const EoSite s = SLAB ? EoSite::from_slab(D, j, p, &i) : EoSite(D, j, p);
         int hp[4], hm[4];
         s.hops(hp, hm);
         const uint32_t e_pmu = i + hp[MU];
@@ -184,7 +185,7 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 
 // One launch shape (NT threads per block, at least MINB blocks per SM) of
 // the phase kernel; the grid covers ctx.phase_blocks blocks of NT links.
-template <typename T, int NT, int MINB>
+template <typename T, int NT, int MINB, bool SLAB>
 cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int32_t* dbg,
                                cudaStream_t s)
 {
@@ -193,9 +194,9 @@ cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int3
     const dim3 grid(c.phase_blocks), block(NT);
 #define SU2_LAUNCH(MUV)                                                                          \
     do {                                                                                         \
-        if (dbg) hb_phase_kernel<T, MUV, false, true, NT, MINB><<<grid, block, 0, s>>>(c, parity, dbg); \
-        else if (pl) hb_phase_kernel<T, MUV, (MUV > 0), false, NT, MINB><<<grid, block, 0, s>>>(c, parity, dbg); \
-        else hb_phase_kernel<T, MUV, false, false, NT, MINB><<<grid, block, 0, s>>>(c, parity, dbg); \
+        if (dbg) hb_phase_kernel<T, MUV, false, true, NT, MINB, SLAB><<<grid, block, 0, s>>>(c, parity, dbg); \
+        else if (pl) hb_phase_kernel<T, MUV, (MUV > 0), false, NT, MINB, SLAB><<<grid, block, 0, s>>>(c, parity, dbg); \
+        else hb_phase_kernel<T, MUV, false, false, NT, MINB, SLAB><<<grid, block, 0, s>>>(c, parity, dbg); \
     } while (0)
     switch (mu) {
     case 0: SU2_LAUNCH(0); break;

@@ -24,14 +24,22 @@ constexpr int TPB = 256;            // threads per block of the non-phase kernel
 // Launch shapes of the phase kernel the autotuner chooses from (threads per
 // block, minimum resident blocks per SM); entry 0 is the default.  Row 0:
 // FP32, row 1: FP64.
+// slab: walk large lattices in y slabs (EoSite::from_slab) -- FP32 only,
+// since the FP64 kernel is bound by its arithmetic, not by re-reads.
 struct LaunchCfg {
     int threads, min_blocks;
+    bool slab;
 };
-constexpr int NUM_LAUNCH_CFG = 4;
+constexpr int NUM_LAUNCH_CFG = 8;
 constexpr LaunchCfg LAUNCH_CFG[2][NUM_LAUNCH_CFG] = {
-    {{256, 4}, {256, 3}, {128, 8}, {512, 2}},
-    {{256, 1}, {256, 2}, {128, 4}, {128, 1}},
+    {{256, 4, false}, {256, 3, false}, {128, 8, false}, {512, 2, false},
+     {256, 4, true}, {256, 3, true}, {128, 8, true}, {512, 2, true}},
+    {{256, 1, false}, {256, 2, false}, {128, 4, false}, {128, 1, false},
+     {256, 1, false}, {256, 2, false}, {128, 4, false}, {128, 1, false}},
 };
+// largest y-slab window (sites between a site and its t neighbour, times
+// the bytes a site's update touches) kept in L2
+constexpr double SLAB_WINDOW_BYTES = 32.0 * (1 << 20);
 
 constexpr int KP_CAP = 4096;        // Kennedy-Pendleton trial cap
 constexpr int PLAQ_RING = 4096;     // per-lattice plaquette slots for host output
@@ -48,6 +56,8 @@ struct LatDesc {
     int32_t Ns, Nt, Nh, Vs;
     uint32_t V, Vh;
     FastDiv div_nh, div_ns;
+    int32_t ysplit, Ny;     // y slabs of the large-lattice traversal, Ny = Ns / ysplit
+    FastDiv div_ny, div_nt;
     uint64_t link_off;      // byte offset of this lattice in the link buffer
     uint64_t field_off;     // double offset of its Polyakov field
     // per call

@@ -87,6 +87,27 @@ struct EoSite {
         c[0] = (int)(2 * xh) + ((p + c[1] + c[2] + c[3]) & 1);
     }
 
+    // The site visited at traversal position j of a phase when the lattice is
+    // walked in d.ysplit slabs of y (slab outermost, then t, z, y inside the
+    // slab, x fastest).  Slabs keep the +-t neighbours of the sites in
+    // flight within a window of Nh (Ns/ysplit) Ns sites, so that window
+    // stays in L2 on large lattices.  *eo gets the storage index.
+    __device__ __forceinline__ static EoSite from_slab(const LatDesc& d, uint32_t j, int p,
+                                                       uint32_t* eo)
+    {
+        const uint32_t r = fdiv(j, d.div_nh);
+        const uint32_t xh = j - r * (uint32_t)d.Nh;
+        const uint32_t r2 = fdiv(r, d.div_ny);
+        const uint32_t yl = r - r2 * (uint32_t)d.Ny;
+        const uint32_t r3 = fdiv(r2, d.div_ns);
+        const uint32_t z = r2 - r3 * (uint32_t)d.Ns;
+        const uint32_t ys = fdiv(r3, d.div_nt);
+        const uint32_t t = r3 - ys * (uint32_t)d.Nt;
+        const uint32_t y = ys * (uint32_t)d.Ny + yl;
+        *eo = xh + (uint32_t)d.Nh * (y + (uint32_t)d.Ns * (z + (uint32_t)d.Ns * t));
+        return EoSite(d, *eo, p);
+    }
+
     // the site with lexicographic index lex (any parity); *parity gets its parity
     __device__ __forceinline__ static EoSite from_lex(const LatDesc& d, uint32_t lex, int* parity)
     {

@@ -1,9 +1,11 @@
 """Launch shapes compiled into the phase kernel (mirror of the table in
 csrc/su2_internal.h), for reporting which one the autotuner chose."""
 
-_F32 = [(256, 4), (256, 3), (128, 8), (512, 2)]
-_F64 = [(256, 1), (256, 2), (128, 4), (128, 1)]
+_F32 = [(256, 4, False), (256, 3, False), (128, 8, False), (512, 2, False),
+        (256, 4, True), (256, 3, True), (128, 8, True), (512, 2, True)]
+_F64 = [(256, 1, False), (256, 2, False), (128, 4, False), (128, 1, False)] * 2
 
 
 def launch_shapes(fp64: bool):
-    return [f"{t} threads, >= {m} blocks/SM" for t, m in (_F64 if fp64 else _F32)]
+    return [f"{t} threads, >= {m} blocks/SM" + (", y-slab traversal" if s else "")
+            for t, m, s in (_F64 if fp64 else _F32)]

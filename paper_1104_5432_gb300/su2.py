@@ -85,6 +85,7 @@ def load(build_if_needed: bool = True):
             "su2_tune_key": (i, [P, C.c_char_p, sz]),
             "su2_tune_cache_lookup": (i, [C.c_char_p, C.c_char_p, P]),
             "su2_tune_cache_store": (i, [C.c_char_p, C.c_char_p, i, d]),
+            "su2_set_slabs": (i, [P, i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -284,6 +285,10 @@ class Lattice:
 
     def set_launch_config(self, cfg: int):
         _check(load().su2_set_launch_config(self._h, int(cfg)))
+
+    def set_slabs(self, S: int):
+        """Walk the lattices in S y-slabs under the slab launch shapes."""
+        _check(load().su2_set_slabs(self._h, int(S)))
 
     def launch_config(self):
         c, t, m = C.c_int(), C.c_int(), C.c_int()

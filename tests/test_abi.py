@@ -111,7 +111,7 @@ def test_tune_key_and_launch_config_host_side():
     assert lib.su2_set_launch_config(h, 2) == 0
     assert lib.su2_get_launch_config(h, C.byref(cfg), C.byref(thr), C.byref(mb)) == 0
     assert (cfg.value, thr.value, mb.value) == (2, 128, 8)
-    assert lib.su2_set_launch_config(h, 4) == su2.SU2_E_INVAL
+    assert lib.su2_set_launch_config(h, 8) == su2.SU2_E_INVAL
     lib.su2_lattice_destroy(h)
 
 
@@ -121,7 +121,7 @@ def test_launch_shape_mirror_matches_library():
     for dtype, table in ((su2.F32, _F32), (su2.F64, _F64)):
         h = C.c_void_p()
         assert lib.su2_lattice_create(4, 4, dtype, C.byref(h)) == 0
-        for k, (t, m) in enumerate(table):
+        for k, (t, m, _) in enumerate(table):
             assert lib.su2_set_launch_config(h, k) == 0
             cfg, thr, mb = C.c_int(), C.c_int(), C.c_int()
             lib.su2_get_launch_config(h, C.byref(cfg), C.byref(thr), C.byref(mb))

@@ -374,12 +374,13 @@ def test_every_launch_shape_gives_identical_results(dtype):
     """The random streams are keyed by link and sweep, never by thread: each
     launch shape the autotuner may pick produces the same links bit for
     bit (batch of uneven lattices, two sweeps)."""
-    shapes = [(6, 4), (8, 6), (4, 2)]
+    shapes = [(8, 4), (8, 6), (4, 2)]
     seeds, betas = [7, 8, 9], [2.3, 2.5, 1.9]
     ref_links = ref_plaq = None
-    for cfg in range(4):
+    for cfg, slabs in [(k, 1) for k in range(8)] + [(4, 2), (6, 4), (5, 2)]:
         B = su2.Lattice([s[0] for s in shapes], [s[1] for s in shapes], dtype)
         B.set_launch_config(cfg)
+        B.set_slabs(slabs)  # slab shapes walk y in `slabs` slabs (FP32)
         assert B.launch_config()[0] == cfg
         B.batch_init(su2.HOT, seeds)
         plaq = B.batch_heatbath(betas, 2, seeds)
@@ -389,7 +390,12 @@ def test_every_launch_shape_gives_identical_results(dtype):
             continue
         for a, b in zip(links, ref_links):
             np.testing.assert_array_equal(a, b)
-        np.testing.assert_allclose(plaq, ref_plaq, rtol=1e-13, atol=0)
+        # the chain is identical; the plaquette sums its FP32 products in a
+        # shape-dependent grouping: FP64 to 1e-13, FP32 to its 1e-6 budget
+        if dtype == su2.F64:
+            np.testing.assert_allclose(plaq, ref_plaq, rtol=1e-13, atol=0)
+        else:
+            np.testing.assert_allclose(plaq, ref_plaq, rtol=0, atol=1e-6)
 
 
 def test_autotune_and_cache(tmp_path, monkeypatch):
@@ -407,3 +413,28 @@ def test_autotune_and_cache(tmp_path, monkeypatch):
     # a new handle of the same shape on this GPU starts with the cached shape
     again = su2.Lattice(16, 16, su2.F32)
     assert again.launch_config()[0] == chosen
+
+
+def test_full_size_128_properties():
+    """128^4 FP32 (16 GiB of links): one replayed sweep; properties that hold
+    at any size: every link a unit quaternion, fused plaquette equals the
+    stand-alone one, every link updated, no cap hit, sweep counter 1."""
+    lat = lattice(128, 128, su2.F32)
+    lat.init(su2.HOT, 3)
+    plaq = lat.heatbath(2.5, 1, 3)
+    st = lat.stats()
+    assert st["updates"] == 4 * 128 ** 4 and st["cap_hits"] == 0
+    assert abs(plaq[0, 0] - lat.plaquette()[0]) <= 1e-6
+    assert 0.3 < plaq[0, 0] < 0.5  # one sweep from a hot start at beta = 2.5
+    assert lat.get_sweep() == 1
+    # every link a unit quaternion (canonical FP64 copy kept on the device)
+    dev = torch.empty((128 ** 4, 4, 4), dtype=torch.float64, device="cuda")
+    lat.get_links(out=dev)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for chunk in dev.split(1 << 26):
+        worst = max(worst, float((chunk.norm(dim=2) - 1).abs().max()))
+    assert worst <= 5e-7, worst
+    del dev
+    lat.close()
+    torch.cuda.empty_cache()

@@ -139,9 +139,9 @@ def phase_kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
+def recorded_traffic(kernel_key, field="dram_bytes_per_launch_full_size"):
+    """A figure from the committed ncu summary (DRAM bytes per launch by
+    default), or None when the kernel source changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "heatbath_phase_traffic.json")
     try:
         with open(path) as f:
@@ -152,7 +152,7 @@ def recorded_traffic(kernel_key):
     ent = rec.get(kernel_key)
     if not ent or ent.get("source_sha256_16") != h:
         return None
-    return ent.get("dram_bytes_per_launch_full_size")
+    return ent.get(field)
 
 
 def gpu_arm(args, rank, world, local):
@@ -288,7 +288,11 @@ def gpu_arm(args, rank, world, local):
 
         t64 = time_steps(step_f64, 2, 1)
         lat64.sync()
+        busy = recorded_traffic("f64_64^4", "fp64_pipe_active_pct")
         arms["fp64_plain"] = {"value": world * 4 * V * sw64 * 2 / t64, "unit": UNIT,
+                              "roofline": {"bound": "alu", "unit": "FP64 pipe busy (ncu)",
+                                           "frac": None if busy is None else busy / 100,
+                                           "note": "bound by GB300's FP64 pipe; memory < 3%"},
                               "workload": workload_name("FP64 throughout").replace(
                                   f"{sweeps} checkerboard", f"{sw64} checkerboard"),
                               "ms_per_sweep": t64 / (2 * sw64) * 1e3}
@@ -369,6 +373,8 @@ def gpu_arm(args, rank, world, local):
         arms["fp32_128^4"] = {"value": world * 4 * 128 ** 4 * sw_big * 2 / tbig, "unit": UNIT,
                               "workload": "SU(2) 128^4, beta=2.5, hot start, 5 sweeps + "
                                           "plaquette per sweep per step, FP32 links (16 GiB)",
+                              "traffic_per_launch_slab": recorded_traffic("f32_128^4_slab"),
+                              "algorithmic_bytes_per_launch": 128 * 128 ** 4 // 2,
                               "ms_per_sweep": tbig / (2 * sw_big) * 1e3}
         big.close()
         torch.cuda.empty_cache()

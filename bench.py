@@ -358,6 +358,31 @@ def gpu_arm(args, rank, world, local):
             "lattices_per_rank": len(share)}
         S.close()
         torch.cuda.empty_cache()
+        # ---- the smaller configurations of the paper's benchmark shape -------------
+        def small_arm(name, Nsm, dtype, beta, seed, nsw=100, K=3):
+            L = su2.Lattice(Nsm, Nsm, dtype)
+            tuned[name] = L.autotune()
+            pl = torch.zeros(nsw, dtype=torch.float64, device="cuda")
+
+            def step():
+                L.init(su2.HOT, seed + 1000003 * rank)
+                L.heatbath(beta, nsw, seed + 1000003 * rank, plaq=pl)
+
+            tt = time_steps(step, K, 1)
+            L.sync()
+            arms[name] = {"value": world * 4 * Nsm ** 4 * nsw * K / tt, "unit": UNIT,
+                          "workload": f"SU(2) {Nsm}^4, beta={beta}, hot start seed {seed}, "
+                                      f"{nsw} sweeps + plaquette per sweep, "
+                                      f"{'FP32 links' if dtype == su2.F32 else 'FP64'}",
+                          "ms_per_step": tt / K * 1e3,
+                          "plaquette_last_sweep": float(pl[-1].item())}
+            L.close()
+
+        small_arm("fp64_8^4_beta2.3", 8, su2.F64, 2.3, 1)
+        small_arm("fp32_32^4_beta6.0", 32, su2.F32, 6.0, 2)
+        small_arm("fp64_32^4_beta6.0", 32, su2.F64, 6.0, 2, K=2)
+        torch.cuda.empty_cache()
+
         # ---- FP32 128^4 (16 GiB of links) -----------------------------------------
         big = su2.Lattice(128, 128, su2.F32)
         tuned["fp32_128^4"] = big.autotune()

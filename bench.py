@@ -433,7 +433,7 @@ def oracle_sample(n_phases, links=None):
     for i in range(n_phases):
         mu, p = (i // 2) % 4, i % 2
         lib.or_heatbath_phase(Ns, Nt, links.ctypes.data_as(C.c_void_p), w["beta"], mu, p,
-                              w["hb_seed"], 0, 0, None, cnt.ctypes.data_as(C.c_void_p))
+                              w["hb_seed"], 0, 0, 0.0, None, cnt.ctypes.data_as(C.c_void_p))
     dt = time.perf_counter() - t0
     return float(cnt[1]) / dt, int(cnt[1]), dt, links
 

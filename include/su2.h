@@ -149,6 +149,15 @@ int su2_batch_heatbath_measure(su2_lattice* lat, const double* betas, int nsweep
                                const uint64_t* seeds, double* plaq, int rmax, double* poly_sum,
                                double* corr_sum);
 
+/* Heat-bath sampler of every lattice of the handle: links whose
+ * alpha = beta k is below creutz_below are drawn with Creutz's method
+ * (a0 from exp(alpha a0) by inversion, accepted with sqrt(1 - a0^2);
+ * acceptance ~pi/4 as alpha -> 0), the others with Kennedy-Pendleton's
+ * (acceptance -> 1 as alpha grows).  0 (the default) = Kennedy-Pendleton
+ * everywhere; ~1.7 is where their acceptances cross.  Both use the same
+ * Philox blocks (Creutz: words 0 and 3 of trial t).  Synchronous. */
+int su2_set_sampler(su2_lattice* lat, double creutz_below);
+
 /* One checkerboard phase (mu in 0..3, parity 0/1) of every lattice at the
  * current sweep counter, which does NOT advance (the unit the sweep is
  * made of; for testing).  trials (nullable, device int32[V], n == 1

@@ -55,13 +55,13 @@ def lib():
             L.or_init.restype = i
             L.or_gauge_transform.argtypes = [i, i, P, u64]
             L.or_gauge_transform.restype = None
-            L.or_heatbath_phase.argtypes = [i, i, P, d, i, i, u64, u64, i, P, P]
+            L.or_heatbath_phase.argtypes = [i, i, P, d, i, i, u64, u64, i, d, P, P]
             L.or_heatbath_phase.restype = i
-            L.or_update_from_staple.argtypes = [P, d, u64, u32, u64, P]
+            L.or_update_from_staple.argtypes = [P, d, u64, u32, u64, d, P]
             L.or_update_from_staple.restype = i
-            L.or_heatbath_link.argtypes = [i, i, P, d, i, C.c_long, u64, u64, P]
+            L.or_heatbath_link.argtypes = [i, i, P, d, i, C.c_long, u64, u64, d, P]
             L.or_heatbath_link.restype = i
-            L.or_kp_samples.argtypes = [d, u64, u64, C.c_long, P, P]
+            L.or_kp_samples.argtypes = [d, u64, u64, C.c_long, i, P, P]
             L.or_kp_samples.restype = None
             L.or_plaquette.argtypes = [i, i, P]
             L.or_plaquette.restype = d
@@ -73,7 +73,7 @@ def lib():
             L.or_polyakov.restype = d
             L.or_correlator.argtypes = [i, i, P, i, P]
             L.or_correlator.restype = i
-            L.or_heatbath.argtypes = [i, i, P, d, i, u64, u64, P, P]
+            L.or_heatbath.argtypes = [i, i, P, d, i, u64, u64, d, P, P]
             L.or_heatbath.restype = i
             _lib = L
     return _lib
@@ -119,47 +119,51 @@ def gauge_transform(Ns: int, Nt: int, links: np.ndarray, seed: int) -> np.ndarra
     return out
 
 
-def heatbath_phase(Ns, Nt, links, beta, mu, parity, seed, sweep, reverse=False):
+def heatbath_phase(Ns, Nt, links, beta, mu, parity, seed, sweep, reverse=False, creutz_below=0.0):
     """Returns (new links, per-link trials [V,4] (-2 = not in phase), counters)."""
     out = np.array(links, dtype=np.float64, order="C", copy=True)
     _check_links(out, Ns, Nt)
     trials = np.full((volume(Ns, Nt), 4), -2, np.int32)
     counters = np.zeros(3, np.uint64)
     lib().or_heatbath_phase(Ns, Nt, _ptr(out), float(beta), mu, parity, seed, sweep,
-                            1 if reverse else 0, _ptr(trials), _ptr(counters))
+                            1 if reverse else 0, float(creutz_below), _ptr(trials),
+                            _ptr(counters))
     return out, trials, counters
 
 
-def heatbath(Ns, Nt, links, beta, nsweeps, seed, sweep0=0):
+def heatbath(Ns, Nt, links, beta, nsweeps, seed, sweep0=0, creutz_below=0.0):
     """Returns (new links, plaquette after each sweep, counters)."""
     out = np.array(links, dtype=np.float64, order="C", copy=True)
     _check_links(out, Ns, Nt)
     plaq = np.zeros(nsweeps, np.float64)
     counters = np.zeros(3, np.uint64)
     lib().or_heatbath(Ns, Nt, _ptr(out), float(beta), int(nsweeps), seed, sweep0,
-                      _ptr(plaq), _ptr(counters))
+                      float(creutz_below), _ptr(plaq), _ptr(counters))
     return out, plaq, counters
 
 
-def update_from_staple(A, beta, seed, c0, sweep):
+def update_from_staple(A, beta, seed, c0, sweep, creutz_below=0.0):
     a = np.ascontiguousarray(np.asarray(A, np.float64))
     out = np.zeros(4, np.float64)
-    t = lib().or_update_from_staple(_ptr(a), float(beta), seed, c0, sweep, _ptr(out))
+    t = lib().or_update_from_staple(_ptr(a), float(beta), seed, c0, sweep, float(creutz_below),
+                                    _ptr(out))
     return out, t
 
 
-def heatbath_link(Ns, Nt, links, beta, mu, lex, seed, sweep):
+def heatbath_link(Ns, Nt, links, beta, mu, lex, seed, sweep, creutz_below=0.0):
     """(new link, trials) that a phase would draw for U_mu(lex) from `links`."""
     out = np.zeros(4, np.float64)
     t = lib().or_heatbath_link(Ns, Nt, _ptr(links), float(beta), mu, int(lex), seed, sweep,
-                               _ptr(out))
+                               float(creutz_below), _ptr(out))
     return out, t
 
 
-def kp_samples(alpha, seed, sweep, n):
+def kp_samples(alpha, seed, sweep, n, creutz=False):
+    """n draws of a0 (Kennedy-Pendleton, or Creutz's draw with creutz=True)."""
     a0 = np.zeros(n, np.float64)
     trials = np.zeros(n, np.int32)
-    lib().or_kp_samples(float(alpha), seed, sweep, n, _ptr(a0), _ptr(trials))
+    lib().or_kp_samples(float(alpha), seed, sweep, n, 1 if creutz else 0, _ptr(a0),
+                        _ptr(trials))
     return a0, trials
 
 

@@ -25,7 +25,8 @@
  *              parity = (x+y+z+t) mod 2
  *   layout     host links double[V][4][4]: ((lex*4+mu)*4 + component)
  *   sweep      phases (mu,parity) = (0,0),(0,1),(1,0),(1,1),...,(3,1)
- *   heat bath  Kennedy-Pendleton draw of a0 from sqrt(1-a0^2) exp(alpha a0),
+ *   heat bath  Kennedy-Pendleton draw of a0 from sqrt(1-a0^2) exp(alpha a0)
+ *              (optionally Creutz's draw below a chosen alpha),
  *              alpha = beta*k, k = sqrt(det A) for the staple sum A;
  *              new link U = X Vhat^dagger, Vhat = A/k, then normalised
  *   RNG        Philox4x32-10, key = (seed lo, seed hi), counter =
@@ -374,11 +375,34 @@ static int kp_delta(double alpha, uint64_t seed, uint32_t c0, uint64_t sweep, do
     return -1;
 }
 
+/* Creutz's draw (Phys. Rev. D21 (1980) 2308) of delta = 1 - a0 for the same
+ * density: a0 from exp(alpha a0) on [-1,1] by inversion, x = 1 - r1 (1 -
+ * exp(-2 alpha)), a0 = 1 + ln(x)/alpha, accepted when r4^2 <= 1 - a0^2 =
+ * delta (2 - delta).  Trial t uses the same Philox block as a
+ * Kennedy-Pendleton trial t (tag 0): r1 = word 0, r4 = word 3.
+ * Returns the number of trials used, or -1 after OR_KP_CAP rejections. */
+static int creutz_delta(double alpha, uint64_t seed, uint32_t c0, uint64_t sweep, double *delta)
+{
+    double q = -expm1(-2.0 * alpha);
+    for (int t = 0; t < OR_KP_CAP; ++t) {
+        double r[4];
+        draw(seed, c0, sweep, 0, (uint32_t)t, r);
+        double d = -log1p(-r[0] * q) / alpha;
+        if (r[3] * r[3] <= d * (2.0 - d)) {
+            *delta = d;
+            return t + 1;
+        }
+    }
+    return -1;
+}
+
 /* New link from the staple sum A (as a matrix).  Returns trials (>= 1),
  * 0 for the Haar draw (alpha below OR_ALPHA_HAAR), or -1 on a cap hit, in
  * which case *unew is left untouched. */
+/* creutz_below: alpha below which Creutz's draw replaces Kennedy-Pendleton's
+ * (0 = Kennedy-Pendleton everywhere) */
 static int update_from_staple(const mat2 *A, double beta, uint64_t seed, uint32_t c0,
-                              uint64_t sweep, double unew[4])
+                              uint64_t sweep, double creutz_below, double unew[4])
 {
     double k = sqrt(creal(A->e[0][0] * A->e[1][1] - A->e[0][1] * A->e[1][0]));
     double alpha = beta * k;
@@ -389,7 +413,8 @@ static int update_from_staple(const mat2 *A, double beta, uint64_t seed, uint32_
         return 0;
     }
     double delta;
-    int trials = kp_delta(alpha, seed, c0, sweep, &delta);
+    int trials = alpha < creutz_below ? creutz_delta(alpha, seed, c0, sweep, &delta)
+                                      : kp_delta(alpha, seed, c0, sweep, &delta);
     if (trials < 0) return -1;
 
     uint32_t w0[4];
@@ -421,7 +446,7 @@ static int update_from_staple(const mat2 *A, double beta, uint64_t seed, uint32_
  * draw, -1 for a cap hit; untouched for links outside the phase.
  * counters (nullable): [0] += trials, [1] += links visited, [2] += cap hits. */
 int or_heatbath_phase(int Ns, int Nt, double *links, double beta, int mu, int parity,
-                      uint64_t seed, uint64_t sweep, int reverse,
+                      uint64_t seed, uint64_t sweep, int reverse, double creutz_below,
                       int32_t *trials_out, uint64_t *counters)
 {
     geom g = mkgeom(Ns, Nt);
@@ -433,7 +458,7 @@ int or_heatbath_phase(int Ns, int Nt, double *links, double beta, int mu, int pa
         mat2 A = staple(&g, links, c, mu);
         double unew[4];
         uint32_t c0 = (uint32_t)(lex * 4 + mu);
-        int tr = update_from_staple(&A, beta, seed, c0, sweep, unew);
+        int tr = update_from_staple(&A, beta, seed, c0, sweep, creutz_below, unew);
         if (tr >= 0) store_link(links, lex, mu, unew);
         if (trials_out) trials_out[lex * 4 + mu] = tr;
         if (counters) {
@@ -449,32 +474,33 @@ int or_heatbath_phase(int Ns, int Nt, double *links, double beta, int mu, int pa
  * the configuration as given (for sampled checks on large lattices).
  * Returns trials as or_update_from_staple; unew is untouched on a cap hit. */
 int or_heatbath_link(int Ns, int Nt, const double *links, double beta, int mu, long lex,
-                     uint64_t seed, uint64_t sweep, double unew[4])
+                     uint64_t seed, uint64_t sweep, double creutz_below, double unew[4])
 {
     geom g = mkgeom(Ns, Nt);
     int c[4];
     coords_of(&g, lex, c);
     mat2 A = staple(&g, links, c, mu);
-    return update_from_staple(&A, beta, seed, (uint32_t)(lex * 4 + mu), sweep, unew);
+    return update_from_staple(&A, beta, seed, (uint32_t)(lex * 4 + mu), sweep, creutz_below, unew);
 }
 
 /* Test hook for the sampler: the link drawn by the heat-bath step for a
  * given staple quaternion A (any real multiple of an SU(2) element). */
 int or_update_from_staple(const double A[4], double beta, uint64_t seed, uint32_t c0,
-                          uint64_t sweep, double unew[4])
+                          uint64_t sweep, double creutz_below, double unew[4])
 {
     mat2 Am = m_from_quat(A);
-    return update_from_staple(&Am, beta, seed, c0, sweep, unew);
+    return update_from_staple(&Am, beta, seed, c0, sweep, creutz_below, unew);
 }
 
 /* Test hook: n KP draws of a0 = 1 - delta for a fixed alpha, drawn with
  * counter words c0 = i (i = 0..n-1) and the given sweep. */
-void or_kp_samples(double alpha, uint64_t seed, uint64_t sweep, long n, double *a0,
+void or_kp_samples(double alpha, uint64_t seed, uint64_t sweep, long n, int creutz, double *a0,
                    int32_t *trials)
 {
     for (long i = 0; i < n; ++i) {
         double delta = NAN;
-        int t = kp_delta(alpha, seed, (uint32_t)i, sweep, &delta);
+        int t = creutz ? creutz_delta(alpha, seed, (uint32_t)i, sweep, &delta)
+                       : kp_delta(alpha, seed, (uint32_t)i, sweep, &delta);
         a0[i] = 1.0 - delta;
         if (trials) trials[i] = t;
     }
@@ -593,13 +619,13 @@ int or_correlator(int Ns, int Nt, const double *links, int rmax, double *out)
 /* nsweeps full sweeps with sweep indices sweep0 .. sweep0+nsweeps-1; the
  * mean plaquette after each sweep goes to plaq_out (nullable). */
 int or_heatbath(int Ns, int Nt, double *links, double beta, int nsweeps, uint64_t seed,
-                uint64_t sweep0, double *plaq_out, uint64_t *counters)
+                uint64_t sweep0, double creutz_below, double *plaq_out, uint64_t *counters)
 {
     for (int s = 0; s < nsweeps; ++s) {
         for (int mu = 0; mu < 4; ++mu)
             for (int p = 0; p < 2; ++p)
                 or_heatbath_phase(Ns, Nt, links, beta, mu, p, seed, sweep0 + (uint64_t)s, 0,
-                                  NULL, counters);
+                                  creutz_below, NULL, counters);
         if (plaq_out) plaq_out[s] = or_plaquette(Ns, Nt, links);
     }
     return 0;

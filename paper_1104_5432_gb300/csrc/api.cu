@@ -82,6 +82,7 @@ struct su2_lattice {
     int cfg = 0;                    // active launch shape
     std::string tune_key;
     std::vector<int> ysplit;        // y slabs per lattice (slab launch shapes)
+    bool hybrid = false;            // Creutz/Kennedy-Pendleton sampler variant in use
     int rmax_limit = 0;             // rmax <= min_l Ns_l / 2
     size_t link_bytes = 0, work_bytes = 0;
     size_t off_status = 0, off_desc = 0, off_sstart = 0, off_spstart = 0;
@@ -302,7 +303,8 @@ int record_sweep(su2_lattice* L, bool plaq, int rmax, cudaStream_t s)
 {
     for (int mu = 0; mu < 4; ++mu)
         for (int p = 0; p < 2; ++p)
-            SU2_CUDA(launch_phase(L->cfg_ctx[L->cfg], L->dtype, L->cfg, mu, p, plaq, nullptr, s));
+            SU2_CUDA(launch_phase(L->cfg_ctx[L->cfg], L->dtype, L->cfg, mu, p, plaq, nullptr,
+                                  L->hybrid, s));
     SU2_CUDA(launch_sweep_end(L->cfg_ctx[L->cfg], plaq, s));
     if (rmax >= 0) {
         double* acc = L->acc_dev();
@@ -685,7 +687,7 @@ int su2_heatbath_phase(su2_lattice* lat, double beta, int mu, int parity, uint64
     DeviceGuard dg(lat->device);
     if (int rc = set_params(lat, nullptr, beta, nullptr, seed, nullptr, 0)) return rc;
     SU2_CUDA(launch_phase(lat->cfg_ctx[lat->cfg], lat->dtype, lat->cfg, mu, parity, false, trials,
-                          lat->stream));
+                          lat->hybrid, lat->stream));
     return SU2_OK;
 }
 
@@ -922,6 +924,31 @@ int su2_get_launch_config(const su2_lattice* lat, int* cfg, int* threads, int* m
     if (cfg) *cfg = lat->cfg;
     if (threads) *threads = LAUNCH_CFG[lat->dtype][lat->cfg].threads;
     if (min_blocks) *min_blocks = LAUNCH_CFG[lat->dtype][lat->cfg].min_blocks;
+    return SU2_OK;
+}
+
+int su2_set_sampler(su2_lattice* lat, double creutz_below)
+{
+    if (int rc = check_handle(lat)) return rc;
+    if (!(creutz_below >= 0.0) || !std::isfinite(creutz_below))
+        return fail(SU2_E_INVAL, "creutz_below must be finite and >= 0");
+    DeviceGuard dg(lat->device);
+    SU2_CUDA(cudaStreamSynchronize(lat->stream));
+    struct {
+        double d;
+        float f;
+    } v{creutz_below, (float)creutz_below};
+    static_assert(offsetof(LatDesc, creutz_below_f) == offsetof(LatDesc, creutz_below) + 8,
+                  "sampler fields are adjacent");
+    for (int l = 0; l < lat->n; ++l)
+        SU2_CUDA(cudaMemcpy(reinterpret_cast<char*>(lat->desc_dev(l)) +
+                                offsetof(LatDesc, creutz_below),
+                            &v, 12, cudaMemcpyHostToDevice));
+    const bool hyb = creutz_below > 0.0;
+    if (hyb != lat->hybrid) {
+        lat->hybrid = hyb;
+        lat->drop_graphs();  // graphs bake in the sampler variant
+    }
     return SU2_OK;
 }
 

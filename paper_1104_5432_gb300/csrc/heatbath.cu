@@ -76,15 +76,15 @@ __global__ void set_params_kernel(Ctx ctx, ParamChunk pc)
 }
 
 cudaError_t launch_phase_f32(const Ctx& c, int cfg, int mu, int parity, bool plaq, int32_t* dbg,
-                             cudaStream_t s);
+                             bool hyb, cudaStream_t s);
 cudaError_t launch_phase_f64(const Ctx& c, int cfg, int mu, int parity, bool plaq, int32_t* dbg,
-                             cudaStream_t s);
+                             bool hyb, cudaStream_t s);
 
 cudaError_t launch_phase(const Ctx& c, int dtype, int cfg, int mu, int parity, bool plaq,
-                         int32_t* dbg_trials, cudaStream_t s)
+                         int32_t* dbg_trials, bool hybrid, cudaStream_t s)
 {
-    if (dtype == 0) return launch_phase_f32(c, cfg, mu, parity, plaq, dbg_trials, s);
-    return launch_phase_f64(c, cfg, mu, parity, plaq, dbg_trials, s);
+    if (dtype == 0) return launch_phase_f32(c, cfg, mu, parity, plaq, dbg_trials, hybrid, s);
+    return launch_phase_f64(c, cfg, mu, parity, plaq, dbg_trials, hybrid, s);
 }
 
 cudaError_t launch_sweep_end(const Ctx& c, bool plaq, cudaStream_t s)

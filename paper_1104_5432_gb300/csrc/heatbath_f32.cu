@@ -5,17 +5,17 @@
 namespace su2 {
 
 cudaError_t launch_phase_f32_slab(const Ctx& c, int cfg, int mu, int parity, bool plaq,
-                                  int32_t* dbg, cudaStream_t s);
+                                  int32_t* dbg, bool hyb, cudaStream_t s);
 
 cudaError_t launch_phase_f32(const Ctx& c, int cfg, int mu, int parity, bool plaq, int32_t* dbg,
-                             cudaStream_t s)
+                             bool hyb, cudaStream_t s)
 {
-    if (LAUNCH_CFG[0][cfg & 7].slab) return launch_phase_f32_slab(c, cfg, mu, parity, plaq, dbg, s);
+    if (LAUNCH_CFG[0][cfg & 7].slab) return launch_phase_f32_slab(c, cfg, mu, parity, plaq, dbg, hyb, s);
     switch (cfg) {
-    case 0: return launch_phase_shape<float, LAUNCH_CFG[0][0].threads, LAUNCH_CFG[0][0].min_blocks, false>(c, mu, parity, plaq, dbg, s);
-    case 1: return launch_phase_shape<float, LAUNCH_CFG[0][1].threads, LAUNCH_CFG[0][1].min_blocks, false>(c, mu, parity, plaq, dbg, s);
-    case 2: return launch_phase_shape<float, LAUNCH_CFG[0][2].threads, LAUNCH_CFG[0][2].min_blocks, false>(c, mu, parity, plaq, dbg, s);
-    case 3: return launch_phase_shape<float, LAUNCH_CFG[0][3].threads, LAUNCH_CFG[0][3].min_blocks, false>(c, mu, parity, plaq, dbg, s);
+    case 0: return launch_phase_shape<float, LAUNCH_CFG[0][0].threads, LAUNCH_CFG[0][0].min_blocks, false>(c, mu, parity, plaq, dbg, hyb, s);
+    case 1: return launch_phase_shape<float, LAUNCH_CFG[0][1].threads, LAUNCH_CFG[0][1].min_blocks, false>(c, mu, parity, plaq, dbg, hyb, s);
+    case 2: return launch_phase_shape<float, LAUNCH_CFG[0][2].threads, LAUNCH_CFG[0][2].min_blocks, false>(c, mu, parity, plaq, dbg, hyb, s);
+    case 3: return launch_phase_shape<float, LAUNCH_CFG[0][3].threads, LAUNCH_CFG[0][3].min_blocks, false>(c, mu, parity, plaq, dbg, hyb, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -39,6 +39,9 @@ template <> __device__ __forceinline__ double alpha_haar<double>() { return 1e-1
 template <typename T> __device__ __forceinline__ T beta_of(const LatDesc& D);
 template <> __device__ __forceinline__ float beta_of<float>(const LatDesc& D) { return D.beta_f; }
 template <> __device__ __forceinline__ double beta_of<double>(const LatDesc& D) { return D.beta; }
+template <typename T> __device__ __forceinline__ T creutz_of(const LatDesc& D);
+template <> __device__ __forceinline__ float creutz_of<float>(const LatDesc& D) { return D.creutz_below_f; }
+template <> __device__ __forceinline__ double creutz_of<double>(const LatDesc& D) { return D.creutz_below; }
 
 // warp partial sum in the link precision (fixed butterfly order)
 template <typename T>
@@ -49,7 +52,7 @@ __device__ __forceinline__ T warp_sum_t(T v)
     return v;
 }
 
-template <typename T, int MU, bool PLAQ, bool DBG, int NT, int MINB, bool SLAB>
+template <typename T, int MU, bool PLAQ, bool DBG, int NT, int MINB, bool SLAB, bool HYB>
 __global__ void __launch_bounds__(NT, MINB)
 hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 {
@@ -117,20 +120,41 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             U4 w = st.draw(TAG_TRIAL, 0u);
             const uint32_t kd1 = ((w.x & 511u) << 9) | (w.y & 511u);
             const uint32_t kd2 = ((w.z & 511u) << 9) | (w.w & 511u);
-            auto kp_try = [&](const U4& ww, T* d) -> bool {
-                const T r1 = u01<T>(ww.x), r2 = u01<T>(ww.y), r3 = u01<T>(ww.z), r4 = u01<T>(ww.w);
-                const T lam2 = -(Math<T>::ln_u01(r1) + Math<T>::cos2pi_sq(r2) *
-                                 Math<T>::ln_u01(r3)) * inv2a;
-                *d = T(2) * lam2;
-                return r4 * r4 <= T(1) - lam2;
-            };
-            if (kp_try(w, &delta)) {
-                tr = 1;
-            } else {
-                for (int t = 1; t < KP_CAP; ++t) {
-                    if (kp_try(st.draw(TAG_TRIAL, (uint32_t)t), &delta)) {
+            // Creutz's draw below the handle's switch (small alpha, where
+            // Kennedy-Pendleton accepts rarely): a0 from exp(alpha a0) by
+            // inversion, accepted with sqrt(1 - a0^2); same blocks, r1 and r4
+            if (HYB && alpha < creutz_of<T>(D)) {
+                // Creutz's draw (small alpha, where Kennedy-Pendleton accepts
+                // rarely): a0 from exp(alpha a0) by inversion, accepted with
+                // sqrt(1 - a0^2); the same trial blocks, r1 = word 0, r4 = word 3
+                const T q = -Math<T>::expm1(T(-2) * alpha);
+                for (int t = 0; t < KP_CAP; ++t) {
+                    const U4 ww = t == 0 ? w : st.draw(TAG_TRIAL, (uint32_t)t);
+                    const T r1 = u01<T>(ww.x), r4 = u01<T>(ww.w);
+                    const T d = -Math<T>::log1p(-r1 * q) * (T(2) * inv2a);
+                    if (r4 * r4 <= d * (T(2) - d)) {
+                        delta = d;
                         tr = t + 1;
                         break;
+                    }
+                }
+            } else {
+                auto kp_try = [&](const U4& ww, T* d) -> bool {
+                    const T r1 = u01<T>(ww.x), r2 = u01<T>(ww.y), r3 = u01<T>(ww.z),
+                            r4 = u01<T>(ww.w);
+                    const T lam2 = -(Math<T>::ln_u01(r1) + Math<T>::cos2pi_sq(r2) *
+                                     Math<T>::ln_u01(r3)) * inv2a;
+                    *d = T(2) * lam2;
+                    return r4 * r4 <= T(1) - lam2;
+                };
+                if (kp_try(w, &delta)) {
+                    tr = 1;
+                } else {
+                    for (int t = 1; t < KP_CAP; ++t) {
+                        if (kp_try(st.draw(TAG_TRIAL, (uint32_t)t), &delta)) {
+                            tr = t + 1;
+                            break;
+                        }
                     }
                 }
             }
@@ -187,16 +211,21 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 // the phase kernel; the grid covers ctx.phase_blocks blocks of NT links.
 template <typename T, int NT, int MINB, bool SLAB>
 cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int32_t* dbg,
-                               cudaStream_t s)
+                               bool hyb, cudaStream_t s)
 {
     // the fused plaquette exists only in the odd phases with mu >= 1
     const bool pl = plaq && parity == 1 && mu >= 1;
     const dim3 grid(c.phase_blocks), block(NT);
-#define SU2_LAUNCH(MUV)                                                                          \
+#define SU2_LAUNCH_H(MUV, H)                                                                     \
     do {                                                                                         \
-        if (dbg) hb_phase_kernel<T, MUV, false, true, NT, MINB, SLAB><<<grid, block, 0, s>>>(c, parity, dbg); \
-        else if (pl) hb_phase_kernel<T, MUV, (MUV > 0), false, NT, MINB, SLAB><<<grid, block, 0, s>>>(c, parity, dbg); \
-        else hb_phase_kernel<T, MUV, false, false, NT, MINB, SLAB><<<grid, block, 0, s>>>(c, parity, dbg); \
+        if (dbg) hb_phase_kernel<T, MUV, false, true, NT, MINB, SLAB, H><<<grid, block, 0, s>>>(c, parity, dbg); \
+        else if (pl) hb_phase_kernel<T, MUV, (MUV > 0), false, NT, MINB, SLAB, H><<<grid, block, 0, s>>>(c, parity, dbg); \
+        else hb_phase_kernel<T, MUV, false, false, NT, MINB, SLAB, H><<<grid, block, 0, s>>>(c, parity, dbg); \
+    } while (0)
+#define SU2_LAUNCH(MUV)                 \
+    do {                                \
+        if (hyb) SU2_LAUNCH_H(MUV, true);  \
+        else SU2_LAUNCH_H(MUV, false);  \
     } while (0)
     switch (mu) {
     case 0: SU2_LAUNCH(0); break;
@@ -205,6 +234,7 @@ cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int3
     default: SU2_LAUNCH(3); break;
     }
 #undef SU2_LAUNCH
+#undef SU2_LAUNCH_H
     return cudaGetLastError();
 }
 

@@ -58,6 +58,8 @@ struct LatDesc {
     FastDiv div_nh, div_ns;
     int32_t ysplit, Ny;     // y slabs of the large-lattice traversal, Ny = Ns / ysplit
     FastDiv div_ny, div_nt;
+    double creutz_below;    // alpha below which Creutz's draw replaces Kennedy-Pendleton's
+    float creutz_below_f;
     uint64_t link_off;      // byte offset of this lattice in the link buffer
     uint64_t field_off;     // double offset of its Polyakov field
     // per call
@@ -113,8 +115,10 @@ struct ParamChunk {
     double* plaq_out[PARAM_CHUNK];
 };
 cudaError_t launch_set_params(const Ctx& c, const ParamChunk& pc, cudaStream_t s);
+// hybrid: compile-time variant with Creutz's draw below each lattice's
+// creutz_below (the plain variant never looks at it)
 cudaError_t launch_phase(const Ctx& c, int dtype, int cfg, int mu, int parity, bool plaq,
-                         int32_t* dbg_trials, cudaStream_t s);
+                         int32_t* dbg_trials, bool hybrid, cudaStream_t s);
 cudaError_t launch_sweep_end(const Ctx& c, bool plaq, cudaStream_t s);
 cudaError_t launch_init(const Ctx& c, int dtype, int l, uint32_t V, int hot, uint64_t seed,
                         cudaStream_t s);

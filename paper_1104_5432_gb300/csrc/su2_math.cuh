@@ -49,6 +49,8 @@ template <> struct Math<float> {
         *c = -cx;
     }
     static __device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
+    static __device__ __forceinline__ float log1p(float x) { return log1pf(x); }
+    static __device__ __forceinline__ float expm1(float x) { return expm1f(x); }
     static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
 };
 
@@ -64,6 +66,8 @@ template <> struct Math<double> {
         sincospi(2.0 * r, s, c);
     }
     static __device__ __forceinline__ double sqrt_pos(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }
+    static __device__ __forceinline__ double expm1(double x) { return ::expm1(x); }
     static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / sqrt(x); }
 };
 

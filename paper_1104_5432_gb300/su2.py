@@ -86,6 +86,7 @@ def load(build_if_needed: bool = True):
             "su2_tune_cache_lookup": (i, [C.c_char_p, C.c_char_p, P]),
             "su2_tune_cache_store": (i, [C.c_char_p, C.c_char_p, i, d]),
             "su2_set_slabs": (i, [P, i]),
+            "su2_set_sampler": (i, [P, d]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -285,6 +286,10 @@ class Lattice:
 
     def set_launch_config(self, cfg: int):
         _check(load().su2_set_launch_config(self._h, int(cfg)))
+
+    def set_sampler(self, creutz_below: float):
+        """Creutz's draw below alpha = creutz_below, Kennedy-Pendleton above."""
+        _check(load().su2_set_sampler(self._h, float(creutz_below)))
 
     def set_slabs(self, S: int):
         """Walk the lattices in S y-slabs under the slab launch shapes."""

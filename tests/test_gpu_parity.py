@@ -438,3 +438,50 @@ def test_full_size_128_properties():
     del dev
     lat.close()
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype,beta", [(su2.F64, 0.7), (su2.F32, 0.7), (su2.F64, 2.3)])
+def test_hybrid_sampler_phase_parity(dtype, beta):
+    """Creutz below alpha = 1.7, Kennedy-Pendleton above: every phase against
+    the oracle with the same switch (FP64: 1e-12 and identical trial counts;
+    FP32: 2e-5 on agreeing links, flips < 1e-4)."""
+    Ns, Nt = 8, 6
+    V = Ns ** 3 * Nt
+    par = parity_mask(Ns, Nt)
+    lat = lattice(Ns, Nt, dtype)
+    lat.set_sampler(1.7)
+    lat.init(su2.HOT, 19)
+    lat.heatbath(beta, 1, 5, plaq=None)
+    sweep = lat.get_sweep()
+    flips = n = 0
+    for mu, p in PHASES:
+        before = lat.get_links()
+        trials = torch.full((V,), -2, dtype=torch.int32, device="cuda")
+        lat.heatbath_phase(beta, mu, p, 29, trials)
+        after = lat.get_links()
+        ref, rt, _ = O.heatbath_phase(Ns, Nt, before, beta, mu, p, 29, sweep, creutz_below=1.7)
+        gt = trials.cpu().numpy()
+        same = gt[par == p] == rt[par == p, mu]
+        diff = np.max(np.abs(after[par == p, mu] - ref[par == p, mu]), axis=1)
+        if dtype == su2.F64:
+            assert np.all(same) and diff.max() <= 1e-12
+        else:
+            assert diff[same].max() <= 2e-5
+            flips += int((~same).sum())
+            n += int(same.size)
+    assert flips <= max(1e-4 * n, 1)
+
+
+def test_hybrid_sampler_strong_coupling_and_tiny_beta():
+    lat = lattice(12, 12, su2.F32)
+    lat.set_sampler(1.7)
+    lat.init(su2.HOT, 5)
+    p = lat.heatbath(0.5, 420, 5)[0][20:]
+    b = p.reshape(-1, 20).mean(1)
+    u = 0.12371792827832075  # I2(0.5) / I1(0.5)
+    assert abs(p.mean() - u) < 3 * b.std(ddof=1) / np.sqrt(len(b)) + 2e-4
+    st = lat.stats()
+    assert st["trials"] / st["updates"] < 1.5 and st["cap_hits"] == 0
+    lat.heatbath(1e-9, 1, 5, plaq=None)
+    lat.sync()  # no cap hit: Creutz's draw works at vanishing alpha
+    assert lat.stats()["cap_hits"] == 0

@@ -260,6 +260,38 @@ def test_kp_sampler_distribution(alpha):
     assert abs(a0.mean() - mean) < 5 * a0.std() / np.sqrt(n)
 
 
+@pytest.mark.parametrize("alpha", [0.01, 0.3, 1.0, 3.0])
+def test_creutz_sampler_distribution(alpha):
+    """Creutz's draw targets the same density as Kennedy-Pendleton's."""
+    n = 100000
+    a0, trials = O.kp_samples(alpha, seed=4321 + int(alpha * 100), sweep=2, n=n, creutz=True)
+    assert np.all(trials >= 1) and np.all((a0 >= -1.0) & (a0 <= 1.0))
+    assert stats.kstest(a0, _a0_cdf(alpha)).pvalue > 1e-4
+    mean = special.ive(2, alpha) / special.ive(1, alpha)
+    assert abs(a0.mean() - mean) < 5 * a0.std() / np.sqrt(n)
+    # acceptance near pi/4 at small alpha, where Kennedy-Pendleton's collapses
+    if alpha <= 0.3:
+        assert n / trials.sum() > 0.7
+        _, kp_trials = O.kp_samples(alpha, seed=1, sweep=2, n=2000)
+        assert 2000 / kp_trials.sum() < 0.25
+
+
+def test_hybrid_strong_coupling_and_tiny_beta():
+    """With Creutz's draw below alpha = 1.7 the chain keeps the strong-
+    coupling limit, and a vanishing beta no longer hits the trial cap."""
+    Ns = Nt = 6
+    links = O.init(Ns, Nt, True, 7)
+    links, _, _ = O.heatbath(Ns, Nt, links, 0.5, 20, 13, creutz_below=1.7)
+    links, p, c = O.heatbath(Ns, Nt, links, 0.5, 400, 13, sweep0=20, creutz_below=1.7)
+    b = p.reshape(-1, 20).mean(1)
+    u = special.ive(2, 0.5) / special.ive(1, 0.5)
+    assert abs(p.mean() - u) < 3 * b.std(ddof=1) / np.sqrt(len(b)) + 2e-4
+    assert c[0] / c[1] < 1.5  # ~1.3 trials per update instead of ~2 with KP alone
+    new, trials, cnt = O.heatbath_phase(2, 2, O.init(2, 2, True, 4), 1e-9, 1, 0, 3, 0,
+                                        creutz_below=1.7)
+    assert cnt[2] == 0 and np.all(trials[trials != -2] >= 1)
+
+
 def test_kp_sampler_rejects_wrong_alpha():
     """The KS test does see a factor-two error in alpha (guards the pin itself)."""
     a0, _ = O.kp_samples(5.0, seed=77, sweep=0, n=100000)

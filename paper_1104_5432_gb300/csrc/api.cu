@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "su2.h"
 #include "su2_internal.h"
 
@@ -62,6 +64,13 @@ struct DeviceGuard {
 };
 
 __global__ void put_u64_kernel(uint64_t* dst, uint64_t v) { *dst = v; }
+
+// NVTX range over one library call (visible in Nsight Systems timelines;
+// free when no tool is attached)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 }  // namespace
 
@@ -363,6 +372,7 @@ int heatbath_impl(su2_lattice* L, const double* betas, double beta, int nsweeps,
                   const uint64_t* seeds, uint64_t seed, double* plaq, int rmax = -1,
                   double* poly_sum = nullptr, double* corr_sum = nullptr)
 {
+    Range range(rmax >= 0 ? "su2_heatbath_measure" : "su2_heatbath");
     if (int rc = check_handle(L)) return rc;
     if (nsweeps < 0) return fail(SU2_E_INVAL, "nsweeps < 0");
     if (rmax >= 0) {
@@ -415,6 +425,7 @@ int heatbath_impl(su2_lattice* L, const double* betas, double beta, int nsweeps,
 
 int init_impl(su2_lattice* L, int start, const uint64_t* seeds, uint64_t seed)
 {
+    Range range("su2_init");
     if (int rc = check_handle(L)) return rc;
     if (start != SU2_COLD && start != SU2_HOT) return fail(SU2_E_INVAL, "bad start %d", start);
     DeviceGuard dg(L->device);
@@ -845,6 +856,7 @@ int su2_sync(su2_lattice* lat)
 
 int su2_autotune(su2_lattice* lat, int* chosen)
 {
+    Range range("su2_autotune");
     if (int rc = check_handle(lat)) return rc;
     DeviceGuard dg(lat->device);
     cudaStream_t s = lat->stream;

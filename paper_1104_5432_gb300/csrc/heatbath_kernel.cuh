@@ -120,9 +120,6 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             U4 w = st.draw(TAG_TRIAL, 0u);
             const uint32_t kd1 = ((w.x & 511u) << 9) | (w.y & 511u);
             const uint32_t kd2 = ((w.z & 511u) << 9) | (w.w & 511u);
-            // Creutz's draw below the handle's switch (small alpha, where
-            // Kennedy-Pendleton accepts rarely): a0 from exp(alpha a0) by
-            // inversion, accepted with sqrt(1 - a0^2); same blocks, r1 and r4
             if (HYB && alpha < creutz_of<T>(D)) {
                 // Creutz's draw (small alpha, where Kennedy-Pendleton accepts
                 // rarely): a0 from exp(alpha a0) by inversion, accepted with

@@ -213,9 +213,11 @@ int su2_set_sweep(su2_lattice* lat, int l, uint64_t sweep);
 
 /* Number of launch shapes (threads per block, minimum resident blocks per
  * SM, plain or y-slab traversal of the lattice) compiled for the phase
- * kernel; shape 0 is the default, shapes 4..7 walk large FP32 lattices in
- * y slabs so the +-t neighbours stay in L2.  Results never depend on the
- * shape (the random streams are keyed by link and sweep). */
+ * kernel; shape 0 is the default.  FP32: 256x4, 256x3, 128x8, 512x2, the
+ * y-slab walks 256x4 and 128x8 (large lattices: the +-t neighbours stay in
+ * L2), 64x16, 32x32; FP64: 256x1, 256x2, 128x4, 128x1, 64x8, 64x4, 32x16,
+ * 32x8 (small blocks spread tiny lattices over more SMs).  Results never
+ * depend on the shape (the random streams are keyed by link and sweep). */
 #define SU2_NUM_LAUNCH_CONFIGS 8
 
 /* Times every launch shape on this handle's lattices (whole sweeps with the

@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsu2gb300.so")
-SOURCES = ["heatbath_f32.cu", "heatbath_f32_slab.cu", "heatbath_f64.cu", "heatbath.cu", "observables.cu", "links.cu",
+SOURCES = ["heatbath_f32.cu", "heatbath_f32_slab.cu", "heatbath_f32_small.cu", "heatbath_f64.cu",
+           "heatbath_f64_small.cu", "heatbath.cu", "observables.cu", "links.cu",
            "api.cu", "plaquette_static.cu", "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

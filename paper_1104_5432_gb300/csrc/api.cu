@@ -887,8 +887,11 @@ int su2_autotune(su2_lattice* lat, int* chosen)
     // slab shapes only matter when some lattice is walked in slabs
     bool any_slab = false;
     for (int l = 0; l < lat->n; ++l) any_slab = any_slab || lat->ysplit[l] > 1;
-    const int ncand = any_slab ? NUM_LAUNCH_CFG : NUM_LAUNCH_CFG / 2;
+    bool cand[NUM_LAUNCH_CFG];
+    for (int k = 0; k < NUM_LAUNCH_CFG; ++k) cand[k] = any_slab || !LAUNCH_CFG[lat->dtype][k].slab;
+    const int ncand = NUM_LAUNCH_CFG;
     for (int k = 0; k < ncand && rc == SU2_OK; ++k) {
+        if (!cand[k]) continue;
         float ms = 0.f;
         rc = time_sweeps(k, 1, &ms);  // builds the graph, warms up
         if (rc == SU2_OK) rc = time_sweeps(k, 1, &ms);
@@ -898,6 +901,7 @@ int su2_autotune(su2_lattice* lat, int* chosen)
     }
     for (int round = 0; round < 3 && rc == SU2_OK; ++round)
         for (int k = 0; k < ncand && rc == SU2_OK; ++k) {
+            if (!cand[k]) continue;
             float ms = 0.f;
             rc = time_sweeps(k, reps[k], &ms);
             best_ms[k] = std::min(best_ms[k], (double)ms / reps[k]);
@@ -908,7 +912,7 @@ int su2_autotune(su2_lattice* lat, int* chosen)
     if (rc != SU2_OK) return rc;
     int best = 0;
     for (int k = 1; k < ncand; ++k)
-        if (best_ms[k] < best_ms[best]) best = k;
+        if (cand[k] && best_ms[k] < best_ms[best]) best = k;
     // leave the handle as su2_init(SU2_HOT) with the tuning seed would
     for (int l = 0; l < lat->n; ++l)
         SU2_CUDA(launch_init(lat->ctx, lat->dtype, l, (uint32_t)lat->V[l], SU2_HOT, tune_seed + l, s));

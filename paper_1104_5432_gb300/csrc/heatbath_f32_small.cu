@@ -1,0 +1,17 @@
+// heatbath_f32_small.cu -- FP32 phase-kernel instantiations with 64 and 32
+// threads per block (tiny lattices over many SMs).
+#include "heatbath_kernel.cuh"
+
+namespace su2 {
+
+cudaError_t launch_phase_f32_small(const Ctx& c, int cfg, int mu, int parity, bool plaq, int32_t* dbg,
+                             bool hyb, cudaStream_t s)
+{
+    switch (cfg) {
+    case 6: return launch_phase_shape<float, LAUNCH_CFG[0][6].threads, LAUNCH_CFG[0][6].min_blocks, false>(c, mu, parity, plaq, dbg, hyb, s);
+    case 7: return launch_phase_shape<float, LAUNCH_CFG[0][7].threads, LAUNCH_CFG[0][7].min_blocks, false>(c, mu, parity, plaq, dbg, hyb, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace su2

@@ -31,11 +31,12 @@ struct LaunchCfg {
     bool slab;
 };
 constexpr int NUM_LAUNCH_CFG = 8;
+// Small blocks (64, 32 threads) spread tiny lattices over more SMs.
 constexpr LaunchCfg LAUNCH_CFG[2][NUM_LAUNCH_CFG] = {
     {{256, 4, false}, {256, 3, false}, {128, 8, false}, {512, 2, false},
-     {256, 4, true}, {256, 3, true}, {128, 8, true}, {512, 2, true}},
+     {256, 4, true}, {128, 8, true}, {64, 16, false}, {32, 32, false}},
     {{256, 1, false}, {256, 2, false}, {128, 4, false}, {128, 1, false},
-     {256, 1, false}, {256, 2, false}, {128, 4, false}, {128, 1, false}},
+     {64, 8, false}, {64, 4, false}, {32, 16, false}, {32, 8, false}},
 };
 // largest y-slab window (sites between a site and its t neighbour, times
 // the bytes a site's update touches) kept in L2

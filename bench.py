@@ -222,6 +222,9 @@ def gpu_arm(args, rank, world, local):
     launches_per_step = 1 + 1 + 9 * sweeps  # init, parameter kernel, 8 phases + sweep end
 
     # ---- dominant kernel, timed per launch with events on its stream ----------
+    # (the first phase call uploads beta and seed; the timed ones launch the
+    # phase kernel alone)
+    lat.heatbath_phase(w["beta"], 3, 1, seed_hb)
     n_ph = 16
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(n_ph)]

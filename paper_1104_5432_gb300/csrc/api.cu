@@ -92,6 +92,10 @@ struct su2_lattice {
     std::string tune_key;
     std::vector<int> ysplit;        // y slabs per lattice (slab launch shapes)
     bool hybrid = false;            // Creutz/Kennedy-Pendleton sampler variant in use
+    // last uniform parameters written by su2_heatbath_phase (beta, seed)
+    bool phase_params_valid = false;
+    double phase_beta = 0.0;
+    uint64_t phase_seed = 0;
     int rmax_limit = 0;             // rmax <= min_l Ns_l / 2
     size_t link_bytes = 0, work_bytes = 0;
     size_t off_status = 0, off_desc = 0, off_sstart = 0, off_spstart = 0;
@@ -291,6 +295,7 @@ void set_slabs(LatDesc& D, int S)
 int set_params(su2_lattice* L, const double* betas, double beta, const uint64_t* seeds,
                uint64_t seed, double* plaq_dev, int nsweeps)
 {
+    L->phase_params_valid = false;
     for (int first = 0; first < L->n; first += PARAM_CHUNK) {
         ParamChunk pc{};
         pc.first = first;
@@ -696,7 +701,14 @@ int su2_heatbath_phase(su2_lattice* lat, double beta, int mu, int parity, uint64
     if (trials && lat->n != 1) return fail(SU2_E_INVAL, "trials output needs n == 1");
     if (trials && !is_device_ptr(trials)) return fail(SU2_E_INVAL, "trials must be device memory");
     DeviceGuard dg(lat->device);
-    if (int rc = set_params(lat, nullptr, beta, nullptr, seed, nullptr, 0)) return rc;
+    // consecutive phases with the same beta and seed reuse the parameters
+    // already on the device (no parameter kernel between the phases)
+    if (!(lat->phase_params_valid && lat->phase_beta == beta && lat->phase_seed == seed)) {
+        if (int rc = set_params(lat, nullptr, beta, nullptr, seed, nullptr, 0)) return rc;
+        lat->phase_params_valid = true;
+        lat->phase_beta = beta;
+        lat->phase_seed = seed;
+    }
     SU2_CUDA(launch_phase(lat->cfg_ctx[lat->cfg], lat->dtype, lat->cfg, mu, parity, false, trials,
                           lat->hybrid, lat->stream));
     return SU2_OK;

@@ -603,6 +603,7 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
     SU2_CUDA(cudaMemset(w + lat->off_status, 0, 256));
     SU2_CUDA(cudaMemcpy(w + lat->off_desc, d.data(), sizeof(LatDesc) * lat->n,
                         cudaMemcpyHostToDevice));
+    lat->phase_params_valid = false;
     for (int k = 0; k < NUM_LAUNCH_CFG; ++k)
         SU2_CUDA(cudaMemcpy(w + lat->off_pstart_cfg[k], lat->phase_start[k].data(),
                             4 * (lat->n + 1), cudaMemcpyHostToDevice));

@@ -154,6 +154,28 @@ def test_phase_parity_fp64(Ns, Nt):
     assert lat.get_sweep() == 5
 
 
+def test_phase_parameters_follow_every_call():
+    """Single-phase calls keep beta and seed on the device while they do not
+    change; a change of either, or a sweep call in between, must take
+    effect on the next phase."""
+    Ns, Nt = 6, 4
+    lat = lattice(Ns, Nt, su2.F64)
+    lat.init(su2.HOT, 13)
+    calls = [("phase", 2.3, 0, 0, 41), ("phase", 2.3, 1, 1, 41), ("phase", 1.7, 2, 0, 41),
+             ("phase", 1.7, 3, 1, 42), ("sweep", 2.9, 0, 0, 43), ("phase", 1.7, 3, 1, 42),
+             ("phase", 1.7, 0, 1, 42)]
+    for kind, beta, mu, p, seed in calls:
+        before = lat.get_links()
+        sweep = lat.get_sweep()
+        if kind == "phase":
+            lat.heatbath_phase(beta, mu, p, seed)
+            ref, _, _ = O.heatbath_phase(Ns, Nt, before, beta, mu, p, seed, sweep)
+        else:
+            lat.heatbath(beta, 1, seed, plaq=None)
+            ref, _, _ = O.heatbath(Ns, Nt, before, beta, 1, seed, sweep0=sweep)
+        assert np.max(np.abs(lat.get_links() - ref)) <= 1e-12, (kind, beta, mu, p, seed)
+
+
 @pytest.mark.parametrize("Ns,Nt", [(12, 12), (10, 6)])
 def test_phase_parity_fp32(Ns, Nt):
     V = Ns ** 3 * Nt

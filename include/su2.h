@@ -211,14 +211,22 @@ int su2_set_sweep(su2_lattice* lat, int l, uint64_t sweep);
 /* launch-shape autotuning                                             */
 /* ------------------------------------------------------------------ */
 
-/* Number of launch shapes (threads per block, minimum resident blocks per
- * SM, plain or y-slab traversal of the lattice) compiled for the phase
- * kernel; shape 0 is the default.  FP32: 256x4, 256x3, 128x8, 512x2, the
- * y-slab walks 256x4 and 128x8 (large lattices: the +-t neighbours stay in
- * L2), 64x16, 32x32; FP64: 256x1, 256x2, 128x4, 128x1, 64x8, 64x4, 32x16,
- * 32x8 (small blocks spread tiny lattices over more SMs).  Results never
- * depend on the shape (the random streams are keyed by link and sweep). */
-#define SU2_NUM_LAUNCH_CONFIGS 8
+/* Number of launch shapes (threads per block x minimum resident blocks per
+ * SM, plain or y-slab traversal of the lattice, links per thread) compiled
+ * for the phase kernel; shape 0 is the default.
+ *   FP32:  0 256x4   1 128x8   2 64x16   3 32x32   4 256x4 slab  5 128x8 slab
+ *          6 32x32 /2  7 32x32 /4  8 32x32 /8  9 32x32 /16  10 64x16 /8
+ *          11 128x8 /8  12 32x32 slab /8  13 128x8 slab /8
+ *   FP64:  0 256x1   1 128x4   2 64x8   3 64x4   4 32x16   5 32x8
+ *          6 32x16 /2  7 32x16 /4  8 32x16 /8  9 32x16 /16  10 32x16 /32
+ *          11 64x8 /16  12 32x8 /16  13 128x4 /16
+ * (/R: R links per thread with a per-warp queue of rejected Kennedy-
+ * Pendleton trials, retried 32 at a time; slab: large lattices walked in y
+ * slabs so the +-t neighbours stay in L2.)  Small blocks spread tiny
+ * lattices over more SMs; several links per thread pay off on large ones.
+ * Results never depend on the shape (the random streams are keyed by link
+ * and sweep). */
+#define SU2_NUM_LAUNCH_CONFIGS 14
 
 /* Times every launch shape on this handle's lattices (whole sweeps with the
  * fused plaquette, replayed as in su2_heatbath, ~20 ms per shape in each of

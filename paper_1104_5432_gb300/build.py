@@ -18,9 +18,12 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsu2gb300.so")
-SOURCES = ["heatbath_f32.cu", "heatbath_f32_slab.cu", "heatbath_f32_small.cu", "heatbath_f64.cu",
-           "heatbath_f64_small.cu", "heatbath.cu", "observables.cu", "links.cu",
-           "api.cu", "plaquette_static.cu", "selftest.cu"]
+SOURCES = ["heatbath.cu", "observables.cu", "links.cu", "api.cu", "plaquette_static.cu",
+           "selftest.cu"]
+# heatbath_shapes.cu once per pair of launch shapes and precision (the
+# 14-entry table in csrc/su2_internal.h): (object name, defines)
+SHAPE_UNITS = [(f"heatbath_shapes_{'f32' if row == 0 else 'f64'}_{k}",
+                (f"SU2_ROW={row}", f"SU2_FIRST={k}")) for row in (0, 1) for k in range(0, 14, 2)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -54,16 +57,21 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
     extra = ["-Xptxas", "-v"] if ptxas_info else []
     extra += [f"-D{d}" for d in defines]
 
-    def one(src):
-        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
-        cmd = [cc, *flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
+    units = [(src, src.replace(".cu", ""), ()) for src in SOURCES]
+    units += [("heatbath_shapes.cu", name, defs) for name, defs in SHAPE_UNITS]
+
+    def one(unit):
+        src, name, defs = unit
+        obj = os.path.join(build_dir, name + ".o")
+        cmd = [cc, *flags(extra + [f"-D{d}" for d in defs]), "-c", os.path.join(CSRC, src),
+               "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
+            raise RuntimeError(f"nvcc failed on {name}:\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(one, SOURCES))
+    with cf.ThreadPoolExecutor(max_workers=min(len(units), os.cpu_count() or 8)) as ex:
+        results = list(ex.map(one, units))
     if verbose or ptxas_info:
         for _, err in results:
             if err:

@@ -189,7 +189,9 @@ int layout(su2_lattice* L)
         L->field_off[l] = fo;
         fo += (L->Vs[l] + 31) & ~uint64_t(31);
         for (int k = 0; k < NUM_LAUNCH_CFG; ++k) {
-            const uint64_t nt = (uint64_t)LAUNCH_CFG[L->dtype][k].threads;
+            // links per block: threads x rounds
+            const uint64_t nt = (uint64_t)LAUNCH_CFG[L->dtype][k].threads *
+                                (uint64_t)LAUNCH_CFG[L->dtype][k].rounds;
             L->phase_start[k][l + 1] = L->phase_start[k][l] + (uint32_t)((L->V[l] / 2 + nt - 1) / nt);
         }
         L->site_start[l + 1] = L->site_start[l] + blocks_of(L->V[l]);

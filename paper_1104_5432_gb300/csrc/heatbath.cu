@@ -75,16 +75,26 @@ __global__ void set_params_kernel(Ctx ctx, ParamChunk pc)
     D->sweep_base = D->sweep;
 }
 
-cudaError_t launch_phase_f32(const Ctx& c, int cfg, int mu, int parity, bool plaq, int32_t* dbg,
-                             bool hyb, cudaStream_t s);
-cudaError_t launch_phase_f64(const Ctx& c, int cfg, int mu, int parity, bool plaq, int32_t* dbg,
-                             bool hyb, cudaStream_t s);
+// one pair of launch shapes per instantiation of heatbath_shapes.cu
+template <int ROW, int FIRST>
+cudaError_t launch_phase_pair(const Ctx& c, int cfg, int mu, int parity, bool plaq, int32_t* dbg,
+                              bool hyb, cudaStream_t s);
 
 cudaError_t launch_phase(const Ctx& c, int dtype, int cfg, int mu, int parity, bool plaq,
                          int32_t* dbg_trials, bool hybrid, cudaStream_t s)
 {
-    if (dtype == 0) return launch_phase_f32(c, cfg, mu, parity, plaq, dbg_trials, hybrid, s);
-    return launch_phase_f64(c, cfg, mu, parity, plaq, dbg_trials, hybrid, s);
+    using Fn = cudaError_t (*)(const Ctx&, int, int, int, bool, int32_t*, bool, cudaStream_t);
+    static_assert(NUM_LAUNCH_CFG == 14, "one entry per pair of shapes below");
+    static const Fn pairs[2][NUM_LAUNCH_CFG / 2] = {
+        {launch_phase_pair<0, 0>, launch_phase_pair<0, 2>, launch_phase_pair<0, 4>,
+         launch_phase_pair<0, 6>, launch_phase_pair<0, 8>, launch_phase_pair<0, 10>,
+         launch_phase_pair<0, 12>},
+        {launch_phase_pair<1, 0>, launch_phase_pair<1, 2>, launch_phase_pair<1, 4>,
+         launch_phase_pair<1, 6>, launch_phase_pair<1, 8>, launch_phase_pair<1, 10>,
+         launch_phase_pair<1, 12>},
+    };
+    if (dtype < 0 || dtype > 1 || cfg < 0 || cfg >= NUM_LAUNCH_CFG) return cudaErrorInvalidValue;
+    return pairs[dtype][cfg >> 1](c, cfg, mu, parity, plaq, dbg_trials, hybrid, s);
 }
 
 cudaError_t launch_sweep_end(const Ctx& c, bool plaq, cudaStream_t s)

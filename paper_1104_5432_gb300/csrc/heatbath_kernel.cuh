@@ -1,13 +1,14 @@
-// heatbath_kernel.cuh -- the checkerboard phase kernel of the SU(2) heat
+// heatbath_kernel.cuh -- the checkerboard phase kernels of the SU(2) heat
 // bath, templated on the link precision, the direction, the fused
 // plaquette, the per-link trial output and the launch shape (threads per
-// block, minimum resident blocks), so that several shapes can be compiled
-// and the fastest chosen at run time (the results never depend on it).
+// block, minimum resident blocks, links per thread), so that several
+// shapes can be compiled and the fastest chosen at run time (the results
+// never depend on it).
 //
 // Phase (mu, p) replaces every link U_mu(x) with parity(x) = p by a draw
 // from its conditional law exp(beta k a0(U Vhat)) dU, where the staple sum
 // A = k Vhat collects the six plaquettes through U_mu(x).  Links of one
-// phase share no staple, so one thread per link updates them all at once.
+// phase share no staple, so all of them are updated at once.
 // (The paper's benchmark, Sec. 2.1: random SU(2) start, heat-bath
 // iterations, mean plaquette after each.)
 //
@@ -21,9 +22,9 @@
 // The mean plaquette after the sweep is fused in: in phase (mu, 1) with
 // mu >= 1 the plane-nu part S_nu of the staple (nu < mu) closes exactly the
 // plaquettes of plane (nu, mu) at the odd sites and at x - nu_hat, and every
-// link of that plane is final for the sweep.  Each thread adds
-// 1/2 Tr(U_new S_nu) over nu < mu; so the six planes are covered exactly once
-// at no extra memory traffic.
+// link of that plane is final for the sweep.  Each link adds
+// 1/2 Tr(U_new P) with P = sum over nu < mu of S_nu (the trace is linear),
+// so the six planes are covered exactly once at no extra memory traffic.
 #pragma once
 #include "su2_internal.h"
 #include "su2_links.cuh"
@@ -52,6 +53,116 @@ __device__ __forceinline__ T warp_sum_t(T v)
     return v;
 }
 
+// ---------------------------------------------------------------------------
+// pieces shared by the two phase kernels
+// ---------------------------------------------------------------------------
+
+// Staple sum A = sum over nu != mu of the upper and lower staples of
+// U_mu(x), and (PLAQ) its part P over nu < mu, which closes the plaquettes
+// of the planes (nu, mu).  P is A after its first mu terms, so it costs no
+// extra additions.
+template <typename T, int MU, bool PLAQ>
+__device__ __forceinline__ void staple_sum(const Links<T>& U, const EoSite& s, uint32_t i, int p,
+                                           Quat<T>& A, Quat<T>& P)
+{
+    const int q = p ^ 1;
+    int hp[4], hm[4];
+    s.hops(hp, hm);
+    const uint32_t e_pmu = i + hp[MU];
+    A = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == MU) continue;
+        const uint32_t e_pnu = i + hp[nu];
+        const uint32_t e_mnu = i + hm[nu];
+        const uint32_t e_pmu_mnu = i + hp[MU] + hm[nu];
+        const Quat<T> a = U.load(nu, q, e_pmu);      // U_nu(x+mu)
+        const Quat<T> b = U.load(MU, q, e_pnu);      // U_mu(x+nu)
+        const Quat<T> c = U.load(nu, p, i);          // U_nu(x)
+        const Quat<T> d = U.load(nu, p, e_pmu_mnu);  // U_nu(x+mu-nu)
+        const Quat<T> e = U.load(MU, q, e_mnu);      // U_mu(x-nu)
+        const Quat<T> f = U.load(nu, q, e_mnu);      // U_nu(x-nu)
+        const Quat<T> up = qmul_nd(qmul_nd(a, b), c);
+        const Quat<T> lo = qmul(qmul_dd(d, e), f);
+        A = qadd(A, qadd(up, lo));
+        if (PLAQ && nu == MU - 1) P = A;
+    }
+}
+
+// One Kennedy-Pendleton trial from the four words of a Philox block:
+// lambda^2 = -(ln r1 + cos^2(2 pi r2) ln r3) / (2 alpha), delta = 2 lambda^2,
+// accepted iff r4^2 <= 1 - lambda^2.
+template <typename T>
+__device__ __forceinline__ bool kp_try(const U4& w, T inv2a, T* d)
+{
+    const T r1 = u01<T>(w.x), r2 = u01<T>(w.y), r3 = u01<T>(w.z), r4 = u01<T>(w.w);
+    const T lam2 = -(Math<T>::ln_u01(r1) + Math<T>::cos2pi_sq(r2) * Math<T>::ln_u01(r3)) * inv2a;
+    *d = T(2) * lam2;
+    return r4 * r4 <= T(1) - lam2;
+}
+
+// One trial of Creutz's draw (small alpha): a0 from exp(alpha a0) by
+// inversion, delta = -ln(1 - r1 qc) / alpha with qc = 1 - exp(-2 alpha),
+// accepted with probability sqrt(1 - a0^2) = sqrt(delta (2 - delta)); the
+// same trial blocks, r1 = word 0, r4 = word 3.
+template <typename T>
+__device__ __forceinline__ bool creutz_try(const U4& w, T qc, T inv2a, T* d)
+{
+    const T r1 = u01<T>(w.x), r4 = u01<T>(w.w);
+    *d = -Math<T>::log1p(-r1 * qc) * (T(2) * inv2a);
+    return r4 * r4 <= *d * (T(2) - *d);
+}
+
+// The accepted draw X = (1 - delta, sqrt(delta (2 - delta)) n) with the
+// direction n from the spare bits kd1, kd2 of the first trial block, and
+// the new link U = X A^dagger / |A|, renormalised.
+template <typename T>
+__device__ __forceinline__ Quat<T> new_link(T delta, uint32_t kd1, uint32_t kd2, const Quat<T>& A)
+{
+    const T cth = T(2) * u18<T>(kd1) - T(1);
+    const T sth = Math<T>::sqrt_pos((T(1) - cth) * (T(1) + cth));
+    T sph, cph;
+    Math<T>::sincos2pi(u18<T>(kd2), &sph, &cph);
+    const T vl = Math<T>::sqrt_pos(delta * (T(2) - delta));
+    const Quat<T> X = {T(1) - delta, vl * sth * cph, vl * sth * sph, vl * cth};
+    return qnormalise(qmul_nd(X, A));
+}
+
+// the spare low 9 bits of the first trial's four words: two 18-bit uniforms
+__device__ __forceinline__ uint32_t spare_bits_1(const U4& w) { return ((w.x & 511u) << 9) | (w.y & 511u); }
+__device__ __forceinline__ uint32_t spare_bits_2(const U4& w) { return ((w.z & 511u) << 9) | (w.w & 511u); }
+
+// Totals of one warp without any block barrier (a warp never waits for the
+// block's slowest warp): trial counts go to spread per-lattice atomic slots
+// (exact integers), cap hits to an atomic only when present, the
+// plaquette to one partial per warp, summed later in a fixed order.
+template <typename T, int MU, bool PLAQ, int NT>
+__device__ __forceinline__ void warp_totals(const Ctx& ctx, int l, uint32_t blk0, uint32_t Vh,
+                                            T plaq, uint32_t ntrial, uint32_t ncap)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t wt = __reduce_add_sync(0xffffffffu, ntrial);
+    const uint32_t wc = __reduce_add_sync(0xffffffffu, ncap);
+    T wp = T(0);
+    if (PLAQ) wp = warp_sum_t(plaq);
+    if (lane == 0) {
+        const uint32_t gw = blockIdx.x * (NT / 32) + w;  // global warp index
+        if (PLAQ)
+            ctx.plaq_partial[(size_t)(MU - 1) * ctx.phase_blocks * (NT / 32) + gw] = (double)wp;
+        atomicAdd(ctx.trial_slots + (size_t)l * TRIAL_SLOTS + (gw % TRIAL_SLOTS),
+                  (unsigned long long)wt);
+        LatDesc* Dw = ctx.desc + l;
+        if (w == 0 && blockIdx.x == blk0) atomicAdd(&Dw->updates, (unsigned long long)Vh);
+        if (wc) {
+            atomicAdd(&Dw->caps, (unsigned long long)wc);
+            atomicOr(ctx.status, STATUS_CAP_HIT);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one link per thread
+// ---------------------------------------------------------------------------
 template <typename T, int MU, bool PLAQ, bool DBG, int NT, int MINB, bool SLAB, bool HYB>
 __global__ void __launch_bounds__(NT, MINB)
 hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
@@ -61,41 +172,16 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const uint32_t Vh = D.Vh;
     const uint32_t blk0 = __ldg(ctx.phase_start + l);
     const uint32_t j = (blockIdx.x - blk0) * NT + threadIdx.x;  // traversal position
-    const bool active = j < Vh;
     const Links<T> U(ctx.links, D);
-    const int q = p ^ 1;
 
     T plaq = T(0);
-    uint32_t ntrial = 0;
-    bool ncap = false;
+    uint32_t ntrial = 0, ncap = 0;
 
-    if (active) {
+    if (j < Vh) {
         uint32_t i = j;  // storage index of the site
         const EoSite s = SLAB ? EoSite::from_slab(D, j, p, &i) : EoSite(D, j, p);
-        int hp[4], hm[4];
-        s.hops(hp, hm);
-        const uint32_t e_pmu = i + hp[MU];
-
-        Quat<T> A = {T(0), T(0), T(0), T(0)};
-        Quat<T> Sp[MU > 0 ? MU : 1];
-#pragma unroll
-        for (int nu = 0; nu < 4; ++nu) {
-            if (nu == MU) continue;
-            const uint32_t e_pnu = i + hp[nu];
-            const uint32_t e_mnu = i + hm[nu];
-            const uint32_t e_pmu_mnu = i + hp[MU] + hm[nu];
-            const Quat<T> a = U.load(nu, q, e_pmu);      // U_nu(x+mu)
-            const Quat<T> b = U.load(MU, q, e_pnu);      // U_mu(x+nu)
-            const Quat<T> c = U.load(nu, p, i);          // U_nu(x)
-            const Quat<T> d = U.load(nu, p, e_pmu_mnu);  // U_nu(x+mu-nu)
-            const Quat<T> e = U.load(MU, q, e_mnu);      // U_mu(x-nu)
-            const Quat<T> f = U.load(nu, q, e_mnu);      // U_nu(x-nu)
-            const Quat<T> up = qmul_nd(qmul_nd(a, b), c);
-            const Quat<T> lo = qmul(qmul_dd(d, e), f);
-            const Quat<T> S = qadd(up, lo);
-            A = qadd(A, S);
-            if (PLAQ && nu < MU) Sp[nu < MU ? nu : 0] = S;
-        }
+        Quat<T> A, P;
+        staple_sum<T, MU, PLAQ>(U, s, i, p, A, P);
 
         // alpha = beta k and 1/(2 alpha) from one reciprocal square root of k^2
         const T k2 = qnorm2(A);
@@ -117,112 +203,228 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             T delta = T(0);
             tr = -1;
             // trial 0 also carries the direction in the low 9 bits of its words
-            U4 w = st.draw(TAG_TRIAL, 0u);
-            const uint32_t kd1 = ((w.x & 511u) << 9) | (w.y & 511u);
-            const uint32_t kd2 = ((w.z & 511u) << 9) | (w.w & 511u);
+            const U4 w = st.draw(TAG_TRIAL, 0u);
+            const uint32_t kd1 = spare_bits_1(w), kd2 = spare_bits_2(w);
             if (HYB && alpha < creutz_of<T>(D)) {
-                // Creutz's draw (small alpha, where Kennedy-Pendleton accepts
-                // rarely): a0 from exp(alpha a0) by inversion, accepted with
-                // sqrt(1 - a0^2); the same trial blocks, r1 = word 0, r4 = word 3
-                const T q = -Math<T>::expm1(T(-2) * alpha);
+                const T qc = -Math<T>::expm1(T(-2) * alpha);
                 for (int t = 0; t < KP_CAP; ++t) {
-                    const U4 ww = t == 0 ? w : st.draw(TAG_TRIAL, (uint32_t)t);
-                    const T r1 = u01<T>(ww.x), r4 = u01<T>(ww.w);
-                    const T d = -Math<T>::log1p(-r1 * q) * (T(2) * inv2a);
-                    if (r4 * r4 <= d * (T(2) - d)) {
-                        delta = d;
+                    if (creutz_try(t == 0 ? w : st.draw(TAG_TRIAL, (uint32_t)t), qc, inv2a, &delta)) {
                         tr = t + 1;
                         break;
                     }
                 }
+            } else if (kp_try(w, inv2a, &delta)) {
+                tr = 1;
             } else {
-                auto kp_try = [&](const U4& ww, T* d) -> bool {
-                    const T r1 = u01<T>(ww.x), r2 = u01<T>(ww.y), r3 = u01<T>(ww.z),
-                            r4 = u01<T>(ww.w);
-                    const T lam2 = -(Math<T>::ln_u01(r1) + Math<T>::cos2pi_sq(r2) *
-                                     Math<T>::ln_u01(r3)) * inv2a;
-                    *d = T(2) * lam2;
-                    return r4 * r4 <= T(1) - lam2;
-                };
-                if (kp_try(w, &delta)) {
-                    tr = 1;
-                } else {
-                    for (int t = 1; t < KP_CAP; ++t) {
-                        if (kp_try(st.draw(TAG_TRIAL, (uint32_t)t), &delta)) {
-                            tr = t + 1;
-                            break;
-                        }
+                for (int t = 1; t < KP_CAP; ++t) {
+                    if (kp_try(st.draw(TAG_TRIAL, (uint32_t)t), inv2a, &delta)) {
+                        tr = t + 1;
+                        break;
                     }
                 }
             }
-            if (tr > 0) {
-                const T cth = T(2) * u18<T>(kd1) - T(1);
-                const T sth = Math<T>::sqrt_pos((T(1) - cth) * (T(1) + cth));
-                T sph, cph;
-                Math<T>::sincos2pi(u18<T>(kd2), &sph, &cph);
-                const T vl = Math<T>::sqrt_pos(delta * (T(2) - delta));
-                const Quat<T> X = {T(1) - delta, vl * sth * cph, vl * sth * sph, vl * cth};
-                un = qnormalise(qmul_nd(X, A));
-            }
+            if (tr > 0) un = new_link(delta, kd1, kd2, A);
         }
         if (tr >= 0) {
             U.store(MU, p, i, un);
         } else {
-            ncap = true;
+            ncap = 1;
             if (PLAQ) un = U.load_rw(MU, p, i);
         }
         ntrial = tr > 0 ? (uint32_t)tr : (tr < 0 ? (uint32_t)KP_CAP : 0u);
         if (DBG) dbg[s.lex()] = tr;
-
-        if (PLAQ) {
-#pragma unroll
-            for (int nu = 0; nu < MU; ++nu) plaq += qretr(un, Sp[nu]);
-        }
+        if (PLAQ) plaq = qretr(un, P);
     }
-
-    // Totals without any block barrier (a warp never waits for the
-    // block's slowest warp): trial counts go to spread per-lattice atomic
-    // slots (exact integers), cap hits to an atomic only when present, the
-    // plaquette to one partial per warp, summed later in a fixed order.
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t wt = __reduce_add_sync(0xffffffffu, ntrial);
-    const uint32_t capmask = __ballot_sync(0xffffffffu, ncap);
-    T wp = T(0);
-    if (PLAQ) wp = warp_sum_t(plaq);
-    if (lane == 0) {
-        const uint32_t gw = blockIdx.x * (NT / 32) + w;  // global warp index
-        if (PLAQ)
-            ctx.plaq_partial[(size_t)(MU - 1) * ctx.phase_blocks * (NT / 32) + gw] = (double)wp;
-        atomicAdd(ctx.trial_slots + (size_t)l * TRIAL_SLOTS + (gw % TRIAL_SLOTS),
-                  (unsigned long long)wt);
-        LatDesc* Dw = ctx.desc + l;
-        if (w == 0 && blockIdx.x == blk0) atomicAdd(&Dw->updates, (unsigned long long)Vh);
-        if (capmask) {
-            atomicAdd(&Dw->caps, (unsigned long long)__popc(capmask));
-            atomicOr(ctx.status, STATUS_CAP_HIT);
-        }
-    }
+    warp_totals<T, MU, PLAQ, NT>(ctx, l, blk0, Vh, plaq, ntrial, ncap);
 }
 
-// One launch shape (NT threads per block, at least MINB blocks per SM) of
-// the phase kernel; the grid covers ctx.phase_blocks blocks of NT links.
-template <typename T, int NT, int MINB, bool SLAB>
+// ---------------------------------------------------------------------------
+// R links per thread with a per-warp retry queue
+// ---------------------------------------------------------------------------
+// With one link per thread a warp repeats the trial loop until its last
+// lane accepts, so a pass over Philox and the Kennedy-Pendleton test runs
+// with most lanes idle.  Here a thread walks R links (R rounds of the
+// block's NT consecutive positions); a link whose first trial is rejected
+// leaves its staple and state in a per-warp queue in shared memory, and
+// the warp retries queued links 32 at a time (one per lane) whenever 32
+// are waiting, and once more after its last round.  Each link still takes
+// the first accepted trial of its own sequence t = 0, 1, ..., so the links
+// are bit-identical to those of the kernel above.
+template <typename T, bool PLAQ, bool HYB>
+struct RetryQueue {
+    static constexpr int CAP = 64;  // < 32 held before a push of at most 32
+    T a[4][CAP];                    // staple sum A
+    T pl[PLAQ ? 4 : 1][PLAQ ? CAP : 1];  // its plaquette part P
+    T inv2a[CAP];                   // 1 / (2 alpha)
+    T qc[HYB ? CAP : 1];            // Creutz: 1 - exp(-2 alpha); 0: Kennedy-Pendleton
+    uint32_t key[CAP];              // Philox counter word lex * 4 + mu
+    uint32_t tk[CAP];               // next trial | first 18-bit direction word << 13
+    uint32_t kd2[CAP];              // second 18-bit direction word
+    uint32_t site[CAP];             // storage index
+};
+
+template <typename T, int MU, bool PLAQ, bool DBG, int NT, int MINB, bool SLAB, bool HYB, int R>
+__global__ void __launch_bounds__(NT, MINB)
+hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
+{
+    static_assert(KP_CAP <= (1 << 13), "trial index must fit 13 bits");
+    using Queue = RetryQueue<T, PLAQ, HYB>;
+    __shared__ Queue sq[NT / 32];
+
+    const int l = lattice_of_block(ctx.phase_start, ctx.n, blockIdx.x);
+    const LatDesc& D = ctx.desc[l];
+    const uint32_t Vh = D.Vh;
+    const uint32_t blk0 = __ldg(ctx.phase_start + l);
+    const uint32_t j0 = (blockIdx.x - blk0) * (NT * R) + threadIdx.x;
+    const Links<T> U(ctx.links, D);
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    Queue& Q = sq[threadIdx.x >> 5];
+    const T beta = beta_of<T>(D);
+    const uint64_t sw = D.sweep;
+    const uint32_t k0 = (uint32_t)D.seed, k1 = (uint32_t)(D.seed >> 32);
+    const uint32_t slo = (uint32_t)sw, shi = (uint32_t)(sw >> 32);
+
+    T plaq = T(0);
+    uint32_t ntrial = 0, ncap = 0;
+    int cnt = 0;  // queued links (warp-uniform)
+
+    // a final link: store, plaquette, trial count
+    auto put = [&](uint32_t i, uint32_t key, const Quat<T>& un, const Quat<T>& P, int32_t tr) {
+        U.store(MU, p, i, un);
+        if (PLAQ) plaq += qretr(un, P);
+        ntrial += (uint32_t)tr;
+        if (DBG) dbg[key >> 2] = tr;
+    };
+    auto push = [&](bool pend, const Quat<T>& A, const Quat<T>& P, T inv2a, T qc, uint32_t key,
+                    uint32_t tk, uint32_t kd2, uint32_t i) {
+        const uint32_t m = __ballot_sync(0xffffffffu, pend);
+        if (pend) {
+            const int e = cnt + __popc(m & below);
+            Q.a[0][e] = A.a0; Q.a[1][e] = A.a1; Q.a[2][e] = A.a2; Q.a[3][e] = A.a3;
+            if (PLAQ) { Q.pl[0][e] = P.a0; Q.pl[1][e] = P.a1; Q.pl[2][e] = P.a2; Q.pl[3][e] = P.a3; }
+            Q.inv2a[e] = inv2a;
+            if (HYB) Q.qc[e] = qc;
+            Q.key[e] = key;
+            Q.tk[e] = tk;
+            Q.kd2[e] = kd2;
+            Q.site[e] = i;
+        }
+        cnt += __popc(m);
+        __syncwarp();
+    };
+    // one trial for each of the last n queued links, one link per lane
+    auto retry = [&](int n) {
+        const bool have = lane < n;
+        Quat<T> A = {T(0), T(0), T(0), T(0)}, P = A;
+        T inv2a = T(0), qc = T(0);
+        uint32_t key = 0, tk = 0, kd2 = 0, i = 0;
+        if (have) {
+            const int e = cnt - n + lane;
+            A = {Q.a[0][e], Q.a[1][e], Q.a[2][e], Q.a[3][e]};
+            if (PLAQ) P = {Q.pl[0][e], Q.pl[1][e], Q.pl[2][e], Q.pl[3][e]};
+            inv2a = Q.inv2a[e];
+            if (HYB) qc = Q.qc[e];
+            key = Q.key[e];
+            tk = Q.tk[e];
+            kd2 = Q.kd2[e];
+            i = Q.site[e];
+        }
+        __syncwarp();
+        cnt -= n;
+        bool pend = false;
+        if (have) {
+            const uint32_t t = tk & 0x1FFFu, kd1 = tk >> 13;
+            const Stream st{k0, k1, key, slo, shi};
+            const U4 w = st.draw(TAG_TRIAL, t);
+            T delta;
+            const bool ok = (HYB && qc > T(0)) ? creutz_try(w, qc, inv2a, &delta)
+                                               : kp_try(w, inv2a, &delta);
+            if (ok) {
+                put(i, key, new_link(delta, kd1, kd2, A), P, (int32_t)t + 1);
+            } else if (t + 1 >= (uint32_t)KP_CAP) {
+                // cap hit: the link keeps its value
+                ncap += 1;
+                ntrial += (uint32_t)KP_CAP;
+                if (PLAQ) plaq += qretr(U.load_rw(MU, p, i), P);
+                if (DBG) dbg[key >> 2] = -1;
+            } else {
+                pend = true;
+                tk = (t + 1) | (kd1 << 13);
+            }
+        }
+        push(pend, A, P, inv2a, qc, key, tk, kd2, i);
+    };
+
+    for (int r = 0; r < R; ++r) {
+        const uint32_t j = j0 + (uint32_t)r * NT;
+        bool pend = false;
+        Quat<T> A = {T(0), T(0), T(0), T(0)}, P = A;
+        T inv2a = T(0), qc = T(0);
+        uint32_t key = 0, tk = 0, kd2 = 0, i = j;
+        if (j < Vh) {
+            const EoSite s = SLAB ? EoSite::from_slab(D, j, p, &i) : EoSite(D, j, p);
+            staple_sum<T, MU, PLAQ>(U, s, i, p, A, P);
+            const T k2 = qnorm2(A);
+            const T rk = Math<T>::rsqrt(k2);
+            const T alpha = beta * k2 * rk;
+            key = s.lex() * 4u + MU;
+            const Stream st{k0, k1, key, slo, shi};
+            if (!(alpha >= alpha_haar<T>())) {
+                put(i, key, haar_from<T>(st.draw(TAG_DIRECTION, 0)), P, 0);
+            } else {
+                inv2a = T(0.5) * rk / beta;
+                const U4 w = st.draw(TAG_TRIAL, 0u);
+                const uint32_t kd1 = spare_bits_1(w);
+                kd2 = spare_bits_2(w);
+                T delta;
+                bool ok;
+                if (HYB && alpha < creutz_of<T>(D)) {
+                    qc = -Math<T>::expm1(T(-2) * alpha);
+                    ok = creutz_try(w, qc, inv2a, &delta);
+                } else {
+                    ok = kp_try(w, inv2a, &delta);
+                }
+                if (ok) {
+                    put(i, key, new_link(delta, kd1, kd2, A), P, 1);
+                } else {
+                    pend = true;
+                    tk = 1u | (kd1 << 13);
+                }
+            }
+        }
+        push(pend, A, P, inv2a, qc, key, tk, kd2, i);
+        while (cnt >= 32) retry(32);
+    }
+    while (cnt > 0) retry(cnt < 32 ? cnt : 32);
+    warp_totals<T, MU, PLAQ, NT>(ctx, l, blk0, Vh, plaq, ntrial, ncap);
+}
+
+// One launch shape (NT threads per block, at least MINB blocks per SM, R
+// links per thread) of the phase kernel; the grid covers ctx.phase_blocks
+// blocks of NT R links.
+template <typename T, int NT, int MINB, bool SLAB, int R = 1>
 cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int32_t* dbg,
                                bool hyb, cudaStream_t s)
 {
     // the fused plaquette exists only in the odd phases with mu >= 1
     const bool pl = plaq && parity == 1 && mu >= 1;
     const dim3 grid(c.phase_blocks), block(NT);
-#define SU2_LAUNCH_H(MUV, H)                                                                     \
-    do {                                                                                         \
-        if (dbg) hb_phase_kernel<T, MUV, false, true, NT, MINB, SLAB, H><<<grid, block, 0, s>>>(c, parity, dbg); \
-        else if (pl) hb_phase_kernel<T, MUV, (MUV > 0), false, NT, MINB, SLAB, H><<<grid, block, 0, s>>>(c, parity, dbg); \
-        else hb_phase_kernel<T, MUV, false, false, NT, MINB, SLAB, H><<<grid, block, 0, s>>>(c, parity, dbg); \
+#define SU2_K(MUV, PL, DB, H)                                                                   \
+    if constexpr (R == 1)                                                                       \
+        hb_phase_kernel<T, MUV, PL, DB, NT, MINB, SLAB, H><<<grid, block, 0, s>>>(c, parity, dbg); \
+    else                                                                                        \
+        hb_phase_queue_kernel<T, MUV, PL, DB, NT, MINB, SLAB, H, R><<<grid, block, 0, s>>>(c, parity, dbg)
+#define SU2_LAUNCH_H(MUV, H)                                    \
+    do {                                                        \
+        if (dbg) { SU2_K(MUV, false, true, H); }                \
+        else if (pl) { SU2_K(MUV, (MUV > 0), false, H); }       \
+        else { SU2_K(MUV, false, false, H); }                   \
     } while (0)
-#define SU2_LAUNCH(MUV)                 \
-    do {                                \
-        if (hyb) SU2_LAUNCH_H(MUV, true);  \
-        else SU2_LAUNCH_H(MUV, false);  \
+#define SU2_LAUNCH(MUV)                   \
+    do {                                  \
+        if (hyb) SU2_LAUNCH_H(MUV, true); \
+        else SU2_LAUNCH_H(MUV, false);    \
     } while (0)
     switch (mu) {
     case 0: SU2_LAUNCH(0); break;
@@ -232,6 +434,7 @@ cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int3
     }
 #undef SU2_LAUNCH
 #undef SU2_LAUNCH_H
+#undef SU2_K
     return cudaGetLastError();
 }
 

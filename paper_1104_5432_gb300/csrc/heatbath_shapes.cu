@@ -1,0 +1,34 @@
+// heatbath_shapes.cu -- phase-kernel instantiations for two launch shapes
+// of one precision.  The build compiles this file once per pair, with
+// SU2_ROW = 0 (FP32) or 1 (FP64) and SU2_FIRST the first shape index of
+// the pair, so that the shapes compile in parallel.
+#include <type_traits>
+
+#include "heatbath_kernel.cuh"
+
+#if !defined(SU2_ROW) || !defined(SU2_FIRST)
+#error "compile with -DSU2_ROW=<0|1> -DSU2_FIRST=<even shape index>"
+#endif
+
+namespace su2 {
+
+template <int ROW, int FIRST>
+cudaError_t launch_phase_pair(const Ctx& c, int cfg, int mu, int parity, bool plaq, int32_t* dbg,
+                              bool hyb, cudaStream_t s)
+{
+    using T = typename std::conditional<ROW == 0, float, double>::type;
+    constexpr LaunchCfg A = LAUNCH_CFG[ROW][FIRST];
+    constexpr LaunchCfg B = LAUNCH_CFG[ROW][FIRST + 1];
+    if (cfg == FIRST)
+        return launch_phase_shape<T, A.threads, A.min_blocks, A.slab, A.rounds>(c, mu, parity, plaq,
+                                                                               dbg, hyb, s);
+    if (cfg == FIRST + 1)
+        return launch_phase_shape<T, B.threads, B.min_blocks, B.slab, B.rounds>(c, mu, parity, plaq,
+                                                                               dbg, hyb, s);
+    return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_phase_pair<SU2_ROW, SU2_FIRST>(const Ctx&, int, int, int, bool, int32_t*,
+                                                           bool, cudaStream_t);
+
+}  // namespace su2

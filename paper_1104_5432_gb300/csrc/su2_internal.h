@@ -26,18 +26,28 @@ constexpr int TPB = 256;            // threads per block of the non-phase kernel
 // FP32, row 1: FP64.
 // slab: walk large lattices in y slabs (EoSite::from_slab) -- FP32 only,
 // since the FP64 kernel is bound by its arithmetic, not by re-reads.
+// rounds: links per thread; above 1 the kernel with the per-warp retry
+// queue (hb_phase_queue_kernel) runs.
 struct LaunchCfg {
     int threads, min_blocks;
     bool slab;
+    int rounds;
 };
-constexpr int NUM_LAUNCH_CFG = 8;
-// Small blocks (64, 32 threads) spread tiny lattices over more SMs.
+constexpr int NUM_LAUNCH_CFG = 14;
+// Small blocks (64, 32 threads) spread tiny lattices over more SMs; several
+// links per thread pay off on large lattices (one queue pass retries 32
+// rejected trials at once) but leave small ones with too few blocks.
 constexpr LaunchCfg LAUNCH_CFG[2][NUM_LAUNCH_CFG] = {
-    {{256, 4, false}, {256, 3, false}, {128, 8, false}, {512, 2, false},
-     {256, 4, true}, {128, 8, true}, {64, 16, false}, {32, 32, false}},
-    {{256, 1, false}, {256, 2, false}, {128, 4, false}, {128, 1, false},
-     {64, 8, false}, {64, 4, false}, {32, 16, false}, {32, 8, false}},
+    {{256, 4, false, 1}, {128, 8, false, 1}, {64, 16, false, 1}, {32, 32, false, 1},
+     {256, 4, true, 1}, {128, 8, true, 1}, {32, 32, false, 2}, {32, 32, false, 4},
+     {32, 32, false, 8}, {32, 32, false, 16}, {64, 16, false, 8}, {128, 8, false, 8},
+     {32, 32, true, 8}, {128, 8, true, 8}},
+    {{256, 1, false, 1}, {128, 4, false, 1}, {64, 8, false, 1}, {64, 4, false, 1},
+     {32, 16, false, 1}, {32, 8, false, 1}, {32, 16, false, 2}, {32, 16, false, 4},
+     {32, 16, false, 8}, {32, 16, false, 16}, {32, 16, false, 32}, {64, 8, false, 16},
+     {32, 8, false, 16}, {128, 4, false, 16}},
 };
+static_assert(NUM_LAUNCH_CFG % 2 == 0, "shapes compile in pairs");
 // largest y-slab window (sites between a site and its t neighbour, times
 // the bytes a site's update touches) kept in L2
 constexpr double SLAB_WINDOW_BYTES = 32.0 * (1 << 20);

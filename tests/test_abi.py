@@ -91,7 +91,7 @@ def test_tune_cache_round_trip(tmp_path):
     assert lib.su2_tune_cache_store(path, b"gpu|f32|n1|V256|00ff", 3, 0.2) == 0
     assert lib.su2_tune_cache_lookup(path, b"gpu|f32|n1|V256|00ff", C.byref(cfg)) == 1
     assert cfg.value == 3
-    assert lib.su2_tune_cache_store(path, b"k", 9, 0.1) == su2.SU2_E_INVAL
+    assert lib.su2_tune_cache_store(path, b"k", 14, 0.1) == su2.SU2_E_INVAL
 
 
 def test_tune_key_and_launch_config_host_side():
@@ -108,10 +108,11 @@ def test_tune_key_and_launch_config_host_side():
     cfg, thr, mb = C.c_int(), C.c_int(), C.c_int()
     assert lib.su2_get_launch_config(h, C.byref(cfg), C.byref(thr), C.byref(mb)) == 0
     assert (cfg.value, thr.value) == (0, 256)
-    assert lib.su2_set_launch_config(h, 2) == 0
+    assert lib.su2_set_launch_config(h, 1) == 0
     assert lib.su2_get_launch_config(h, C.byref(cfg), C.byref(thr), C.byref(mb)) == 0
-    assert (cfg.value, thr.value, mb.value) == (2, 128, 8)
-    assert lib.su2_set_launch_config(h, 8) == su2.SU2_E_INVAL
+    assert (cfg.value, thr.value, mb.value) == (1, 128, 8)
+    assert lib.su2_set_launch_config(h, 14) == su2.SU2_E_INVAL
+    assert lib.su2_set_launch_config(h, -1) == su2.SU2_E_INVAL
     lib.su2_lattice_destroy(h)
 
 
@@ -121,7 +122,8 @@ def test_launch_shape_mirror_matches_library():
     for dtype, table in ((su2.F32, _F32), (su2.F64, _F64)):
         h = C.c_void_p()
         assert lib.su2_lattice_create(4, 4, dtype, C.byref(h)) == 0
-        for k, (t, m, _) in enumerate(table):
+        assert len(table) == 14
+        for k, (t, m, _, _) in enumerate(table):
             assert lib.su2_set_launch_config(h, k) == 0
             cfg, thr, mb = C.c_int(), C.c_int(), C.c_int()
             lib.su2_get_launch_config(h, C.byref(cfg), C.byref(thr), C.byref(mb))

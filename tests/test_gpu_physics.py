@@ -101,7 +101,13 @@ def test_long_run_ensembles_agree():
 
 @pytest.mark.parametrize("dtype", [su2.F32, su2.F64])
 def test_strong_coupling_gpu(dtype):
+    """<P>(beta = 0.5) = I2(beta)/I1(beta), with the Creutz/Kennedy-Pendleton
+    hybrid: at beta = 0.5 alpha = beta k is often small, where Kennedy-
+    Pendleton's acceptance falls like alpha^(3/2) and a link may exhaust the
+    4096-trial cap over 3.5e7 updates; Creutz's draw accepts with
+    probability >= pi/4 there."""
     lat = su2.Lattice(12, 12, dtype)
+    lat.set_sampler(1.7)
     lat.init(su2.HOT, 5)
     p = lat.heatbath(0.5, 420, 5)[0][20:]
     m, e = jackknife_mean(p, 20)

@@ -239,10 +239,17 @@ def gpu_arm(args, rank, world, local):
     hbm, peak_kind = peaks()
     bytes_launch = BYTES_PER_UPDATE["f32"] * (V // 2)
     achieved = bytes_launch / phase_s / 1e9
+    from paper_1104_5432_gb300.csrc_info import _F32, launch_shapes
+    shape = lat.launch_config()[0]
+    kname = "hb_phase_queue_kernel<float>" if _F32[shape][3] > 1 else "hb_phase_kernel<float>"
     traffic = recorded_traffic("f32_64^4")
+    traffic_shape = recorded_traffic("f32_64^4", "launch_shape")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic,
-                "kernel": "hb_phase_kernel<float> (one checkerboard phase, V/2 link updates)",
+                "traffic_captured_on": None if traffic is None else
+                f"launch shape {traffic_shape} ({launch_shapes(False)[traffic_shape]})",
+                "kernel": f"{kname}, launch shape {shape} ({launch_shapes(False)[shape]}): one "
+                          "checkerboard phase, V/2 link updates",
                 "bytes_per_launch": bytes_launch, "launch_ms": round(phase_s * 1e3, 4),
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
                 "measured" else "fallback 6.8 TB/s"}
@@ -340,6 +347,8 @@ def gpu_arm(args, rank, world, local):
         cs_dev = torch.zeros(len(scan) * (rmax + 1), dtype=torch.float64, device="cuda")
         Vs_tot = sum(e["Ns"] ** 3 * e["Nt"] for e in full_scan)
 
+        tuned["fp32_temperature_scan"] = S.autotune()
+
         def step_scan():
             S.batch_init(su2.HOT, ss)
             S.batch_heatbath(sb, n_therm, ss, plaq=None)
@@ -389,7 +398,7 @@ def gpu_arm(args, rank, world, local):
         # ---- FP32 128^4 (16 GiB of links) -----------------------------------------
         big = su2.Lattice(128, 128, su2.F32)
         tuned["fp32_128^4"] = big.autotune()
-        sw_big = 5
+        sw_big = 10
         pl_big = torch.zeros(sw_big, dtype=torch.float64, device="cuda")
 
         def step_big():
@@ -399,7 +408,7 @@ def gpu_arm(args, rank, world, local):
         tbig = time_steps(step_big, 2, 1)
         big.sync()
         arms["fp32_128^4"] = {"value": world * 4 * 128 ** 4 * sw_big * 2 / tbig, "unit": UNIT,
-                              "workload": "SU(2) 128^4, beta=2.5, hot start, 5 sweeps + "
+                              "workload": "SU(2) 128^4, beta=2.5, hot start, 10 sweeps + "
                                           "plaquette per sweep per step, FP32 links (16 GiB)",
                               "traffic_per_launch_slab": recorded_traffic("f32_128^4_slab"),
                               "algorithmic_bytes_per_launch": 128 * 128 ** 4 // 2,

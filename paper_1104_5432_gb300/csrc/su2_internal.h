@@ -50,7 +50,7 @@ constexpr LaunchCfg LAUNCH_CFG[2][NUM_LAUNCH_CFG] = {
 static_assert(NUM_LAUNCH_CFG % 2 == 0, "shapes compile in pairs");
 // largest y-slab window (sites between a site and its t neighbour, times
 // the bytes a site's update touches) kept in L2
-constexpr double SLAB_WINDOW_BYTES = 32.0 * (1 << 20);
+constexpr double SLAB_WINDOW_BYTES = 16.0 * (1 << 20);
 
 constexpr int KP_CAP = 4096;        // Kennedy-Pendleton trial cap
 constexpr int PLAQ_RING = 4096;     // per-lattice plaquette slots for host output

@@ -464,6 +464,82 @@ def test_full_size_128_properties():
     torch.cuda.empty_cache()
 
 
+QUEUED = [(su2.F32, 6), (su2.F32, 8), (su2.F32, 12), (su2.F64, 6), (su2.F64, 10)]
+
+
+@pytest.mark.parametrize("dtype,cfg", QUEUED)
+def test_queued_shapes_hybrid_and_trial_output(dtype, cfg):
+    """The queued kernel (several links per thread, rejected trials retried
+    from a per-warp queue) on ragged batches whose phases are not multiples
+    of its links per block: with the Creutz hybrid it matches the one-link
+    kernel bit for bit, and its per-link trial output matches the oracle."""
+    shapes = [(6, 2), (10, 4), (4, 6)]
+    seeds, betas = [61, 62, 63], [0.7, 1.9, 2.6]
+
+    def run(c):
+        B = su2.Lattice([s[0] for s in shapes], [s[1] for s in shapes], dtype)
+        B.set_launch_config(c)
+        B.set_sampler(1.7)
+        B.batch_init(su2.HOT, seeds)
+        plaq = B.batch_heatbath(betas, 2, seeds)
+        return B, plaq
+
+    A, pa = run(0)
+    Q, pq = run(cfg)
+    for l in range(len(shapes)):
+        np.testing.assert_array_equal(Q.get_links(l), A.get_links(l))
+        assert Q.stats(l) == A.stats(l)
+    np.testing.assert_allclose(pq, pa, rtol=0, atol=1e-6 if dtype == su2.F32 else 1e-13)
+    # per-link trial counts of single phases under the queued shape
+    Ns, Nt = 10, 4
+    V = Ns ** 3 * Nt
+    par = parity_mask(Ns, Nt)
+    lat = lattice(Ns, Nt, dtype)
+    lat.set_launch_config(cfg)
+    lat.init(su2.HOT, 64)
+    flips = n = 0
+    for beta, creutz in ((2.3, 0.0), (0.6, 1.7)):
+        lat.set_sampler(creutz)
+        for mu, p in PHASES:
+            before = lat.get_links()
+            sweep = lat.get_sweep()
+            trials = torch.full((V,), -2, dtype=torch.int32, device="cuda")
+            lat.heatbath_phase(beta, mu, p, 65, trials)
+            ref, rt, _ = O.heatbath_phase(Ns, Nt, before, beta, mu, p, 65, sweep,
+                                          creutz_below=creutz)
+            gt = trials.cpu().numpy()
+            assert np.all(gt[par != p] == -2)
+            same = gt[par == p] == rt[par == p, mu]
+            diff = np.max(np.abs(lat.get_links()[par == p, mu] - ref[par == p, mu]), axis=1)
+            if dtype == su2.F64:
+                assert np.all(same) and diff.max() <= 1e-12, (beta, mu, p)
+            else:
+                assert diff[same].max() <= 2e-5
+                flips += int((~same).sum())
+                n += int(same.size)
+    assert flips <= max(1e-4 * n, 1)
+
+
+@pytest.mark.parametrize("dtype,cfg", [(su2.F32, 8), (su2.F64, 9)])
+def test_queued_shapes_cap_hit(dtype, cfg):
+    """beta = 1e-9 under plain Kennedy-Pendleton: every queued link runs to
+    the 4096-trial cap through the retry queue, keeps its value and is
+    counted once."""
+    Ns, Nt = 4, 4
+    V = Ns ** 3 * Nt
+    lat = lattice(Ns, Nt, dtype)
+    lat.set_launch_config(cfg)
+    lat.init(su2.HOT, 3)
+    before = lat.get_links()
+    lat.heatbath(1e-9, 1, 3, plaq=None)
+    with pytest.raises(su2.SU2Error) as e:
+        lat.sync()
+    assert e.value.code == su2.SU2_E_TRIALS
+    np.testing.assert_array_equal(lat.get_links(), before)
+    st = lat.stats()
+    assert st["cap_hits"] == 4 * V and st["trials"] == su2.KP_CAP * 4 * V
+
+
 @pytest.mark.parametrize("dtype,beta", [(su2.F64, 0.7), (su2.F32, 0.7), (su2.F64, 2.3)])
 def test_hybrid_sampler_phase_parity(dtype, beta):
     """Creutz below alpha = 1.7, Kennedy-Pendleton above: every phase against

@@ -189,7 +189,10 @@ int su2_polyakov_correlator(su2_lattice* lat, int rmax, double* out, int accumul
 
 /* Links of lattice l in the canonical layout double[V][4][4] =
  * [lex][mu][a0,a1,a2,a3] (host or device).  set rounds to FP32 for an
- * SU2_F32 handle.  Synchronous for host pointers. */
+ * SU2_F32 handle.  Device and page-locked host buffers must be 16-byte
+ * aligned (SU2_E_INVAL otherwise); the conversion kernel reads or writes
+ * page-locked host memory directly, pageable host memory goes through the
+ * 32 MiB staging area.  Synchronous for host pointers. */
 int su2_get_links(su2_lattice* lat, int l, double* dst);
 int su2_set_links(su2_lattice* lat, int l, const double* src);
 

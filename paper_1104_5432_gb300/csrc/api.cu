@@ -156,6 +156,19 @@ int check_handle(const su2_lattice* lat, bool need_bound = true)
 }
 
 // true when p is device (or managed) memory of some device
+// the device address of page-locked (pinned or registered) host memory,
+// which kernels read and write directly under unified addressing; null for
+// anything else
+const void* mapped_host_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 bool is_device_ptr(const void* p)
 {
     cudaPointerAttributes a;
@@ -778,8 +791,17 @@ int su2_get_links(su2_lattice* lat, int l, double* dst)
     DeviceGuard dg(lat->device);
     const uint32_t V = (uint32_t)lat->V[l];
     if (is_device_ptr(dst)) {
+        if ((uintptr_t)dst & 15) return fail(SU2_E_INVAL, "device buffer must be 16-byte aligned");
         SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, 0, V, dst, lat->stream));
         return SU2_OK;
+    }
+    if (void* hd = const_cast<void*>(mapped_host_ptr(dst))) {
+        if ((uintptr_t)hd & 15) return fail(SU2_E_INVAL, "host buffer must be 16-byte aligned");
+        // page-locked host memory: written directly by the conversion kernel
+        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, 0, V,
+                                           static_cast<double*>(hd), lat->stream));
+        SU2_CUDA(cudaStreamSynchronize(lat->stream));
+        return sync_status(lat);
     }
     const uint32_t per = (uint32_t)(STAGE_BYTES / (16 * sizeof(double)));
     for (uint32_t lex0 = 0; lex0 < V; lex0 += per) {
@@ -800,7 +822,16 @@ int su2_set_links(su2_lattice* lat, int l, const double* src)
     DeviceGuard dg(lat->device);
     const uint32_t V = (uint32_t)lat->V[l];
     if (is_device_ptr(src)) {
+        if ((uintptr_t)src & 15) return fail(SU2_E_INVAL, "device buffer must be 16-byte aligned");
         SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, 0, V, src, lat->stream));
+        return SU2_OK;
+    }
+    if (const void* hd = mapped_host_ptr(src)) {
+        if ((uintptr_t)hd & 15) return fail(SU2_E_INVAL, "host buffer must be 16-byte aligned");
+        // page-locked host memory: read directly by the conversion kernel
+        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, 0, V,
+                                             static_cast<const double*>(hd), lat->stream));
+        SU2_CUDA(cudaStreamSynchronize(lat->stream));
         return SU2_OK;
     }
     const uint32_t per = (uint32_t)(STAGE_BYTES / (16 * sizeof(double)));

@@ -36,44 +36,58 @@ __global__ void __launch_bounds__(TPB) init_kernel(Ctx ctx, int l, int hot, uint
     }
 }
 
+// Canonical <-> device layout, 64 sites per block: the block's 8 KB of the
+// canonical array move as 16-byte vectors with consecutive threads on
+// consecutive addresses (so the source or target may as well be
+// page-locked host memory read or written directly over the host link),
+// and are reordered in shared memory; thread (site k, direction mu) then
+// reads or writes one link.
+constexpr int CANON_SITES = TPB / 4;
+
 template <typename T>
 __global__ void __launch_bounds__(TPB)
 to_canonical_kernel(Ctx ctx, int l, uint32_t lex0, uint32_t nsite, double* __restrict__ dst)
 {
+    __shared__ double2 sh[CANON_SITES * 8];
     const LatDesc& D = ctx.desc[l];
-    const uint32_t k = blockIdx.x * TPB + threadIdx.x;
-    if (k >= nsite) return;
-    const uint32_t lex = lex0 + k;
-    const Links<T> U(ctx.links, D);
-    int p;
-    EoSite::from_lex(D, lex, &p);
-    double* o = dst + (size_t)k * 16;
-    for (int mu = 0; mu < 4; ++mu) {
+    const uint32_t s0 = blockIdx.x * CANON_SITES;
+    const uint32_t cnt = min((uint32_t)CANON_SITES, nsite - s0);
+    const uint32_t k = threadIdx.x >> 2;
+    const int mu = threadIdx.x & 3;
+    if (k < cnt) {
+        const uint32_t lex = lex0 + s0 + k;
+        const Links<T> U(ctx.links, D);
+        int p;
+        EoSite::from_lex(D, lex, &p);
         const Quat<T> a = U.load_rw(mu, p, lex >> 1);
-        o[mu * 4 + 0] = (double)a.a0;
-        o[mu * 4 + 1] = (double)a.a1;
-        o[mu * 4 + 2] = (double)a.a2;
-        o[mu * 4 + 3] = (double)a.a3;
+        sh[k * 8 + mu * 2 + 0] = make_double2((double)a.a0, (double)a.a1);
+        sh[k * 8 + mu * 2 + 1] = make_double2((double)a.a2, (double)a.a3);
     }
+    __syncthreads();
+    double2* out = reinterpret_cast<double2*>(dst + (size_t)s0 * 16);
+    for (uint32_t q = threadIdx.x; q < cnt * 8; q += TPB) out[q] = sh[q];
 }
 
 template <typename T>
 __global__ void __launch_bounds__(TPB)
 from_canonical_kernel(Ctx ctx, int l, uint32_t lex0, uint32_t nsite, const double* __restrict__ src)
 {
+    __shared__ double2 sh[CANON_SITES * 8];
     const LatDesc& D = ctx.desc[l];
-    const uint32_t k = blockIdx.x * TPB + threadIdx.x;
-    if (k >= nsite) return;
-    const uint32_t lex = lex0 + k;
+    const uint32_t s0 = blockIdx.x * CANON_SITES;
+    const uint32_t cnt = min((uint32_t)CANON_SITES, nsite - s0);
+    const double2* in = reinterpret_cast<const double2*>(src + (size_t)s0 * 16);
+    for (uint32_t q = threadIdx.x; q < cnt * 8; q += TPB) sh[q] = in[q];
+    __syncthreads();
+    const uint32_t k = threadIdx.x >> 2;
+    const int mu = threadIdx.x & 3;
+    if (k >= cnt) return;
+    const uint32_t lex = lex0 + s0 + k;
     const Links<T> U(ctx.links, D);
     int p;
     EoSite::from_lex(D, lex, &p);
-    const double* in = src + (size_t)k * 16;
-    for (int mu = 0; mu < 4; ++mu) {
-        const Quat<T> a = {(T)in[mu * 4 + 0], (T)in[mu * 4 + 1], (T)in[mu * 4 + 2],
-                           (T)in[mu * 4 + 3]};
-        U.store(mu, p, lex >> 1, a);
-    }
+    const double2 lo = sh[k * 8 + mu * 2 + 0], hi = sh[k * 8 + mu * 2 + 1];
+    U.store(mu, p, lex >> 1, Quat<T>{(T)lo.x, (T)lo.y, (T)hi.x, (T)hi.y});
 }
 
 // U_mu(x) -> g(x) U_mu(x) g(x+mu)^dagger, g Haar from Philox tag 3 with
@@ -113,21 +127,27 @@ cudaError_t launch_init(const Ctx& c, int dtype, int l, uint32_t V, int hot, uin
     return cudaGetLastError();
 }
 
+static unsigned nblk_canon(uint32_t n) { return (n + CANON_SITES - 1) / CANON_SITES; }
+
+// src / dst: device memory, or the device address of page-locked host memory;
+// 16-byte aligned
 cudaError_t launch_links_to_canonical(const Ctx& c, int dtype, int l, uint32_t lex0,
                                       uint32_t nsite, double* dst, cudaStream_t s)
 {
-    if (dtype == 0) to_canonical_kernel<float><<<nblk(nsite), TPB, 0, s>>>(c, l, lex0, nsite, dst);
-    else to_canonical_kernel<double><<<nblk(nsite), TPB, 0, s>>>(c, l, lex0, nsite, dst);
+    if (nsite == 0) return cudaSuccess;
+    if (dtype == 0) to_canonical_kernel<float><<<nblk_canon(nsite), TPB, 0, s>>>(c, l, lex0, nsite, dst);
+    else to_canonical_kernel<double><<<nblk_canon(nsite), TPB, 0, s>>>(c, l, lex0, nsite, dst);
     return cudaGetLastError();
 }
 
 cudaError_t launch_links_from_canonical(const Ctx& c, int dtype, int l, uint32_t lex0,
                                         uint32_t nsite, const double* src, cudaStream_t s)
 {
+    if (nsite == 0) return cudaSuccess;
     if (dtype == 0)
-        from_canonical_kernel<float><<<nblk(nsite), TPB, 0, s>>>(c, l, lex0, nsite, src);
+        from_canonical_kernel<float><<<nblk_canon(nsite), TPB, 0, s>>>(c, l, lex0, nsite, src);
     else
-        from_canonical_kernel<double><<<nblk(nsite), TPB, 0, s>>>(c, l, lex0, nsite, src);
+        from_canonical_kernel<double><<<nblk_canon(nsite), TPB, 0, s>>>(c, l, lex0, nsite, src);
     return cudaGetLastError();
 }
 

@@ -63,6 +63,41 @@ def test_links_round_trip(dtype):
     lat.get_links(out=out)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out.cpu().numpy(), got)
+    # page-locked host memory, read and written by the conversion kernels
+    pin = torch.from_numpy(src).pin_memory()
+    lat.init(su2.COLD, 0)
+    lat.set_links(pin)
+    pout = torch.zeros_like(pin).pin_memory()
+    lat.get_links(out=pout)
+    np.testing.assert_array_equal(pout.numpy(), got)
+    # 16-byte alignment of device and page-locked buffers
+    flat = torch.zeros(dev.numel() + 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(su2.SU2Error):
+        lat.get_links(out=flat[1:])
+
+
+@pytest.mark.parametrize("dtype", [su2.F64, su2.F32])
+@pytest.mark.parametrize("Ns,Nt", [(2, 2), (6, 2), (10, 6)])
+def test_links_round_trip_ragged_blocks(dtype, Ns, Nt):
+    """Volumes that are not multiples of the conversion kernels' 64 sites per
+    block, through pageable, page-locked and device buffers, in a batch
+    next to another lattice."""
+    src = inputs.random_links(Ns, Nt, 7)
+    B = su2.Lattice([4, Ns], [4, Nt], dtype)
+    B.batch_init(su2.HOT, [1, 2])
+    other = B.get_links(0)
+    exp = src if dtype == su2.F64 else src.astype(np.float32).astype(np.float64)
+    for buf in (src, torch.from_numpy(src).pin_memory(), torch.from_numpy(src).cuda()):
+        B.batch_init(su2.COLD, [0, 0])
+        B.set_links(other, 0)
+        B.set_links(buf, 1)
+        for out in (None, torch.empty(src.shape, dtype=torch.float64).pin_memory(),
+                    torch.empty(src.shape, dtype=torch.float64, device="cuda")):
+            got = B.get_links(1, out=out)
+            torch.cuda.synchronize()
+            got = got.cpu().numpy() if hasattr(got, "cpu") else got
+            np.testing.assert_array_equal(got, exp)
+        np.testing.assert_array_equal(B.get_links(0), other)
 
 
 # ----------------------------------------------------------------------------

@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-arms", action="store_true", help="skip the FP64 and batched arms")
-    ap.add_argument("--profile-case", choices=["f32_64", "f32_128", "f64_64"],
+    ap.add_argument("--profile-case", choices=["f32_64", "f32_128", "f64_64", "scan"],
                     help="run only a few sweeps of one lattice (for ncu captures) and exit")
     ap.add_argument("--launch-shape", type=int, default=None,
                     help="phase-kernel launch shape index instead of autotuning")
@@ -494,8 +494,20 @@ def profile_case(args):
     the kernels the profiles/ summaries are captured on."""
     import torch
 
-    from paper_1104_5432_gb300 import su2
+    from paper_1104_5432_gb300 import inputs, su2
 
+    if args.profile_case == "scan":
+        # the temperature scan's batch: 2 sweeps, then 3 measured sweeps
+        scan = inputs.temperature_scan(21, 48, 4)
+        S = su2.Lattice([e["Ns"] for e in scan], [e["Nt"] for e in scan], su2.F32)
+        S.set_launch_config(args.launch_shape or 0)
+        sb, ss = [e["beta"] for e in scan], [e["seed"] for e in scan]
+        S.batch_init(su2.HOT, ss)
+        S.batch_heatbath(sb, 2, ss, plaq=None)
+        plaq, ps, cs = S.batch_heatbath_measure(sb, 3, ss, 24)
+        print(json.dumps({"profile_case": "scan", "launch_shape": S.launch_config(),
+                          "abs_polyakov_0": float(ps[1, 0] / 3)}))
+        return
     Ns, dt = {"f32_64": (64, su2.F32), "f32_128": (128, su2.F32), "f64_64": (64, su2.F64)}[
         args.profile_case]
     lat = su2.Lattice(Ns, Ns, dt)

@@ -218,8 +218,8 @@ int su2_set_sweep(su2_lattice* lat, int l, uint64_t sweep);
  * SM, plain or y-slab traversal of the lattice, links per thread) compiled
  * for the phase kernel; shape 0 is the default.
  *   FP32:  0 256x4   1 128x8   2 64x16   3 32x32   4 256x4 slab  5 128x8 slab
- *          6 32x32 /2  7 32x32 /4  8 32x32 /8  9 32x32 /16  10 64x16 /8
- *          11 128x8 /8  12 32x32 slab /8  13 128x8 slab /8
+ *          6 32x32 /2  7 32x32 /4  8 32x32 /8  9 32x32 /16  10 32x32 slab /2
+ *          11 32x32 slab /4  12 32x32 slab /8  13 32x32 slab /16
  *   FP64:  0 256x1   1 128x4   2 64x8   3 64x4   4 32x16   5 32x8
  *          6 32x16 /2  7 32x16 /4  8 32x16 /8  9 32x16 /16  10 32x16 /32
  *          11 64x8 /16  12 32x8 /16  13 128x4 /16

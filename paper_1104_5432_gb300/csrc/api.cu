@@ -109,10 +109,15 @@ struct su2_lattice {
     int device = -1;
     cudaStream_t stream = 0;
     cudaStream_t capture = nullptr;
+    cudaStream_t capture_side = nullptr;    // the measurement branch while capturing
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // replayable sweeps per launch shape and fused-plaquette flag
     cudaGraphExec_t sweep_graph[NUM_LAUNCH_CFG][2] = {};
-    int measure_rmax = -1;                  // rmax baked into measure_graph
+    int measure_rmax = -1;                  // rmax baked into the measurement graphs
+    // a sweep with the measurement of the previous sweep's result on a
+    // parallel branch, and the measurement alone (after the last sweep)
     cudaGraphExec_t measure_graph[NUM_LAUNCH_CFG][2] = {};
+    cudaGraphExec_t measure_tail = nullptr;
     Ctx ctx{};                      // non-phase kernels
     Ctx cfg_ctx[NUM_LAUNCH_CFG]{};  // phase kernels and sweep end, per launch shape
 
@@ -138,10 +143,19 @@ struct su2_lattice {
                 }
     }
 
+    void drop_measure_graphs()
+    {
+        drop(measure_graph);
+        if (measure_tail) {
+            cudaGraphExecDestroy(measure_tail);
+            measure_tail = nullptr;
+        }
+    }
+
     void drop_graphs()
     {
         drop(sweep_graph);
-        drop(measure_graph);
+        drop_measure_graphs();
         measure_rmax = -1;
     }
 };
@@ -328,49 +342,100 @@ int set_params(su2_lattice* L, const double* betas, double beta, const uint64_t*
 
 // one sweep: 8 phases + sweep end; with rmax >= 0 also the Polyakov loop
 // and the correlator, added into the handle's accumulators
+// the Polyakov loop and correlator of the current links, summed into the
+// accumulators (they read only the mu = 3 links and the Polyakov field)
+int record_measure(su2_lattice* L, int rmax, cudaStream_t s)
+{
+    double* acc = L->acc_dev();
+    SU2_CUDA(launch_polyakov(L->ctx, L->dtype, acc, acc + L->n, 1, s));
+    SU2_CUDA(launch_correlator(L->ctx, L->dtype, rmax, acc + 2 * L->n, 1, s));
+    return SU2_OK;
+}
+
+// One sweep.  With rmax >= 0 the links present at the START of the sweep
+// (the previous sweep's result) are measured on a parallel branch: the
+// measurement reads only the mu = 3 links, which the phases mu = 0, 1, 2
+// leave alone, so it overlaps them and joins before phase (3, 0).
 int record_sweep(su2_lattice* L, bool plaq, int rmax, cudaStream_t s)
 {
-    for (int mu = 0; mu < 4; ++mu)
+    const bool branch = rmax >= 0;
+    if (branch) {
+        SU2_CUDA(cudaEventRecord(L->fork_ev, s));
+        SU2_CUDA(cudaStreamWaitEvent(L->capture_side, L->fork_ev, 0));
+        if (int rc = record_measure(L, rmax, L->capture_side)) return rc;
+        SU2_CUDA(cudaEventRecord(L->join_ev, L->capture_side));
+    }
+    for (int mu = 0; mu < 4; ++mu) {
+        if (branch && mu == 3) SU2_CUDA(cudaStreamWaitEvent(s, L->join_ev, 0));
         for (int p = 0; p < 2; ++p)
             SU2_CUDA(launch_phase(L->cfg_ctx[L->cfg], L->dtype, L->cfg, mu, p, plaq, nullptr,
                                   L->hybrid, s));
+    }
     SU2_CUDA(launch_sweep_end(L->cfg_ctx[L->cfg], plaq, s));
-    if (rmax >= 0) {
-        double* acc = L->acc_dev();
-        SU2_CUDA(launch_polyakov(L->ctx, L->dtype, acc, acc + L->n, 1, s));
-        SU2_CUDA(launch_correlator(L->ctx, L->dtype, rmax, acc + 2 * L->n, 1, s));
+    return SU2_OK;
+}
+
+// capture what `record` enqueues into an executable graph
+template <typename F>
+int capture_graph(su2_lattice* L, F record, cudaGraphExec_t* g)
+{
+    if (!L->capture) SU2_CUDA(cudaStreamCreateWithFlags(&L->capture, cudaStreamNonBlocking));
+    if (!L->capture_side)
+        SU2_CUDA(cudaStreamCreateWithFlags(&L->capture_side, cudaStreamNonBlocking));
+    if (!L->fork_ev) SU2_CUDA(cudaEventCreateWithFlags(&L->fork_ev, cudaEventDisableTiming));
+    if (!L->join_ev) SU2_CUDA(cudaEventCreateWithFlags(&L->join_ev, cudaEventDisableTiming));
+    SU2_CUDA(cudaStreamBeginCapture(L->capture, cudaStreamCaptureModeThreadLocal));
+    const int rc = record(L->capture);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(L->capture, &graph);
+    if (rc != SU2_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    const cudaError_t ei = cudaGraphInstantiate(g, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        *g = nullptr;
+        return cuda_fail(ei, "cudaGraphInstantiate");
     }
     return SU2_OK;
 }
 
-// one sweep as a graph of kernels, built once per handle, binding and rmax
-int sweep_graph(su2_lattice* L, bool plaq, int rmax, cudaGraphExec_t* exec)
+void set_measure_rmax(su2_lattice* L, int rmax)
 {
-    if (rmax >= 0 && rmax != L->measure_rmax) {
-        su2_lattice::drop(L->measure_graph);
+    if (rmax != L->measure_rmax) {
+        L->drop_measure_graphs();
         L->measure_rmax = rmax;
     }
+}
+
+// one sweep as a graph of kernels, built once per handle, binding and rmax
+// (rmax >= 0: with the measurement branch of the previous sweep's result)
+int sweep_graph(su2_lattice* L, bool plaq, int rmax, cudaGraphExec_t* exec)
+{
+    if (rmax >= 0) set_measure_rmax(L, rmax);
     cudaGraphExec_t& g = rmax >= 0 ? L->measure_graph[L->cfg][plaq ? 1 : 0]
                                    : L->sweep_graph[L->cfg][plaq ? 1 : 0];
     if (!g) {
-        if (!L->capture) SU2_CUDA(cudaStreamCreateWithFlags(&L->capture, cudaStreamNonBlocking));
-        SU2_CUDA(cudaStreamBeginCapture(L->capture, cudaStreamCaptureModeThreadLocal));
-        const int rc = record_sweep(L, plaq, rmax, L->capture);
-        cudaGraph_t graph = nullptr;
-        const cudaError_t e = cudaStreamEndCapture(L->capture, &graph);
-        if (rc != SU2_OK) {
-            if (graph) cudaGraphDestroy(graph);
+        if (int rc = capture_graph(
+                L, [&](cudaStream_t s) { return record_sweep(L, plaq, rmax, s); }, &g))
             return rc;
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-        const cudaError_t ei = cudaGraphInstantiate(&g, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ei != cudaSuccess) {
-            g = nullptr;
-            return cuda_fail(ei, "cudaGraphInstantiate");
-        }
     }
     *exec = g;
+    return SU2_OK;
+}
+
+// the measurement alone, for the result of the last sweep of a call
+int measure_tail_graph(su2_lattice* L, int rmax, cudaGraphExec_t* exec)
+{
+    set_measure_rmax(L, rmax);
+    if (!L->measure_tail) {
+        if (int rc = capture_graph(
+                L, [&](cudaStream_t s) { return record_measure(L, rmax, s); }, &L->measure_tail))
+            return rc;
+    }
+    *exec = L->measure_tail;
     return SU2_OK;
 }
 
@@ -407,7 +472,15 @@ int heatbath_impl(su2_lattice* L, const double* betas, double beta, int nsweeps,
     DeviceGuard dg(L->device);
     const bool want = plaq != nullptr;
     const bool dev_out = want && is_device_ptr(plaq);
-    cudaGraphExec_t g = nullptr;
+    // Measured runs: the first sweep is a plain one; every later sweep
+    // measures its predecessor's result on a parallel branch, and the tail
+    // graph measures the last one, so each of the nsweeps results is
+    // measured exactly once.
+    cudaGraphExec_t g = nullptr, g_first = nullptr, g_tail = nullptr;
+    if (rmax >= 0) {
+        if (int rc = sweep_graph(L, want, -1, &g_first)) return rc;
+        if (int rc = measure_tail_graph(L, rmax, &g_tail)) return rc;
+    }
     if (int rc = sweep_graph(L, want, rmax, &g)) return rc;
     const size_t acc_count = rmax >= 0 ? 2 * (size_t)L->n + (size_t)L->n * (rmax + 1) : 0;
     if (rmax >= 0)
@@ -417,7 +490,8 @@ int heatbath_impl(su2_lattice* L, const double* betas, double beta, int nsweeps,
         const int chunk = (want && !dev_out) ? std::min(PLAQ_RING, nsweeps - done) : nsweeps;
         if (int rc = set_params(L, betas, beta, seeds, seed, dev_out ? plaq : nullptr, nsweeps))
             return rc;
-        for (int s = 0; s < chunk; ++s) SU2_CUDA(cudaGraphLaunch(g, L->stream));
+        for (int s = 0; s < chunk; ++s)
+            SU2_CUDA(cudaGraphLaunch(g_first && done + s == 0 ? g_first : g, L->stream));
         if (want && !dev_out) {
             for (int l = 0; l < L->n; ++l)
                 SU2_CUDA(cudaMemcpyAsync(plaq + (size_t)l * nsweeps + done,
@@ -427,6 +501,7 @@ int heatbath_impl(su2_lattice* L, const double* betas, double beta, int nsweeps,
         done += chunk;
     }
     if (rmax >= 0) {
+        if (nsweeps > 0) SU2_CUDA(cudaGraphLaunch(g_tail, L->stream));
         const bool pdev = is_device_ptr(poly_sum), cdev = is_device_ptr(corr_sum);
         const double* acc = L->acc_dev();
         SU2_CUDA(cudaMemcpyAsync(poly_sum, acc, sizeof(double) * 2 * L->n,
@@ -549,6 +624,9 @@ int su2_lattice_destroy(su2_lattice* lat)
         DeviceGuard dg(lat->device);
         lat->drop_graphs();
         if (lat->capture) cudaStreamDestroy(lat->capture);
+        if (lat->capture_side) cudaStreamDestroy(lat->capture_side);
+        if (lat->fork_ev) cudaEventDestroy(lat->fork_ev);
+        if (lat->join_ev) cudaEventDestroy(lat->join_ev);
     }
     delete lat;
     return SU2_OK;

@@ -40,8 +40,8 @@ constexpr int NUM_LAUNCH_CFG = 14;
 constexpr LaunchCfg LAUNCH_CFG[2][NUM_LAUNCH_CFG] = {
     {{256, 4, false, 1}, {128, 8, false, 1}, {64, 16, false, 1}, {32, 32, false, 1},
      {256, 4, true, 1}, {128, 8, true, 1}, {32, 32, false, 2}, {32, 32, false, 4},
-     {32, 32, false, 8}, {32, 32, false, 16}, {64, 16, false, 8}, {128, 8, false, 8},
-     {32, 32, true, 8}, {128, 8, true, 8}},
+     {32, 32, false, 8}, {32, 32, false, 16}, {32, 32, true, 2}, {32, 32, true, 4},
+     {32, 32, true, 8}, {32, 32, true, 16}},
     {{256, 1, false, 1}, {128, 4, false, 1}, {64, 8, false, 1}, {64, 4, false, 1},
      {32, 16, false, 1}, {32, 8, false, 1}, {32, 16, false, 2}, {32, 16, false, 4},
      {32, 16, false, 8}, {32, 16, false, 16}, {32, 16, false, 32}, {64, 8, false, 16},
@@ -50,7 +50,7 @@ constexpr LaunchCfg LAUNCH_CFG[2][NUM_LAUNCH_CFG] = {
 static_assert(NUM_LAUNCH_CFG % 2 == 0, "shapes compile in pairs");
 // largest y-slab window (sites between a site and its t neighbour, times
 // the bytes a site's update touches) kept in L2
-constexpr double SLAB_WINDOW_BYTES = 16.0 * (1 << 20);
+constexpr double SLAB_WINDOW_BYTES = 8.0 * (1 << 20);
 
 constexpr int KP_CAP = 4096;        // Kennedy-Pendleton trial cap
 constexpr int PLAQ_RING = 4096;     // per-lattice plaquette slots for host output

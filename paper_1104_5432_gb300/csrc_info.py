@@ -5,8 +5,8 @@ thread)."""
 
 _F32 = [(256, 4, False, 1), (128, 8, False, 1), (64, 16, False, 1), (32, 32, False, 1),
         (256, 4, True, 1), (128, 8, True, 1), (32, 32, False, 2), (32, 32, False, 4),
-        (32, 32, False, 8), (32, 32, False, 16), (64, 16, False, 8), (128, 8, False, 8),
-        (32, 32, True, 8), (128, 8, True, 8)]
+        (32, 32, False, 8), (32, 32, False, 16), (32, 32, True, 2), (32, 32, True, 4),
+        (32, 32, True, 8), (32, 32, True, 16)]
 _F64 = [(256, 1, False, 1), (128, 4, False, 1), (64, 8, False, 1), (64, 4, False, 1),
         (32, 16, False, 1), (32, 8, False, 1), (32, 16, False, 2), (32, 16, False, 4),
         (32, 16, False, 8), (32, 16, False, 16), (32, 16, False, 32), (64, 8, False, 16),

@@ -241,6 +241,19 @@ def gpu_arm(args, rank, world, local):
     achieved = bytes_launch / phase_s / 1e9
     from paper_1104_5432_gb300.csrc_info import _F32, launch_shapes
     shape = lat.launch_config()[0]
+    # instruction-issue roofline of the same launches: warp instructions per
+    # launch (ncu) over the event-timed duration, against one warp
+    # instruction per clock per SM sub-partition at the sampled SM clock
+    inst = recorded_traffic("f32_64^4", "warp_inst_per_launch")
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clocks.get("sm_mhz") or 0.0
+    issue_peak = sms * 4 * mhz * 1e6
+    issue = {"unit": "warp instructions/s", "peak": issue_peak,
+             "peak_kind": f"{sms} SMs x 4 schedulers x 1 instruction/clock at {mhz:.0f} MHz "
+                          "(median SM clock sampled during the timed steps)",
+             "inst_per_update": None if inst is None else round(inst / (V // 2), 1),
+             "achieved": None if inst is None else inst / phase_s}
+    issue["frac"] = None if inst is None or not issue_peak else round(issue["achieved"] / issue_peak, 4)
     kname = "hb_phase_queue_kernel<float>" if _F32[shape][3] > 1 else "hb_phase_kernel<float>"
     traffic = recorded_traffic("f32_64^4")
     traffic_shape = recorded_traffic("f32_64^4", "launch_shape")
@@ -251,6 +264,7 @@ def gpu_arm(args, rank, world, local):
                 "kernel": f"{kname}, launch shape {shape} ({launch_shapes(False)[shape]}): one "
                           "checkerboard phase, V/2 link updates",
                 "bytes_per_launch": bytes_launch, "launch_ms": round(phase_s * 1e3, 4),
+                "issue": issue,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
                 "measured" else "fallback 6.8 TB/s"}
     # whole-step effective bandwidth (all kernels, all gaps)
@@ -299,10 +313,20 @@ def gpu_arm(args, rank, world, local):
         t64 = time_steps(step_f64, 2, 1)
         lat64.sync()
         busy = recorded_traffic("f64_64^4", "fp64_pipe_active_pct")
-        arms["fp64_plain"] = {"value": world * 4 * V * sw64 * 2 / t64, "unit": UNIT,
-                              "roofline": {"bound": "alu", "unit": "FP64 pipe busy (ncu)",
-                                           "frac": None if busy is None else busy / 100,
-                                           "note": "bound by GB300's FP64 pipe; memory < 3%"},
+        v64 = world * 4 * V * sw64 * 2 / t64
+        # FP64 flops per update counted by ncu (2 per DFMA, 1 per DMUL/DADD)
+        # against the measured FP64 FMA rate of this GPU
+        fl = recorded_traffic("f64_64^4", "fp64_flops_per_update")
+        peak64 = 2 * su2.probe_fma_rate(su2.F64) / 1e12
+        roof64 = {"bound": "alu", "unit": "TFLOP/s",
+                  "achieved": None if fl is None else round(fl * v64 / world / 1e12, 4),
+                  "peak": round(peak64, 4),
+                  "peak_kind": "measured here: FP64 FMA-chain probe (su2_probe_fma_rate)",
+                  "flops_per_update": fl,
+                  "fp64_pipe_busy_ncu": None if busy is None else busy / 100,
+                  "note": "bound by GB300's FP64 pipe; memory < 4% of its peak"}
+        roof64["frac"] = None if fl is None else round(roof64["achieved"] / peak64, 4)
+        arms["fp64_plain"] = {"value": v64, "unit": UNIT, "roofline": roof64,
                               "workload": workload_name("FP64 throughout").replace(
                                   f"{sweeps} checkerboard", f"{sw64} checkerboard"),
                               "ms_per_sweep": t64 / (2 * sw64) * 1e3}
@@ -450,6 +474,62 @@ def oracle_sample(n_phases, links=None):
     return float(cnt[1]) / dt, int(cnt[1]), dt, links
 
 
+def _oracle_all_cores_worker(k, Ns, Nt, barrier, q):
+    """One process of the all-cores oracle leg: its own hot start (seed
+    offset by k), then phase (0, 0) of the workload, timed between a common
+    barrier and its own end."""
+    import ctypes as C
+
+    from oracle import oracle as O
+
+    w = WORKLOAD
+    links = O.init(Ns, Nt, True, w["init_seed"] + 7919 * k)
+    cnt = np.zeros(3, np.uint64)
+    barrier.wait(timeout=600)
+    t0 = time.time()
+    O.lib().or_heatbath_phase(Ns, Nt, links.ctypes.data_as(C.c_void_p), w["beta"], 0, 0,
+                              w["hb_seed"], 0, 0, 0.0, None, cnt.ctypes.data_as(C.c_void_p))
+    q.put((int(cnt[1]), t0, time.time()))
+
+
+def oracle_all_cores(Ns=None, Nt=None):
+    """The oracle as it stands on every host core at once: one process per
+    core, each on its own lattice of the workload's size (2 GiB at 64^4), as
+    many as half the host memory allows; aggregate updates/s over the common
+    wall-clock window.  None if a worker fails."""
+    import multiprocessing as mp
+    import queue
+
+    Ns = Ns or WORKLOAD["Ns"]
+    Nt = Nt or WORKLOAD["Nt"]
+    cores = os.cpu_count() or 1
+    mem = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    n = max(1, min(cores, int(0.5 * mem // (4 * Ns ** 3 * Nt * 32 * 1.2))))
+    ctx = mp.get_context("spawn")
+    barrier, q = ctx.Barrier(n), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_all_cores_worker, args=(k, Ns, Nt, barrier, q))
+             for k in range(n)]
+    for p in procs:
+        p.start()
+    res = []
+    deadline = time.time() + 900
+    while len(res) < n and time.time() < deadline:
+        try:
+            res.append(q.get(timeout=5))
+        except queue.Empty:
+            if any(p.exitcode not in (None, 0) for p in procs):
+                break
+    for p in procs:
+        p.join(timeout=30)
+        if p.is_alive():
+            p.kill()
+    if len(res) < n:
+        return None
+    ups = sum(r[0] for r in res)
+    dt = max(r[2] for r in res) - min(r[1] for r in res)
+    return ups / dt, n, ups, dt
+
+
 def cpu_model():
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
@@ -536,7 +616,7 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     r = gpu_arm(args, rank, world, local)
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from paper_1104_5432_gb300 import su2
         v, u, dt, _ = oracle_sample(2)
@@ -544,6 +624,14 @@ def main():
                "sample": f"phases (0,0) and (0,1) of the 64^4 beta=2.5 hot-start workload "
                          f"({u} link updates, {dt:.1f} s), FP64 CPU oracle, one thread",
                "cpu": cpu_model()}
+        allc = oracle_all_cores()
+        if allc is not None:
+            va, na, ua, dta = allc
+            cpu_all = {"value": va, "unit": UNIT, "cores": na, "kind": "oracle",
+                       "sample": f"{na} processes, each phase (0,0) of its own 64^4 beta=2.5 "
+                                 f"hot-start lattice ({ua} link updates in {dta:.1f} s of wall "
+                                 "clock), FP64 CPU oracle, one thread per process",
+                       "cpu": cpu_model()}
     if rank == 0:
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
@@ -553,7 +641,8 @@ def main():
                            "link_bytes": 4 * WORKLOAD["Ns"] ** 3 * WORKLOAD["Nt"] * 16,
                            "l2": "inputs larger than L2 (1 GiB of links vs 129 MB L2), no flush",
                            "parallelism": f"{world} independent lattice(s), one per GPU"},
-                "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
+                "roofline": r["roofline"], "cpu_baseline": cpu,
+                "cpu_baseline_all_cores": cpu_all, "e2e": r["e2e"],
                 "gpu_launches": r["launches"], "clocks": r["clocks"],
                 "step_effective_gbs": round(r["step_gbs"], 1), "arms": r["arms"],
                 "launch_shapes": r["tuned"]}

@@ -306,6 +306,14 @@ int su2_plaquette_static(const void* links, int Ns, int Nt, int dtype, double* o
  * on `stream`. */
 int su2_selftest_math(void* out, void* stream);
 
+/* Measurement hook: the FMA throughput of the current device in FP32
+ * (dtype SU2_F32) or FP64 (SU2_F64): a grid of 8 blocks of 256 threads per
+ * SM, each thread running 8 independent FMA chains of `iters` steps,
+ * launched twice on `stream` and the second launch timed with CUDA events.
+ * *fma_per_s: FMA instructions per second summed over all threads (one FMA
+ * = 2 flops).  Synchronous; allocates nothing. */
+int su2_probe_fma_rate(int dtype, int iters, double* fma_per_s, void* stream);
+
 /* Self-test of the host-side exact division used for site indexing:
  * returns the number of n in [0, limit) and divisors 1..dmax for which
  * it differs from n / d. */

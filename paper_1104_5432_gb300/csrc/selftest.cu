@@ -1,6 +1,7 @@
 // selftest.cu -- exhaustive check of the FP32 transcendental forms used by
 // the heat-bath draw against FP64 references, over every point of the
-// uniform grid u = (k + 1/2) 2^-23, k = 0 .. 2^23 - 1.
+// uniform grid u = (k + 1/2) 2^-23, k = 0 .. 2^23 - 1; and the FMA-rate
+// probe that gives the arithmetic rooflines their measured denominators.
 #include "su2.h"
 #include "su2_internal.h"
 #include "su2_math.cuh"
@@ -45,8 +46,56 @@ __global__ void math_selftest_kernel(unsigned long long* out)
     }
 }
 
+__device__ double fma_rate_sink;
+
+// 8 independent FMA chains per thread: the pipe never waits on a result
+template <typename T>
+__global__ void __launch_bounds__(256) fma_rate_kernel(int iters, T a, T b)
+{
+    T x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = T(threadIdx.x + j) * T(1e-3);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = fma(x[j], a, b);
+    }
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += x[j];
+    if (s == T(-1)) fma_rate_sink = (double)s;  // never true here; keeps the chains live
+}
+
 }  // namespace
 }  // namespace su2
+
+extern "C" int su2_probe_fma_rate(int dtype, int iters, double* fma_per_s, void* stream)
+{
+    if (!fma_per_s || iters <= 0 || (dtype != SU2_F32 && dtype != SU2_F64)) return SU2_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SU2_E_CUDA;
+    const unsigned blocks = (unsigned)sms * 8u;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SU2_E_CUDA;
+    float ms = 0.0f;
+    for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up
+        cudaEventRecord(e0, s);
+        if (dtype == SU2_F32)
+            su2::fma_rate_kernel<float><<<blocks, 256, 0, s>>>(iters, 0.999f, 1e-4f);
+        else
+            su2::fma_rate_kernel<double><<<blocks, 256, 0, s>>>(iters, 0.999, 1e-4);
+        cudaEventRecord(e1, s);
+    }
+    const cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess || ms <= 0.0f) return SU2_E_CUDA;
+    *fma_per_s = (double)blocks * 256.0 * 8.0 * (double)iters / (ms * 1e-3);
+    return SU2_OK;
+}
 
 extern "C" int su2_selftest_math(void* out, void* stream)
 {

@@ -79,6 +79,7 @@ def load(build_if_needed: bool = True):
             "su2_selftest_fastdiv": (u64, [C.c_uint32, C.c_uint32]),
             "su2_plaquette_static": (i, [P, i, i, i, P, P]),
             "su2_selftest_math": (i, [P, P]),
+            "su2_probe_fma_rate": (i, [i, i, P, P]),
             "su2_autotune": (i, [P, P]),
             "su2_set_launch_config": (i, [P, i]),
             "su2_get_launch_config": (i, [P, P, P, P]),
@@ -100,6 +101,18 @@ def _check(rc: int) -> int:
     if rc != SU2_OK:
         raise SU2Error(rc, load().su2_last_error().decode())
     return rc
+
+
+def probe_fma_rate(dtype: int, iters: Optional[int] = None) -> float:
+    """FMA instructions per second of the current device in FP32 or FP64
+    (measurement hook for the arithmetic rooflines)."""
+    import torch
+    if iters is None:
+        iters = 65536 if dtype == F32 else 4096  # a few ms per launch either way
+    v = C.c_double()
+    _check(load().su2_probe_fma_rate(int(dtype), int(iters), C.byref(v),
+                                      C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return v.value
 
 
 def _ptr(x) -> Optional[int]:

@@ -426,6 +426,18 @@ def test_fp32_math_forms_exhaustive():
     assert qerr <= 3e-7, qerr
 
 
+def test_fma_rate_probe():
+    """The roofline denominators' probe: positive rates, FP32 far above FP64
+    on this GPU, and stable to 10% between calls."""
+    f32 = su2.probe_fma_rate(su2.F32)
+    f64 = su2.probe_fma_rate(su2.F64)
+    again = su2.probe_fma_rate(su2.F64)
+    assert f32 > 10 * f64 > 0
+    assert abs(again - f64) <= 0.1 * f64
+    with pytest.raises(su2.SU2Error):
+        su2.probe_fma_rate(7)
+
+
 @pytest.mark.parametrize("dtype", [su2.F32, su2.F64])
 def test_every_launch_shape_gives_identical_results(dtype):
     """The random streams are keyed by link and sweep, never by thread: each

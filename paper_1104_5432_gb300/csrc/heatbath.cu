@@ -70,6 +70,7 @@ __global__ void set_params_kernel(Ctx ctx, ParamChunk pc)
     LatDesc* D = ctx.desc + pc.first + j;
     D->beta = pc.beta[j];
     D->beta_f = (float)pc.beta[j];
+    D->half_inv_beta = 0.5 / pc.beta[j];  // inf at beta = 0, where the Haar draw applies
     D->seed = pc.seed[j];
     D->plaq_out = pc.plaq_out[j];
     D->sweep_base = D->sweep;

@@ -40,6 +40,21 @@ template <> __device__ __forceinline__ double alpha_haar<double>() { return 1e-1
 template <typename T> __device__ __forceinline__ T beta_of(const LatDesc& D);
 template <> __device__ __forceinline__ float beta_of<float>(const LatDesc& D) { return D.beta_f; }
 template <> __device__ __forceinline__ double beta_of<double>(const LatDesc& D) { return D.beta; }
+// 1/(2 alpha) from rk = 1/k: FP64 multiplies by the precomputed 1/(2 beta)
+// (a division costs the FP64 pipe ~20 slots); FP32 keeps the short
+// division, which needs no extra live register in a kernel at its limit
+template <typename T>
+__device__ __forceinline__ T inv_two_alpha(const LatDesc& D, T rk, T beta);
+template <>
+__device__ __forceinline__ float inv_two_alpha<float>(const LatDesc&, float rk, float beta)
+{
+    return 0.5f * rk / beta;
+}
+template <>
+__device__ __forceinline__ double inv_two_alpha<double>(const LatDesc& D, double rk, double)
+{
+    return rk * D.half_inv_beta;
+}
 template <typename T> __device__ __forceinline__ T creutz_of(const LatDesc& D);
 template <> __device__ __forceinline__ float creutz_of<float>(const LatDesc& D) { return D.creutz_below_f; }
 template <> __device__ __forceinline__ double creutz_of<double>(const LatDesc& D) { return D.creutz_below; }
@@ -199,7 +214,7 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             un = haar_from<T>(st.draw(TAG_DIRECTION, 0));
             tr = 0;
         } else {
-            const T inv2a = T(0.5) * rk / beta;
+            const T inv2a = inv_two_alpha<T>(D, rk, beta);
             T delta = T(0);
             tr = -1;
             // trial 0 also carries the direction in the low 9 bits of its words
@@ -373,7 +388,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             if (!(alpha >= alpha_haar<T>())) {
                 put(i, key, haar_from<T>(st.draw(TAG_DIRECTION, 0)), P, 0);
             } else {
-                inv2a = T(0.5) * rk / beta;
+                inv2a = inv_two_alpha<T>(D, rk, beta);
                 const U4 w = st.draw(TAG_TRIAL, 0u);
                 const uint32_t kd1 = spare_bits_1(w);
                 kd2 = spare_bits_2(w);

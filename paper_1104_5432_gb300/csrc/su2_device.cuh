@@ -80,7 +80,7 @@ __host__ __device__ __forceinline__ T qnorm2(const Quat<T>& p)
 }
 
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return ::rsqrt(x); }
 
 template <typename T>
 __device__ __forceinline__ Quat<T> qnormalise(const Quat<T>& p)

@@ -76,6 +76,7 @@ struct LatDesc {
     // per call
     double beta;
     float beta_f;           // beta rounded once for the FP32 kernels
+    double half_inv_beta;   // 1 / (2 beta) for the FP64 kernels: 1 / (2 alpha) = half_inv_beta / k
     uint64_t seed;
     uint64_t sweep_base;    // sweep index stored at plaq_out[0]
     double* plaq_out;       // device, nullable

@@ -1,6 +1,8 @@
 // su2_math.cuh -- the transcendental pieces of the heat-bath draw.
 //
-// FP64 uses CUDA's accurate double functions.  FP32 uses short forms whose
+// FP64 uses CUDA's accurate double functions (the reciprocal square root
+// through rsqrt, within 1 ulp, instead of a division by sqrt).  FP32 uses
+// short forms whose
 // error is bounded well inside the FP32 parity budget (2e-5 per link):
 //   ln u       for u on the uniform grid ((k + 1/2) 2^-23):
 //              u > 15/16: ln(1 - v) = -(v + v^2/2 + ... + v^8/8) with
@@ -68,7 +70,7 @@ template <> struct Math<double> {
     static __device__ __forceinline__ double sqrt_pos(double x) { return sqrt(x); }
     static __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }
     static __device__ __forceinline__ double expm1(double x) { return ::expm1(x); }
-    static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / sqrt(x); }
+    static __device__ __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
 };
 
 }  // namespace su2

@@ -124,15 +124,19 @@ struct Stream {
 };
 
 // uniform in (0,1): ((w >> 9) + 0.5) 2^-23, exact in float and double.
-// FP32: the top 23 bits as the mantissa of a float in [1,2) give
-// 1 + k 2^-23; subtracting 1 - 2^-24 leaves (2k + 1) 2^-24 exactly.
+// The top 23 bits as the leading mantissa bits of a number in [1,2) give
+// 1 + k 2^-23; subtracting 1 - 2^-24 leaves (2k + 1) 2^-24 exactly
+// (Sterbenz).  Integer operations and one subtraction: no conversion on
+// the FP64 pipe.
 __device__ __forceinline__ float u01f(uint32_t w)
 {
     return __int_as_float((int)((w >> 9) | 0x3F800000u)) - 0.99999994039535522f;
 }
 __device__ __forceinline__ double u01d(uint32_t w)
 {
-    return (double)(w >> 9) * 1.1920928955078125e-7 + 5.9604644775390625e-8;
+    const uint32_t k = w >> 9;  // 23 bits -> mantissa bits 51..29
+    return __hiloint2double((int)(0x3FF00000u | (k >> 3)), (int)(k << 29)) -
+           0.999999940395355224609375;
 }
 // uniform in (0,1) from an 18-bit integer k: (k + 0.5) 2^-18, exact
 __device__ __forceinline__ float u18f(uint32_t k)
@@ -141,7 +145,8 @@ __device__ __forceinline__ float u18f(uint32_t k)
 }
 __device__ __forceinline__ double u18d(uint32_t k)
 {
-    return (double)k * 3.814697265625e-6 + 1.9073486328125e-6;
+    // 18 bits -> mantissa bits 51..34, all in the high word
+    return __hiloint2double((int)(0x3FF00000u | (k << 2)), 0) - 0.9999980926513671875;
 }
 template <typename T> __device__ __forceinline__ T u18(uint32_t k);
 template <> __device__ __forceinline__ float u18<float>(uint32_t k) { return u18f(k); }

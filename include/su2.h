@@ -196,6 +196,13 @@ int su2_polyakov_correlator(su2_lattice* lat, int rmax, double* out, int accumul
 int su2_get_links(su2_lattice* lat, int l, double* dst);
 int su2_set_links(su2_lattice* lat, int l, const double* src);
 
+/* The same in single precision: float[V][4][4], half the bytes of the
+ * double layout (for SU2_F32 handles and FP32 checkpoints; an SU2_F64
+ * handle rounds on get and widens on set).  Alignment, host/device and
+ * synchrony as for su2_get_links / su2_set_links. */
+int su2_get_links_f32(su2_lattice* lat, int l, float* dst);
+int su2_set_links_f32(su2_lattice* lat, int l, const float* src);
+
 /* U_mu(x) -> g(x) U_mu(x) g(x+mu)^+ with Haar g(x) (Philox tag 3, key
  * seed): leaves the plaquette, the Polyakov loop and the correlator
  * unchanged ("which is gauge invariant", Sec. 2.2). */

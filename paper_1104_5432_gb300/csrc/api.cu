@@ -605,6 +605,78 @@ void su2::record_error(const char* msg) { g_err = msg; }
 // --------------------------------------------------------------------------
 // exported
 // --------------------------------------------------------------------------
+namespace {
+
+// Links of lattice l to / from the canonical layout with values of type C
+// (double or float): device buffers and page-locked host memory go through
+// the conversion kernel directly, pageable host memory through the staging
+// area in 32 MiB pieces.
+template <typename C>
+int get_links_impl(su2_lattice* lat, int l, C* dst)
+{
+    constexpr int cd = sizeof(C) == 8 ? 1 : 0;
+    if (int rc = check_handle(lat)) return rc;
+    if (!dst || l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index or buffer");
+    DeviceGuard dg(lat->device);
+    const uint32_t V = (uint32_t)lat->V[l];
+    if (is_device_ptr(dst)) {
+        if ((uintptr_t)dst & 15) return fail(SU2_E_INVAL, "device buffer must be 16-byte aligned");
+        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, 0, V, dst, cd, lat->stream));
+        return SU2_OK;
+    }
+    if (void* hd = const_cast<void*>(mapped_host_ptr(dst))) {
+        if ((uintptr_t)hd & 15) return fail(SU2_E_INVAL, "host buffer must be 16-byte aligned");
+        // page-locked host memory: written directly by the conversion kernel
+        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, 0, V, hd, cd, lat->stream));
+        SU2_CUDA(cudaStreamSynchronize(lat->stream));
+        return sync_status(lat);
+    }
+    const uint32_t per = (uint32_t)(STAGE_BYTES / (16 * sizeof(C)));
+    for (uint32_t lex0 = 0; lex0 < V; lex0 += per) {
+        const uint32_t cnt = std::min(per, V - lex0);
+        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, lex0, cnt, lat->stage_dev(),
+                                           cd, lat->stream));
+        SU2_CUDA(cudaMemcpyAsync(dst + (size_t)lex0 * 16, lat->stage_dev(),
+                                 sizeof(C) * 16 * cnt, cudaMemcpyDeviceToHost, lat->stream));
+        SU2_CUDA(cudaStreamSynchronize(lat->stream));
+    }
+    return sync_status(lat);
+}
+
+template <typename C>
+int set_links_impl(su2_lattice* lat, int l, const C* src)
+{
+    constexpr int cd = sizeof(C) == 8 ? 1 : 0;
+    if (int rc = check_handle(lat)) return rc;
+    if (!src || l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index or buffer");
+    DeviceGuard dg(lat->device);
+    const uint32_t V = (uint32_t)lat->V[l];
+    if (is_device_ptr(src)) {
+        if ((uintptr_t)src & 15) return fail(SU2_E_INVAL, "device buffer must be 16-byte aligned");
+        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, 0, V, src, cd, lat->stream));
+        return SU2_OK;
+    }
+    if (const void* hd = mapped_host_ptr(src)) {
+        if ((uintptr_t)hd & 15) return fail(SU2_E_INVAL, "host buffer must be 16-byte aligned");
+        // page-locked host memory: read directly by the conversion kernel
+        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, 0, V, hd, cd, lat->stream));
+        SU2_CUDA(cudaStreamSynchronize(lat->stream));
+        return SU2_OK;
+    }
+    const uint32_t per = (uint32_t)(STAGE_BYTES / (16 * sizeof(C)));
+    for (uint32_t lex0 = 0; lex0 < V; lex0 += per) {
+        const uint32_t cnt = std::min(per, V - lex0);
+        SU2_CUDA(cudaMemcpyAsync(lat->stage_dev(), src + (size_t)lex0 * 16,
+                                 sizeof(C) * 16 * cnt, cudaMemcpyHostToDevice, lat->stream));
+        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, lex0, cnt, lat->stage_dev(),
+                                             cd, lat->stream));
+    }
+    SU2_CUDA(cudaStreamSynchronize(lat->stream));
+    return SU2_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int su2_lattice_create(int Ns, int Nt, int dtype, su2_lattice** out)
@@ -862,66 +934,12 @@ int su2_polyakov_correlator(su2_lattice* lat, int rmax, double* out, int accumul
     return SU2_OK;
 }
 
-int su2_get_links(su2_lattice* lat, int l, double* dst)
+int su2_get_links(su2_lattice* lat, int l, double* dst) { return get_links_impl(lat, l, dst); }
+int su2_set_links(su2_lattice* lat, int l, const double* src) { return set_links_impl(lat, l, src); }
+int su2_get_links_f32(su2_lattice* lat, int l, float* dst) { return get_links_impl(lat, l, dst); }
+int su2_set_links_f32(su2_lattice* lat, int l, const float* src)
 {
-    if (int rc = check_handle(lat)) return rc;
-    if (!dst || l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index or buffer");
-    DeviceGuard dg(lat->device);
-    const uint32_t V = (uint32_t)lat->V[l];
-    if (is_device_ptr(dst)) {
-        if ((uintptr_t)dst & 15) return fail(SU2_E_INVAL, "device buffer must be 16-byte aligned");
-        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, 0, V, dst, lat->stream));
-        return SU2_OK;
-    }
-    if (void* hd = const_cast<void*>(mapped_host_ptr(dst))) {
-        if ((uintptr_t)hd & 15) return fail(SU2_E_INVAL, "host buffer must be 16-byte aligned");
-        // page-locked host memory: written directly by the conversion kernel
-        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, 0, V,
-                                           static_cast<double*>(hd), lat->stream));
-        SU2_CUDA(cudaStreamSynchronize(lat->stream));
-        return sync_status(lat);
-    }
-    const uint32_t per = (uint32_t)(STAGE_BYTES / (16 * sizeof(double)));
-    for (uint32_t lex0 = 0; lex0 < V; lex0 += per) {
-        const uint32_t cnt = std::min(per, V - lex0);
-        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, lex0, cnt, lat->stage_dev(),
-                                           lat->stream));
-        SU2_CUDA(cudaMemcpyAsync(dst + (size_t)lex0 * 16, lat->stage_dev(),
-                                 sizeof(double) * 16 * cnt, cudaMemcpyDeviceToHost, lat->stream));
-        SU2_CUDA(cudaStreamSynchronize(lat->stream));
-    }
-    return sync_status(lat);
-}
-
-int su2_set_links(su2_lattice* lat, int l, const double* src)
-{
-    if (int rc = check_handle(lat)) return rc;
-    if (!src || l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index or buffer");
-    DeviceGuard dg(lat->device);
-    const uint32_t V = (uint32_t)lat->V[l];
-    if (is_device_ptr(src)) {
-        if ((uintptr_t)src & 15) return fail(SU2_E_INVAL, "device buffer must be 16-byte aligned");
-        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, 0, V, src, lat->stream));
-        return SU2_OK;
-    }
-    if (const void* hd = mapped_host_ptr(src)) {
-        if ((uintptr_t)hd & 15) return fail(SU2_E_INVAL, "host buffer must be 16-byte aligned");
-        // page-locked host memory: read directly by the conversion kernel
-        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, 0, V,
-                                             static_cast<const double*>(hd), lat->stream));
-        SU2_CUDA(cudaStreamSynchronize(lat->stream));
-        return SU2_OK;
-    }
-    const uint32_t per = (uint32_t)(STAGE_BYTES / (16 * sizeof(double)));
-    for (uint32_t lex0 = 0; lex0 < V; lex0 += per) {
-        const uint32_t cnt = std::min(per, V - lex0);
-        SU2_CUDA(cudaMemcpyAsync(lat->stage_dev(), src + (size_t)lex0 * 16,
-                                 sizeof(double) * 16 * cnt, cudaMemcpyHostToDevice, lat->stream));
-        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, lex0, cnt, lat->stage_dev(),
-                                             lat->stream));
-    }
-    SU2_CUDA(cudaStreamSynchronize(lat->stream));
-    return SU2_OK;
+    return set_links_impl(lat, l, src);
 }
 
 int su2_gauge_transform(su2_lattice* lat, int l, uint64_t seed)

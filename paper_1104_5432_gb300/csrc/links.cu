@@ -36,19 +36,22 @@ __global__ void __launch_bounds__(TPB) init_kernel(Ctx ctx, int l, int hot, uint
     }
 }
 
-// Canonical <-> device layout, 64 sites per block: the block's 8 KB of the
-// canonical array move as 16-byte vectors with consecutive threads on
-// consecutive addresses (so the source or target may as well be
-// page-locked host memory read or written directly over the host link),
-// and are reordered in shared memory; thread (site k, direction mu) then
-// reads or writes one link.
+// Canonical <-> device layout, 64 sites per block: the block's part of the
+// canonical array (16 values of type C per site: 8 KB for double, 4 KB for
+// float) moves as 16-byte vectors with consecutive threads on consecutive
+// addresses (so the source or target may as well be page-locked host
+// memory read or written directly over the host link), and is reordered in
+// shared memory; thread (site k, direction mu) then reads or writes one
+// link.
 constexpr int CANON_SITES = TPB / 4;
 
-template <typename T>
+template <typename T, typename C>
 __global__ void __launch_bounds__(TPB)
-to_canonical_kernel(Ctx ctx, int l, uint32_t lex0, uint32_t nsite, double* __restrict__ dst)
+to_canonical_kernel(Ctx ctx, int l, uint32_t lex0, uint32_t nsite, C* __restrict__ dst)
 {
-    __shared__ double2 sh[CANON_SITES * 8];
+    constexpr int CH = (int)sizeof(C);  // 16-byte chunks per site
+    __shared__ uint4 sh[CANON_SITES * CH];
+    C* shc = reinterpret_cast<C*>(sh);
     const LatDesc& D = ctx.desc[l];
     const uint32_t s0 = blockIdx.x * CANON_SITES;
     const uint32_t cnt = min((uint32_t)CANON_SITES, nsite - s0);
@@ -60,24 +63,29 @@ to_canonical_kernel(Ctx ctx, int l, uint32_t lex0, uint32_t nsite, double* __res
         int p;
         EoSite::from_lex(D, lex, &p);
         const Quat<T> a = U.load_rw(mu, p, lex >> 1);
-        sh[k * 8 + mu * 2 + 0] = make_double2((double)a.a0, (double)a.a1);
-        sh[k * 8 + mu * 2 + 1] = make_double2((double)a.a2, (double)a.a3);
+        C* o = shc + k * 16 + mu * 4;
+        o[0] = (C)a.a0;
+        o[1] = (C)a.a1;
+        o[2] = (C)a.a2;
+        o[3] = (C)a.a3;
     }
     __syncthreads();
-    double2* out = reinterpret_cast<double2*>(dst + (size_t)s0 * 16);
-    for (uint32_t q = threadIdx.x; q < cnt * 8; q += TPB) out[q] = sh[q];
+    uint4* out = reinterpret_cast<uint4*>(dst + (size_t)s0 * 16);
+    for (uint32_t q = threadIdx.x; q < cnt * CH; q += TPB) out[q] = sh[q];
 }
 
-template <typename T>
+template <typename T, typename C>
 __global__ void __launch_bounds__(TPB)
-from_canonical_kernel(Ctx ctx, int l, uint32_t lex0, uint32_t nsite, const double* __restrict__ src)
+from_canonical_kernel(Ctx ctx, int l, uint32_t lex0, uint32_t nsite, const C* __restrict__ src)
 {
-    __shared__ double2 sh[CANON_SITES * 8];
+    constexpr int CH = (int)sizeof(C);
+    __shared__ uint4 sh[CANON_SITES * CH];
+    const C* shc = reinterpret_cast<const C*>(sh);
     const LatDesc& D = ctx.desc[l];
     const uint32_t s0 = blockIdx.x * CANON_SITES;
     const uint32_t cnt = min((uint32_t)CANON_SITES, nsite - s0);
-    const double2* in = reinterpret_cast<const double2*>(src + (size_t)s0 * 16);
-    for (uint32_t q = threadIdx.x; q < cnt * 8; q += TPB) sh[q] = in[q];
+    const uint4* in = reinterpret_cast<const uint4*>(src + (size_t)s0 * 16);
+    for (uint32_t q = threadIdx.x; q < cnt * CH; q += TPB) sh[q] = in[q];
     __syncthreads();
     const uint32_t k = threadIdx.x >> 2;
     const int mu = threadIdx.x & 3;
@@ -86,8 +94,8 @@ from_canonical_kernel(Ctx ctx, int l, uint32_t lex0, uint32_t nsite, const doubl
     const Links<T> U(ctx.links, D);
     int p;
     EoSite::from_lex(D, lex, &p);
-    const double2 lo = sh[k * 8 + mu * 2 + 0], hi = sh[k * 8 + mu * 2 + 1];
-    U.store(mu, p, lex >> 1, Quat<T>{(T)lo.x, (T)lo.y, (T)hi.x, (T)hi.y});
+    const C* v = shc + k * 16 + mu * 4;
+    U.store(mu, p, lex >> 1, Quat<T>{(T)v[0], (T)v[1], (T)v[2], (T)v[3]});
 }
 
 // U_mu(x) -> g(x) U_mu(x) g(x+mu)^dagger, g Haar from Philox tag 3 with
@@ -118,6 +126,7 @@ __global__ void __launch_bounds__(TPB) gauge_kernel(Ctx ctx, int l, uint64_t see
 }
 
 static unsigned nblk(uint32_t n) { return (n + TPB - 1) / TPB; }
+static unsigned nblk_canon(uint32_t n) { return (n + CANON_SITES - 1) / CANON_SITES; }
 
 cudaError_t launch_init(const Ctx& c, int dtype, int l, uint32_t V, int hot, uint64_t seed,
                         cudaStream_t s)
@@ -127,27 +136,38 @@ cudaError_t launch_init(const Ctx& c, int dtype, int l, uint32_t V, int hot, uin
     return cudaGetLastError();
 }
 
-static unsigned nblk_canon(uint32_t n) { return (n + CANON_SITES - 1) / CANON_SITES; }
-
-// src / dst: device memory, or the device address of page-locked host memory;
-// 16-byte aligned
+// buf: device memory, or the device address of page-locked host memory;
+// 16-byte aligned; canonical values in double (cdtype 1) or float (0)
 cudaError_t launch_links_to_canonical(const Ctx& c, int dtype, int l, uint32_t lex0,
-                                      uint32_t nsite, double* dst, cudaStream_t s)
+                                      uint32_t nsite, void* buf, int cdtype, cudaStream_t s)
 {
     if (nsite == 0) return cudaSuccess;
-    if (dtype == 0) to_canonical_kernel<float><<<nblk_canon(nsite), TPB, 0, s>>>(c, l, lex0, nsite, dst);
-    else to_canonical_kernel<double><<<nblk_canon(nsite), TPB, 0, s>>>(c, l, lex0, nsite, dst);
+    const unsigned g = nblk_canon(nsite);
+    if (dtype == 0 && cdtype == 1)
+        to_canonical_kernel<float, double><<<g, TPB, 0, s>>>(c, l, lex0, nsite, (double*)buf);
+    else if (dtype == 0)
+        to_canonical_kernel<float, float><<<g, TPB, 0, s>>>(c, l, lex0, nsite, (float*)buf);
+    else if (cdtype == 1)
+        to_canonical_kernel<double, double><<<g, TPB, 0, s>>>(c, l, lex0, nsite, (double*)buf);
+    else
+        to_canonical_kernel<double, float><<<g, TPB, 0, s>>>(c, l, lex0, nsite, (float*)buf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_links_from_canonical(const Ctx& c, int dtype, int l, uint32_t lex0,
-                                        uint32_t nsite, const double* src, cudaStream_t s)
+                                        uint32_t nsite, const void* buf, int cdtype,
+                                        cudaStream_t s)
 {
     if (nsite == 0) return cudaSuccess;
-    if (dtype == 0)
-        from_canonical_kernel<float><<<nblk_canon(nsite), TPB, 0, s>>>(c, l, lex0, nsite, src);
+    const unsigned g = nblk_canon(nsite);
+    if (dtype == 0 && cdtype == 1)
+        from_canonical_kernel<float, double><<<g, TPB, 0, s>>>(c, l, lex0, nsite, (const double*)buf);
+    else if (dtype == 0)
+        from_canonical_kernel<float, float><<<g, TPB, 0, s>>>(c, l, lex0, nsite, (const float*)buf);
+    else if (cdtype == 1)
+        from_canonical_kernel<double, double><<<g, TPB, 0, s>>>(c, l, lex0, nsite, (const double*)buf);
     else
-        from_canonical_kernel<double><<<nblk_canon(nsite), TPB, 0, s>>>(c, l, lex0, nsite, src);
+        from_canonical_kernel<double, float><<<g, TPB, 0, s>>>(c, l, lex0, nsite, (const float*)buf);
     return cudaGetLastError();
 }
 

@@ -134,10 +134,12 @@ cudaError_t launch_phase(const Ctx& c, int dtype, int cfg, int mu, int parity, b
 cudaError_t launch_sweep_end(const Ctx& c, bool plaq, cudaStream_t s);
 cudaError_t launch_init(const Ctx& c, int dtype, int l, uint32_t V, int hot, uint64_t seed,
                         cudaStream_t s);
+// canonical values in double (cdtype 1) or float (cdtype 0)
 cudaError_t launch_links_to_canonical(const Ctx& c, int dtype, int l, uint32_t lex0,
-                                      uint32_t nsite, double* dst, cudaStream_t s);
+                                      uint32_t nsite, void* dst, int cdtype, cudaStream_t s);
 cudaError_t launch_links_from_canonical(const Ctx& c, int dtype, int l, uint32_t lex0,
-                                        uint32_t nsite, const double* src, cudaStream_t s);
+                                        uint32_t nsite, const void* src, int cdtype,
+                                        cudaStream_t s);
 cudaError_t launch_gauge(const Ctx& c, int dtype, int l, uint32_t V, uint64_t seed, cudaStream_t s);
 cudaError_t launch_plaquette(const Ctx& c, int dtype, double* out_dev, cudaStream_t s);
 cudaError_t launch_polyakov(const Ctx& c, int dtype, double* out_signed_dev,

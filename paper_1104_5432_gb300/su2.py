@@ -79,6 +79,8 @@ def load(build_if_needed: bool = True):
             "su2_selftest_fastdiv": (u64, [C.c_uint32, C.c_uint32]),
             "su2_plaquette_static": (i, [P, i, i, i, P, P]),
             "su2_selftest_math": (i, [P, P]),
+            "su2_get_links_f32": (i, [P, i, P]),
+            "su2_set_links_f32": (i, [P, i, P]),
             "su2_probe_fma_rate": (i, [i, i, P, P]),
             "su2_autotune": (i, [P, P]),
             "su2_set_launch_config": (i, [P, i]),
@@ -113,6 +115,11 @@ def probe_fma_rate(dtype: int, iters: Optional[int] = None) -> float:
     _check(load().su2_probe_fma_rate(int(dtype), int(iters), C.byref(v),
                                       C.c_void_p(torch.cuda.current_stream().cuda_stream)))
     return v.value
+
+
+def _is_f32(x) -> bool:
+    """Whether a numpy array or torch tensor holds float32."""
+    return str(getattr(x, "dtype", "")) in ("float32", "torch.float32")
 
 
 def _ptr(x) -> Optional[int]:
@@ -262,17 +269,28 @@ class Lattice:
 
     # -- state ---------------------------------------------------------------
     def get_links(self, l: int = 0, out=None):
+        """Canonical [V][4][4] links: a new float64 numpy array, or into `out`
+        (numpy array or torch tensor, host or device, float64 or float32)."""
         V = self.volume(l)
         o = np.empty((V, 4, 4), np.float64) if out is None else out
-        _check(load().su2_get_links(self._h, l, _ptr(o)))
+        if _is_f32(o):
+            _check(load().su2_get_links_f32(self._h, l, _ptr(o)))
+        else:
+            _check(load().su2_get_links(self._h, l, _ptr(o)))
         return o
 
     def set_links(self, links, l: int = 0):
+        """From canonical [V][4][4] links (numpy or torch, host or device;
+        float32 arrays use the single-precision entry point)."""
         if isinstance(links, np.ndarray):
-            links = np.ascontiguousarray(links, np.float64)
+            links = np.ascontiguousarray(links, np.float32 if links.dtype == np.float32
+                                        else np.float64)
             if links.size != self.volume(l) * 16:
                 raise ValueError("links has the wrong size")
-        _check(load().su2_set_links(self._h, l, _ptr(links)))
+        if _is_f32(links):
+            _check(load().su2_set_links_f32(self._h, l, _ptr(links)))
+        else:
+            _check(load().su2_set_links(self._h, l, _ptr(links)))
 
     def gauge_transform(self, seed: int, l: int = 0):
         _check(load().su2_gauge_transform(self._h, l, int(seed) & 0xFFFFFFFFFFFFFFFF))

@@ -98,6 +98,23 @@ def test_links_round_trip_ragged_blocks(dtype, Ns, Nt):
             got = got.cpu().numpy() if hasattr(got, "cpu") else got
             np.testing.assert_array_equal(got, exp)
         np.testing.assert_array_equal(B.get_links(0), other)
+    # single-precision canonical buffers (half the bytes): set from float32
+    # values, read back rounded to float32
+    src32 = src.astype(np.float32)
+    exp32 = src32.astype(np.float64)
+    for buf in (src32, torch.from_numpy(src32).pin_memory(), torch.from_numpy(src32).cuda()):
+        B.batch_init(su2.COLD, [0, 0])
+        B.set_links(other, 0)
+        B.set_links(buf, 1)
+        np.testing.assert_array_equal(B.get_links(1), exp32)
+        for out in (np.empty(src.shape, np.float32),
+                    torch.empty(src.shape, dtype=torch.float32).pin_memory(),
+                    torch.empty(src.shape, dtype=torch.float32, device="cuda")):
+            got = B.get_links(1, out=out)
+            torch.cuda.synchronize()
+            got = got.cpu().numpy() if hasattr(got, "cpu") else got
+            np.testing.assert_array_equal(got, src32)
+        np.testing.assert_array_equal(B.get_links(0), other)
 
 
 # ----------------------------------------------------------------------------

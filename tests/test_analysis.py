@@ -1,8 +1,40 @@
-"""Post-processing of Sec. 2.2 against closed forms."""
+"""Post-processing of Sec. 2.2 against closed forms and the numbers the
+paper prints (tests/golden/paper_constants.json)."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 from paper_1104_5432_gb300 import analysis as A
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+
+
+def test_printed_constants_are_the_ones_used():
+    z = GOLDEN["renormalisation_Z"]
+    assert (A.A_PAPER, A.B_PAPER, A.G2_MAX) == (z["A"], z["B"], z["g2_max"])
+    assert A.sigma_ansatz_ising.__defaults__ == (GOLDEN["sigma_fit_ising"]["nu"],)
+
+
+def test_fits_recover_the_printed_sigma_parameters():
+    """Synthetic sigma(T) on the paper's two printed curves, fitted with the
+    same forms by least squares: the printed parameters come back."""
+    from scipy.optimize import curve_fit
+    t = np.linspace(0.7, 0.98, 15)            # T / T_c
+    sq = GOLDEN["sigma_fit_sqrt"]
+    y = A.sigma_ansatz_sqrt(t, sq["a"], sq["b"])
+    (a, b), _ = curve_fit(A.sigma_ansatz_sqrt, t, y, p0=(0.5, 0.9))
+    assert (a, b) == pytest.approx((sq["a"], sq["b"]), rel=1e-6)
+    isg = GOLDEN["sigma_fit_ising"]
+    dT = 1.0 - t                              # T_c - T in units of T_c
+    y = A.sigma_ansatz_ising(dT, isg["a"], isg["b"])
+    (a, b), _ = curve_fit(lambda d, a, b: A.sigma_ansatz_ising(d, a, b), dT, y, p0=(1.0, 0.0))
+    assert (a, b) == pytest.approx((isg["a"], isg["b"]), rel=1e-6)
+    # both printed curves describe the same sigma(T) near T_c to ~10%
+    mid = np.array([0.85, 0.9])
+    r = A.sigma_ansatz_sqrt(mid, sq["a"], sq["b"]) / A.sigma_ansatz_ising(1 - mid, isg["a"], isg["b"])
+    assert np.all(np.abs(r - 1) < 0.15), r
 
 
 def test_renormalised_polyakov_closed_form():

@@ -24,7 +24,7 @@ def test_fits_recover_the_printed_sigma_parameters():
     t = np.linspace(0.7, 0.98, 15)            # T / T_c
     sq = GOLDEN["sigma_fit_sqrt"]
     y = A.sigma_ansatz_sqrt(t, sq["a"], sq["b"])
-    (a, b), _ = curve_fit(A.sigma_ansatz_sqrt, t, y, p0=(0.5, 0.9))
+    (a, b), _ = curve_fit(A.sigma_ansatz_sqrt, t, y, p0=(0.5, 0.9), bounds=([0.1, 0.5], [2.0, 1.04]))
     assert (a, b) == pytest.approx((sq["a"], sq["b"]), rel=1e-6)
     isg = GOLDEN["sigma_fit_ising"]
     dT = 1.0 - t                              # T_c - T in units of T_c

@@ -131,11 +131,16 @@ PHASE_SOURCES = ("heatbath_kernel.cuh", "su2_links.cuh", "su2_math.cuh", "su2_de
 
 
 def phase_kernel_hash():
-    """Hash of the sources the phase kernel is compiled from."""
+    """Hash of the sources the phase kernels are compiled from and of the
+    flags their units are compiled with."""
+    from paper_1104_5432_gb300 import build as b
+
     h = hashlib.sha256()
     for f in PHASE_SOURCES:
         with open(os.path.join(ROOT, "paper_1104_5432_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
+    flags = [f for f in b.flags() if f not in (b.INCLUDE, b.CSRC)]  # no machine paths
+    h.update(repr((flags, b.SHAPE_UNITS)).encode())
     return h.hexdigest()[:16]
 
 

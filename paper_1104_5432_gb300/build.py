@@ -21,9 +21,15 @@ LIB = os.path.join(PKG, "libsu2gb300.so")
 SOURCES = ["heatbath.cu", "observables.cu", "links.cu", "api.cu", "plaquette_static.cu",
            "selftest.cu"]
 # heatbath_shapes.cu once per pair of launch shapes and precision (the
-# 14-entry table in csrc/su2_internal.h): (object name, defines)
+# 14-entry table in csrc/su2_internal.h): (object name, defines, flags).
+# The FP32 phase kernels flush denormals to zero: none can occur on their
+# path (links, staple sums and uniforms are >= 2^-24 in magnitude or exactly
+# 0, the log series is evaluated in Horner form, alpha and 1/(2 alpha) stay
+# normal down to beta = 1e-9), and without denormal handling the division
+# and square-root sequences are shorter (2% at 64^4).
 SHAPE_UNITS = [(f"heatbath_shapes_{'f32' if row == 0 else 'f64'}_{k}",
-                (f"SU2_ROW={row}", f"SU2_FIRST={k}")) for row in (0, 1) for k in range(0, 14, 2)]
+                (f"SU2_ROW={row}", f"SU2_FIRST={k}"), ("-ftz=true",) if row == 0 else ())
+               for row in (0, 1) for k in range(0, 14, 2)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -57,14 +63,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
     extra = ["-Xptxas", "-v"] if ptxas_info else []
     extra += [f"-D{d}" for d in defines]
 
-    units = [(src, src.replace(".cu", ""), ()) for src in SOURCES]
-    units += [("heatbath_shapes.cu", name, defs) for name, defs in SHAPE_UNITS]
+    units = [(src, src.replace(".cu", ""), (), ()) for src in SOURCES]
+    units += [("heatbath_shapes.cu", name, defs, fl) for name, defs, fl in SHAPE_UNITS]
 
     def one(unit):
-        src, name, defs = unit
+        src, name, defs, fl = unit
         obj = os.path.join(build_dir, name + ".o")
-        cmd = [cc, *flags(extra + [f"-D{d}" for d in defs]), "-c", os.path.join(CSRC, src),
-               "-o", obj]
+        cmd = [cc, *flags(extra + list(fl) + [f"-D{d}" for d in defs]), "-c",
+               os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {name}:\n{r.stderr}")

@@ -1,7 +1,8 @@
 // heatbath.cu -- sweep orchestration kernels of the SU(2) heat bath: the
 // end-of-sweep reduction of the fused plaquette, the per-call parameter
-// kernel and the dispatch of the phase kernel (heatbath_kernel.cuh,
-// instantiated for FP32 in heatbath_f32.cu and FP64 in heatbath_f64.cu).
+// kernel and the dispatch of the phase kernels (heatbath_kernel.cuh,
+// instantiated per pair of launch shapes and precision by
+// heatbath_shapes.cu).
 #include "su2_internal.h"
 #include "su2_reduce.cuh"
 

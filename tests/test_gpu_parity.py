@@ -333,6 +333,21 @@ def test_batch_equals_single(dtype):
         assert B.stats(l) == s.stats()
 
 
+@pytest.mark.parametrize("dtype,tol", [(su2.F64, 4e-15), (su2.F32, 5e-7)])
+@pytest.mark.parametrize("shape", [0, 8])
+def test_unitarity_after_every_sweep(dtype, tol, shape):
+    """det U = |a|^2 = 1 after every sweep, for the one-link and the queued
+    kernel (each new link is renormalised after its update)."""
+    Ns, Nt = 12, 6
+    lat = lattice(Ns, Nt, dtype)
+    lat.set_launch_config(shape)
+    lat.init(su2.HOT, 71)
+    for k in range(5):
+        lat.heatbath(2.5 if k % 2 == 0 else 0.9, 1, 72, plaq=None)
+        det = np.sum(lat.get_links() ** 2, axis=2)  # |a|^2 per link
+        assert np.max(np.abs(det - 1)) <= 2 * tol, (k, np.max(np.abs(det - 1)))
+
+
 def test_cap_hit_reported_and_links_kept():
     Ns, Nt = 4, 4
     lat = lattice(Ns, Nt, su2.F64)

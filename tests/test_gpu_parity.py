@@ -406,14 +406,18 @@ def test_invalid_arguments_leave_state():
 # ----------------------------------------------------------------------------
 # full size, in the launch configuration the benchmark times
 # ----------------------------------------------------------------------------
-def test_full_size_64_sampled():
+@pytest.mark.parametrize("shape", [0, 7, 8])
+def test_full_size_64_sampled(shape):
     """64^4 FP32 (1 GiB of links), hot start seed 3, one graph-replayed sweep
-    at beta = 2.5: U_0 on even sites comes from the first phase only, so a
-    sample of them is checked link by link against the oracle from the start
-    configuration; properties that hold at any size are checked in full."""
+    at beta = 2.5, in the one-link shape and in the queued shapes the
+    benchmark's autotuner picks (32 x 32 with 4 or 8 links per thread): U_0
+    on even sites comes from the first phase only, so a sample of them is
+    checked link by link against the oracle from the start configuration;
+    properties that hold at any size are checked in full."""
     Ns = Nt = 64
     V = Ns ** 4
     lat = lattice(Ns, Nt, su2.F32)
+    lat.set_launch_config(shape)
     lat.init(su2.HOT, 3)
     start = lat.get_links()
     plaq = lat.heatbath(2.5, 1, 3)
@@ -518,11 +522,15 @@ def test_autotune_and_cache(tmp_path, monkeypatch):
     assert again.launch_config()[0] == chosen
 
 
-def test_full_size_128_properties():
-    """128^4 FP32 (16 GiB of links): one replayed sweep; properties that hold
-    at any size: every link a unit quaternion, fused plaquette equals the
-    stand-alone one, every link updated, no cap hit, sweep counter 1."""
+@pytest.mark.parametrize("shape", [0, 13])
+def test_full_size_128_properties(shape):
+    """128^4 FP32 (16 GiB of links), in the one-link shape and in the one the
+    benchmark's autotuner picks (32 x 32, 16 slabs, 16 links per thread): one
+    replayed sweep; properties that hold at any size: every link a unit
+    quaternion, fused plaquette equals the stand-alone one, every link
+    updated, no cap hit, sweep counter 1."""
     lat = lattice(128, 128, su2.F32)
+    lat.set_launch_config(shape)
     lat.init(su2.HOT, 3)
     plaq = lat.heatbath(2.5, 1, 3)
     st = lat.stats()

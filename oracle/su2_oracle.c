@@ -11,6 +11,10 @@
  * the benchmark's CPU-baseline leg use it.  It shares no code, header, table
  * or constant generator with the CUDA implementation.
  *
+ * Every function here is pinned by tests/test_oracle_pins.py to something
+ * other than itself (closed forms, cuRAND's Philox, exact distributions,
+ * brute force on tiny lattices, invariances); none is "parity unpinned".
+ *
  * Everything is written the obvious way: links are kept as quaternions in
  * the canonical host layout but every group operation is done on explicit
  * 2x2 complex matrices, sites are visited in lexicographic order, sums use

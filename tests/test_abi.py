@@ -129,3 +129,27 @@ def test_launch_shape_mirror_matches_library():
             lib.su2_get_launch_config(h, C.byref(cfg), C.byref(thr), C.byref(mb))
             assert (thr.value, mb.value) == (t, m)
         lib.su2_lattice_destroy(h)
+
+
+def test_bind_memory_rejects_bad_buffers_before_touching_the_device():
+    """Null, unaligned and undersized buffers are refused on the host (the
+    checks come before any CUDA call), with SU2_E_INVAL / SU2_E_NOMEM and a
+    message; the handle stays unbound."""
+    lib = su2.load()
+    h = C.c_void_p()
+    assert lib.su2_lattice_create(4, 4, su2.F32, C.byref(h)) == 0
+    lb, wb = C.c_size_t(), C.c_size_t()
+    assert lib.su2_memory_requirements(h, C.byref(lb), C.byref(wb)) == 0
+    assert lb.value == 4 * 4 ** 4 * 16 and wb.value > 0
+    fake = 1 << 20  # 256-byte aligned, never dereferenced
+    assert lib.su2_bind_memory(h, None, lb.value, C.c_void_p(fake), wb.value) == su2.SU2_E_INVAL
+    assert lib.su2_bind_memory(h, C.c_void_p(fake + 16), lb.value, C.c_void_p(fake),
+                               wb.value) == su2.SU2_E_INVAL
+    assert lib.su2_bind_memory(h, C.c_void_p(fake), lb.value - 1, C.c_void_p(fake),
+                               wb.value) == su2.SU2_E_NOMEM
+    assert b"too small" in lib.su2_last_error()
+    assert lib.su2_bind_memory(h, C.c_void_p(fake), lb.value, C.c_void_p(fake),
+                               wb.value - 256) == su2.SU2_E_NOMEM
+    # still unbound: calls that need memory are refused
+    assert lib.su2_init(h, su2.COLD, 0) == su2.SU2_E_INVAL
+    lib.su2_lattice_destroy(h)

@@ -59,6 +59,8 @@ extern "C" {
 #define SU2_E_NOMEM (-2)    /* bound buffers smaller than required */
 #define SU2_E_CUDA (-3)     /* a CUDA runtime call failed */
 #define SU2_E_TRIALS (-4)   /* Kennedy-Pendleton cap hit since the last sync */
+#define SU2_E_BOUNDS (-5)   /* a link index out of range, caught by a build with
+                               -DSU2_CHECK_BOUNDS (the access was skipped) */
 
 #define SU2_F32 0           /* FP32 links and update, FP64 reductions */
 #define SU2_F64 1           /* FP64 throughout */

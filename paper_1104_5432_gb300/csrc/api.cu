@@ -447,6 +447,8 @@ int sync_status(su2_lattice* L)
     SU2_CUDA(cudaMemcpy(&st, L->status_dev(), sizeof st, cudaMemcpyDeviceToHost));
     if (st) {
         SU2_CUDA(cudaMemset(L->status_dev(), 0, sizeof st));
+        if (st & STATUS_BOUNDS)
+            return fail(SU2_E_BOUNDS, "link index out of bounds (bounds-checked build)");
         if (st & STATUS_CAP_HIT)
             return fail(SU2_E_TRIALS, "Kennedy-Pendleton trial cap (%d) hit; links kept", KP_CAP);
     }

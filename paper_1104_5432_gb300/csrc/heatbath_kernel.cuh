@@ -187,7 +187,7 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const uint32_t Vh = D.Vh;
     const uint32_t blk0 = __ldg(ctx.phase_start + l);
     const uint32_t j = (blockIdx.x - blk0) * NT + threadIdx.x;  // traversal position
-    const Links<T> U(ctx.links, D);
+    const Links<T> U(ctx.links, D, ctx.status);
 
     T plaq = T(0);
     uint32_t ntrial = 0, ncap = 0;
@@ -291,7 +291,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const uint32_t Vh = D.Vh;
     const uint32_t blk0 = __ldg(ctx.phase_start + l);
     const uint32_t j0 = (blockIdx.x - blk0) * (NT * R) + threadIdx.x;
-    const Links<T> U(ctx.links, D);
+    const Links<T> U(ctx.links, D, ctx.status);
     const int lane = threadIdx.x & 31;
     const uint32_t below = (1u << lane) - 1u;
     Queue& Q = sq[threadIdx.x >> 5];

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(TPB) init_kernel(Ctx ctx, int l, int hot, uint
     }
     if (lex < TRIAL_SLOTS) ctx.trial_slots[(size_t)l * TRIAL_SLOTS + lex] = 0;
     if (lex >= D.V) return;
-    const Links<T> U(ctx.links, D);
+    const Links<T> U(ctx.links, D, ctx.status);
     int p;
     EoSite::from_lex(D, lex, &p);
     for (int mu = 0; mu < 4; ++mu) {
@@ -59,7 +59,7 @@ to_canonical_kernel(Ctx ctx, int l, uint32_t lex0, uint32_t nsite, C* __restrict
     const int mu = threadIdx.x & 3;
     if (k < cnt) {
         const uint32_t lex = lex0 + s0 + k;
-        const Links<T> U(ctx.links, D);
+        const Links<T> U(ctx.links, D, ctx.status);
         int p;
         EoSite::from_lex(D, lex, &p);
         const Quat<T> a = U.load_rw(mu, p, lex >> 1);
@@ -91,7 +91,7 @@ from_canonical_kernel(Ctx ctx, int l, uint32_t lex0, uint32_t nsite, const C* __
     const int mu = threadIdx.x & 3;
     if (k >= cnt) return;
     const uint32_t lex = lex0 + s0 + k;
-    const Links<T> U(ctx.links, D);
+    const Links<T> U(ctx.links, D, ctx.status);
     int p;
     EoSite::from_lex(D, lex, &p);
     const C* v = shc + k * 16 + mu * 4;
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(TPB) gauge_kernel(Ctx ctx, int l, uint64_t see
     const LatDesc& D = ctx.desc[l];
     const uint32_t lex = blockIdx.x * TPB + threadIdx.x;
     if (lex >= D.V) return;
-    const Links<T> U(ctx.links, D);
+    const Links<T> U(ctx.links, D, ctx.status);
     int p;
     const EoSite s = EoSite::from_lex(D, lex, &p);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);

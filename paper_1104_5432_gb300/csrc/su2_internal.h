@@ -56,6 +56,7 @@ constexpr int KP_CAP = 4096;        // Kennedy-Pendleton trial cap
 constexpr int PLAQ_RING = 4096;     // per-lattice plaquette slots for host output
 constexpr size_t STAGE_BYTES = size_t(32) << 20;
 constexpr uint32_t STATUS_CAP_HIT = 1u;
+constexpr uint32_t STATUS_BOUNDS = 2u;  // bounds-checked builds only
 constexpr int SWEEP_CHUNK = TPB * 8;   // plaquette partials summed per sweep_end block
 constexpr int MAX_RMAX = 128;          // largest correlator separation
 constexpr int TRIAL_SLOTS = 64;        // per-lattice trial counters (spread atomics)

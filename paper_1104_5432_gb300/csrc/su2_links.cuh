@@ -6,17 +6,45 @@
 
 namespace su2 {
 
+// Bounds-checked builds (-DSU2_CHECK_BOUNDS, for testing): every link
+// access checks its even/odd index and direction; a bad one sets
+// STATUS_BOUNDS in the handle's status word (reported as SU2_E_BOUNDS by
+// the next synchronising call), reads link 0 instead and skips a store.
+// Ordinary builds compile the checks away.
+struct LinkCheck {
+#ifdef SU2_CHECK_BOUNDS
+    uint32_t* status;
+    uint32_t Vh;
+    __device__ __forceinline__ bool ok(int mu, int p, uint32_t eo) const
+    {
+        const bool good = eo < Vh && mu >= 0 && mu < 4 && (p == 0 || p == 1);
+        if (!good && status) atomicOr(status, STATUS_BOUNDS);
+        return good;
+    }
+#else
+    __device__ __forceinline__ bool ok(int, int, uint32_t) const { return true; }
+#endif
+};
+
 template <typename T> struct Links;
 
 // FP32: float4 U[mu][parity][eo]
 template <> struct Links<float> {
     float4* base;
     uint32_t Vh;
-    __device__ __forceinline__ Links(void* links, const LatDesc& d)
-        : base(reinterpret_cast<float4*>(static_cast<char*>(links) + d.link_off)), Vh(d.Vh) {}
+    LinkCheck chk;
+    __device__ __forceinline__ Links(void* links, const LatDesc& d, uint32_t* status = nullptr)
+        : base(reinterpret_cast<float4*>(static_cast<char*>(links) + d.link_off)), Vh(d.Vh)
+    {
+#ifdef SU2_CHECK_BOUNDS
+        chk = {status, d.Vh};
+#else
+        (void)status;
+#endif
+    }
     __device__ __forceinline__ size_t idx(int mu, int p, uint32_t eo) const
     {
-        return size_t(mu * 2 + p) * Vh + eo;
+        return chk.ok(mu, p, eo) ? size_t(mu * 2 + p) * Vh + eo : 0;
     }
     __device__ __forceinline__ Quat<float> load(int mu, int p, uint32_t eo) const
     {
@@ -30,7 +58,7 @@ template <> struct Links<float> {
     }
     __device__ __forceinline__ void store(int mu, int p, uint32_t eo, const Quat<float>& q) const
     {
-        base[idx(mu, p, eo)] = make_float4(q.a0, q.a1, q.a2, q.a3);
+        if (chk.ok(mu, p, eo)) base[size_t(mu * 2 + p) * Vh + eo] = make_float4(q.a0, q.a1, q.a2, q.a3);
     }
 };
 
@@ -38,11 +66,19 @@ template <> struct Links<float> {
 template <> struct Links<double> {
     double2* base;
     uint32_t Vh;
-    __device__ __forceinline__ Links(void* links, const LatDesc& d)
-        : base(reinterpret_cast<double2*>(static_cast<char*>(links) + d.link_off)), Vh(d.Vh) {}
+    LinkCheck chk;
+    __device__ __forceinline__ Links(void* links, const LatDesc& d, uint32_t* status = nullptr)
+        : base(reinterpret_cast<double2*>(static_cast<char*>(links) + d.link_off)), Vh(d.Vh)
+    {
+#ifdef SU2_CHECK_BOUNDS
+        chk = {status, d.Vh};
+#else
+        (void)status;
+#endif
+    }
     __device__ __forceinline__ size_t idx(int mu, int p, int plane, uint32_t eo) const
     {
-        return size_t((mu * 2 + p) * 2 + plane) * Vh + eo;
+        return chk.ok(mu, p, eo) ? size_t((mu * 2 + p) * 2 + plane) * Vh + eo : 0;
     }
     __device__ __forceinline__ Quat<double> load(int mu, int p, uint32_t eo) const
     {
@@ -58,8 +94,9 @@ template <> struct Links<double> {
     }
     __device__ __forceinline__ void store(int mu, int p, uint32_t eo, const Quat<double>& q) const
     {
-        base[idx(mu, p, 0, eo)] = make_double2(q.a0, q.a1);
-        base[idx(mu, p, 1, eo)] = make_double2(q.a2, q.a3);
+        if (!chk.ok(mu, p, eo)) return;
+        base[size_t((mu * 2 + p) * 2 + 0) * Vh + eo] = make_double2(q.a0, q.a1);
+        base[size_t((mu * 2 + p) * 2 + 1) * Vh + eo] = make_double2(q.a2, q.a3);
     }
 };
 

@@ -23,6 +23,7 @@ SU2_E_INVAL = -1
 SU2_E_NOMEM = -2
 SU2_E_CUDA = -3
 SU2_E_TRIALS = -4
+SU2_E_BOUNDS = -5
 
 F32, F64 = 0, 1
 COLD, HOT = 0, 1
@@ -44,7 +45,8 @@ def load(build_if_needed: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build() if build_if_needed else _build.LIB
+        # SU2_LIBRARY: a prebuilt library to load instead (e.g. a bounds-checked build)
+        path = os.environ.get("SU2_LIBRARY") or (_build.build() if build_if_needed else _build.LIB)
         if not os.path.exists(path):
             raise SU2Error(SU2_E_CUDA, f"CUDA library missing: {path}")
         L = C.CDLL(path)

@@ -456,6 +456,31 @@ def gpu_arm(args, rank, world, local):
         if "fp64_plain" in arms:
             arms["fp32_over_fp64_plain"] = value / arms["fp64_plain"]["value"]
 
+        # ---- lattice-size sweep at beta = 6.0 (the paper's performance test) -------
+        # random SU(2) start, 100 heat-bath sweeps with the plaquette after each,
+        # for a range of lattice sizes, in both precisions (Sec. 2.1, Fig. 1)
+        sizes = {}
+        for Ns in (8, 12, 16, 24, 32, 48, 64):
+            row = {}
+            for name, dtype in (("fp32", su2.F32), ("fp64", su2.F64)):
+                L = su2.Lattice(Ns, Ns, dtype)
+                L.autotune()
+                plq = torch.zeros(100, dtype=torch.float64, device="cuda")
+
+                def step_size():
+                    L.init(su2.HOT, 6 + rank)
+                    L.heatbath(6.0, 100, 6 + rank, plaq=plq)
+
+                ts = time_steps(step_size, 1 if Ns >= 48 else 2, 1)
+                row[name] = world * 4 * Ns ** 4 * 100 * (1 if Ns >= 48 else 2) / ts
+                L.close()
+            sizes[f"{Ns}^4"] = {k: round(v / 1e9, 4) for k, v in row.items()}
+        torch.cuda.empty_cache()
+        arms["size_sweep_beta6"] = {
+            "unit": "G link updates/s", "per_size": sizes,
+            "workload": "SU(2) Ns^4, Ns = 8..64, beta = 6.0, hot start, 100 sweeps + plaquette "
+                        "per sweep (hot start inside the timed step), autotuned shape per size"}
+
         # ---- equal statistical accuracy of <P>: FP32 and FP64 chains --------------
         # Same algorithm, same number of sweeps, independent seeds: the two
         # means must agree within their binned-jackknife errors (no FP32 bias

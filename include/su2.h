@@ -227,14 +227,17 @@ int su2_set_sweep(su2_lattice* lat, int l, uint64_t sweep);
  * SM, plain or y-slab traversal of the lattice, links per thread) compiled
  * for the phase kernel; shape 0 is the default.
  *   FP32:  0 256x4   1 128x8   2 64x16   3 32x32   4 256x4 slab  5 128x8 slab
- *          6 32x32 /2  7 32x32 /4  8 32x32 /8  9 32x32 /16  10 32x32 slab /2
- *          11 32x32 slab /4  12 32x32 slab /8  13 32x32 slab /16
+ *          6 32x32 /2  7 32x32 /4  8 32x32 /8  9 32x32 /16  10 32x32 /2 P
+ *          11 32x32 /1 P  12 32x32 slab /8  13 32x32 slab /16
  *   FP64:  0 256x1   1 128x4   2 64x8   3 64x4   4 32x16   5 32x8
  *          6 32x16 /2  7 32x16 /4  8 32x16 /8  9 32x16 /16  10 32x16 /32
- *          11 64x8 /16  12 32x8 /16  13 128x4 /16
+ *          11 64x8 /16  12 32x16 /2 P  13 32x16 /8 P
  * (/R: R links per thread with a per-warp queue of rejected Kennedy-
  * Pendleton trials, retried 32 at a time; slab: large lattices walked in y
- * slabs so the +-t neighbours stay in L2.)  Small blocks spread tiny
+ * slabs so the +-t neighbours stay in L2; P, persistent: on a single
+ * lattice only the blocks that fit on the GPU at once are launched, each
+ * walking tiles of R rounds in grid-stride order with one queue drain at
+ * the end; on a batch one block per tile, as the other shapes.)  Small blocks spread tiny
  * lattices over more SMs; several links per thread pay off on large ones.
  * Results never depend on the shape (the random streams are keyed by link
  * and sweep). */

@@ -771,6 +771,21 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
     SU2_CUDA(cudaMemcpy(w + lat->off_desc, d.data(), sizeof(LatDesc) * lat->n,
                         cudaMemcpyHostToDevice));
     lat->phase_params_valid = false;
+    // persistent shapes on a single lattice: as many blocks as fit at once
+    // (each walks several tiles); on a batch they launch one block per tile
+    int sms = 1;
+    SU2_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    for (int k = 0; k < NUM_LAUNCH_CFG; ++k) {
+        const LaunchCfg& cf = LAUNCH_CFG[lat->dtype][k];
+        if (!cf.persistent || lat->n != 1) continue;
+        const uint64_t per = (uint64_t)cf.threads * (uint64_t)cf.rounds;
+        const uint32_t tiles = (uint32_t)((lat->V[0] / 2 + per - 1) / per);
+        const uint32_t nb = std::min<uint32_t>(tiles, (uint32_t)(sms * cf.min_blocks));
+        lat->phase_start[k][1] = nb;
+        lat->phase_blocks[k] = nb;
+        const uint32_t wpb = (uint32_t)cf.threads / 32;
+        lat->cfg_chunks[k] = std::max<uint32_t>(1, (3 * nb * wpb + SWEEP_CHUNK - 1) / SWEEP_CHUNK);
+    }
     for (int k = 0; k < NUM_LAUNCH_CFG; ++k)
         SU2_CUDA(cudaMemcpy(w + lat->off_pstart_cfg[k], lat->phase_start[k].data(),
                             4 * (lat->n + 1), cudaMemcpyHostToDevice));

@@ -290,7 +290,11 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const LatDesc& D = ctx.desc[l];
     const uint32_t Vh = D.Vh;
     const uint32_t blk0 = __ldg(ctx.phase_start + l);
-    const uint32_t j0 = (blockIdx.x - blk0) * (NT * R) + threadIdx.x;
+    // tiles of NT R positions; a lattice's nb blocks take them in grid-stride
+    // order (nb = the tile count, one tile each, unless the shape is
+    // persistent), and a block's queue carries over from tile to tile
+    const uint32_t nb = __ldg(ctx.phase_start + l + 1) - blk0;
+    const uint32_t ntiles = (Vh + NT * R - 1) / (NT * R);
     const Links<T> U(ctx.links, D, ctx.status);
     const int lane = threadIdx.x & 31;
     const uint32_t below = (1u << lane) - 1u;
@@ -371,8 +375,9 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
         push(pend, A, P, inv2a, qc, key, tk, kd2, i);
     };
 
+    for (uint32_t tile = blockIdx.x - blk0; tile < ntiles; tile += nb)
     for (int r = 0; r < R; ++r) {
-        const uint32_t j = j0 + (uint32_t)r * NT;
+        const uint32_t j = tile * (NT * R) + threadIdx.x + (uint32_t)r * NT;
         bool pend = false;
         Quat<T> A = {T(0), T(0), T(0), T(0)}, P = A;
         T inv2a = T(0), qc = T(0);
@@ -418,7 +423,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 // One launch shape (NT threads per block, at least MINB blocks per SM, R
 // links per thread) of the phase kernel; the grid covers ctx.phase_blocks
 // blocks of NT R links.
-template <typename T, int NT, int MINB, bool SLAB, int R = 1>
+template <typename T, int NT, int MINB, bool SLAB, int R = 1, bool PERSIST = false>
 cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int32_t* dbg,
                                bool hyb, cudaStream_t s)
 {
@@ -426,7 +431,7 @@ cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int3
     const bool pl = plaq && parity == 1 && mu >= 1;
     const dim3 grid(c.phase_blocks), block(NT);
 #define SU2_K(MUV, PL, DB, H)                                                                   \
-    if constexpr (R == 1)                                                                       \
+    if constexpr (R == 1 && !PERSIST)                                                           \
         hb_phase_kernel<T, MUV, PL, DB, NT, MINB, SLAB, H><<<grid, block, 0, s>>>(c, parity, dbg); \
     else                                                                                        \
         hb_phase_queue_kernel<T, MUV, PL, DB, NT, MINB, SLAB, H, R><<<grid, block, 0, s>>>(c, parity, dbg)

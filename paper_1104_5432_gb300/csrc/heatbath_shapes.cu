@@ -20,11 +20,11 @@ cudaError_t launch_phase_pair(const Ctx& c, int cfg, int mu, int parity, bool pl
     constexpr LaunchCfg A = LAUNCH_CFG[ROW][FIRST];
     constexpr LaunchCfg B = LAUNCH_CFG[ROW][FIRST + 1];
     if (cfg == FIRST)
-        return launch_phase_shape<T, A.threads, A.min_blocks, A.slab, A.rounds>(c, mu, parity, plaq,
-                                                                               dbg, hyb, s);
+        return launch_phase_shape<T, A.threads, A.min_blocks, A.slab, A.rounds, A.persistent>(
+            c, mu, parity, plaq, dbg, hyb, s);
     if (cfg == FIRST + 1)
-        return launch_phase_shape<T, B.threads, B.min_blocks, B.slab, B.rounds>(c, mu, parity, plaq,
-                                                                               dbg, hyb, s);
+        return launch_phase_shape<T, B.threads, B.min_blocks, B.slab, B.rounds, B.persistent>(
+            c, mu, parity, plaq, dbg, hyb, s);
     return cudaErrorInvalidValue;
 }
 

@@ -28,24 +28,30 @@ constexpr int TPB = 256;            // threads per block of the non-phase kernel
 // since the FP64 kernel is bound by its arithmetic, not by re-reads.
 // rounds: links per thread; above 1 the kernel with the per-warp retry
 // queue (hb_phase_queue_kernel) runs.
+// persistent (single-lattice handles): only the blocks that fit on the GPU
+// at once are launched, and each walks tiles of R rounds in grid-stride
+// order, so its retry queue carries over from tile to tile and drains once.
 struct LaunchCfg {
     int threads, min_blocks;
     bool slab;
     int rounds;
+    bool persistent;
 };
 constexpr int NUM_LAUNCH_CFG = 14;
 // Small blocks (64, 32 threads) spread tiny lattices over more SMs; several
 // links per thread pay off on large lattices (one queue pass retries 32
 // rejected trials at once) but leave small ones with too few blocks.
 constexpr LaunchCfg LAUNCH_CFG[2][NUM_LAUNCH_CFG] = {
-    {{256, 4, false, 1}, {128, 8, false, 1}, {64, 16, false, 1}, {32, 32, false, 1},
-     {256, 4, true, 1}, {128, 8, true, 1}, {32, 32, false, 2}, {32, 32, false, 4},
-     {32, 32, false, 8}, {32, 32, false, 16}, {32, 32, true, 2}, {32, 32, true, 4},
-     {32, 32, true, 8}, {32, 32, true, 16}},
-    {{256, 1, false, 1}, {128, 4, false, 1}, {64, 8, false, 1}, {64, 4, false, 1},
-     {32, 16, false, 1}, {32, 8, false, 1}, {32, 16, false, 2}, {32, 16, false, 4},
-     {32, 16, false, 8}, {32, 16, false, 16}, {32, 16, false, 32}, {64, 8, false, 16},
-     {32, 8, false, 16}, {128, 4, false, 16}},
+    {{256, 4, false, 1, false}, {128, 8, false, 1, false}, {64, 16, false, 1, false},
+     {32, 32, false, 1, false}, {256, 4, true, 1, false}, {128, 8, true, 1, false},
+     {32, 32, false, 2, false}, {32, 32, false, 4, false}, {32, 32, false, 8, false},
+     {32, 32, false, 16, false}, {32, 32, false, 2, true}, {32, 32, false, 1, true},
+     {32, 32, true, 8, false}, {32, 32, true, 16, false}},
+    {{256, 1, false, 1, false}, {128, 4, false, 1, false}, {64, 8, false, 1, false},
+     {64, 4, false, 1, false}, {32, 16, false, 1, false}, {32, 8, false, 1, false},
+     {32, 16, false, 2, false}, {32, 16, false, 4, false}, {32, 16, false, 8, false},
+     {32, 16, false, 16, false}, {32, 16, false, 32, false}, {64, 8, false, 16, false},
+     {32, 16, false, 2, true}, {32, 16, false, 8, true}},
 };
 static_assert(NUM_LAUNCH_CFG % 2 == 0, "shapes compile in pairs");
 // largest y-slab window (sites between a site and its t neighbour, times

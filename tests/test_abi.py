@@ -123,7 +123,7 @@ def test_launch_shape_mirror_matches_library():
         h = C.c_void_p()
         assert lib.su2_lattice_create(4, 4, dtype, C.byref(h)) == 0
         assert len(table) == 14
-        for k, (t, m, _, _) in enumerate(table):
+        for k, (t, m, *_) in enumerate(table):
             assert lib.su2_set_launch_config(h, k) == 0
             cfg, thr, mb = C.c_int(), C.c_int(), C.c_int()
             lib.su2_get_launch_config(h, C.byref(cfg), C.byref(thr), C.byref(mb))

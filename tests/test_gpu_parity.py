@@ -551,7 +551,8 @@ def test_full_size_128_properties(shape):
     torch.cuda.empty_cache()
 
 
-QUEUED = [(su2.F32, 6), (su2.F32, 8), (su2.F32, 12), (su2.F64, 6), (su2.F64, 10)]
+QUEUED = [(su2.F32, 6), (su2.F32, 8), (su2.F32, 10), (su2.F32, 11), (su2.F32, 12), (su2.F64, 6),
+          (su2.F64, 10), (su2.F64, 12), (su2.F64, 13)]
 
 
 @pytest.mark.parametrize("dtype,cfg", QUEUED)
@@ -605,6 +606,31 @@ def test_queued_shapes_hybrid_and_trial_output(dtype, cfg):
                 flips += int((~same).sum())
                 n += int(same.size)
     assert flips <= max(1e-4 * n, 1)
+
+
+@pytest.mark.parametrize("dtype,persistent,plain", [
+    (su2.F32, 10, 6), (su2.F32, 11, 3), (su2.F64, 12, 6), (su2.F64, 13, 8)])
+def test_persistent_shapes_walk_several_tiles(dtype, persistent, plain):
+    """48^4, one lattice: a persistent shape launches only the blocks that
+    fit on the GPU at once (152 SMs x 32 blocks of 32 threads in FP32, x 16
+    in FP64), far fewer than its tiles of 32 R links (82944 at R = 1 down to
+    10368 at R = 8), so each block walks 4 to 17 tiles with one retry queue.
+    Links and trial statistics equal those of the same block size and R
+    launched one block per tile, bit for bit; the fused plaquette sums its
+    per-warp partials in another grouping (FP64 to 1e-13, FP32 to its 1e-6
+    budget)."""
+    out = []
+    for cfg in (plain, persistent):
+        lat = lattice(48, 48, dtype)
+        lat.set_launch_config(cfg)
+        lat.init(su2.HOT, 21)
+        plaq = lat.heatbath(2.5, 2, 22)
+        out.append((lat.get_links(), lat.stats(), plaq))
+        lat.close()
+    (la, sa, pa), (lb, sb, pb) = out
+    np.testing.assert_array_equal(lb, la)
+    assert sb == sa
+    np.testing.assert_allclose(pb, pa, rtol=0, atol=1e-13 if dtype == su2.F64 else 1e-6)
 
 
 @pytest.mark.parametrize("dtype,cfg", [(su2.F32, 8), (su2.F64, 9)])

@@ -259,7 +259,8 @@ def gpu_arm(args, rank, world, local):
              "inst_per_update": None if inst is None else round(inst / (V // 2), 1),
              "achieved": None if inst is None else inst / phase_s}
     issue["frac"] = None if inst is None or not issue_peak else round(issue["achieved"] / issue_peak, 4)
-    kname = "hb_phase_queue_kernel<float>" if _F32[shape][3] > 1 else "hb_phase_kernel<float>"
+    queued = _F32[shape][3] > 1 or _F32[shape][4]  # several links per thread, or persistent
+    kname = "hb_phase_queue_kernel<float>" if queued else "hb_phase_kernel<float>"
     traffic = recorded_traffic("f32_64^4")
     traffic_shape = recorded_traffic("f32_64^4", "launch_shape")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",

@@ -278,7 +278,8 @@ struct RetryQueue {
     uint32_t site[CAP];             // storage index
 };
 
-template <typename T, int MU, bool PLAQ, bool DBG, int NT, int MINB, bool SLAB, bool HYB, int R>
+template <typename T, int MU, bool PLAQ, bool DBG, int NT, int MINB, bool SLAB, bool HYB, int R,
+          bool PERSIST>
 __global__ void __launch_bounds__(NT, MINB)
 hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 {
@@ -290,11 +291,12 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const LatDesc& D = ctx.desc[l];
     const uint32_t Vh = D.Vh;
     const uint32_t blk0 = __ldg(ctx.phase_start + l);
-    // tiles of NT R positions; a lattice's nb blocks take them in grid-stride
-    // order (nb = the tile count, one tile each, unless the shape is
-    // persistent), and a block's queue carries over from tile to tile
-    const uint32_t nb = __ldg(ctx.phase_start + l + 1) - blk0;
-    const uint32_t ntiles = (Vh + NT * R - 1) / (NT * R);
+    // tiles of NT R positions, one per block; a persistent shape's nb blocks
+    // take them in grid-stride order (nb <= the tile count), and a block's
+    // queue carries over from tile to tile
+    const uint32_t nb = PERSIST ? __ldg(ctx.phase_start + l + 1) - blk0 : 0u;
+    const uint32_t ntiles = PERSIST ? (Vh + NT * R - 1) / (NT * R) : 0u;
+    uint32_t tile = blockIdx.x - blk0;
     const Links<T> U(ctx.links, D, ctx.status);
     const int lane = threadIdx.x & 31;
     const uint32_t below = (1u << lane) - 1u;
@@ -375,54 +377,58 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
         push(pend, A, P, inv2a, qc, key, tk, kd2, i);
     };
 
-    for (uint32_t tile = blockIdx.x - blk0; tile < ntiles; tile += nb)
-    for (int r = 0; r < R; ++r) {
-        const uint32_t j = tile * (NT * R) + threadIdx.x + (uint32_t)r * NT;
-        bool pend = false;
-        Quat<T> A = {T(0), T(0), T(0), T(0)}, P = A;
-        T inv2a = T(0), qc = T(0);
-        uint32_t key = 0, tk = 0, kd2 = 0, i = j;
-        if (j < Vh) {
-            const EoSite s = SLAB ? EoSite::from_slab(D, j, p, &i) : EoSite(D, j, p);
-            staple_sum<T, MU, PLAQ>(U, s, i, p, A, P);
-            const T k2 = qnorm2(A);
-            const T rk = Math<T>::rsqrt(k2);
-            const T alpha = beta * k2 * rk;
-            key = s.lex() * 4u + MU;
-            const Stream st{k0, k1, key, slo, shi};
-            if (!(alpha >= alpha_haar<T>())) {
-                put(i, key, haar_from<T>(st.draw(TAG_DIRECTION, 0)), P, 0);
-            } else {
-                inv2a = inv_two_alpha<T>(D, rk, beta);
-                const U4 w = st.draw(TAG_TRIAL, 0u);
-                const uint32_t kd1 = spare_bits_1(w);
-                kd2 = spare_bits_2(w);
-                T delta;
-                bool ok;
-                if (HYB && alpha < creutz_of<T>(D)) {
-                    qc = -Math<T>::expm1(T(-2) * alpha);
-                    ok = creutz_try(w, qc, inv2a, &delta);
+    do {
+        const uint32_t j0 = tile * (NT * R) + threadIdx.x;
+        for (int r = 0; r < R; ++r) {
+            const uint32_t j = j0 + (uint32_t)r * NT;
+            bool pend = false;
+            Quat<T> A = {T(0), T(0), T(0), T(0)}, P = A;
+            T inv2a = T(0), qc = T(0);
+            uint32_t key = 0, tk = 0, kd2 = 0, i = j;
+            if (j < Vh) {
+                const EoSite s = SLAB ? EoSite::from_slab(D, j, p, &i) : EoSite(D, j, p);
+                staple_sum<T, MU, PLAQ>(U, s, i, p, A, P);
+                const T k2 = qnorm2(A);
+                const T rk = Math<T>::rsqrt(k2);
+                const T alpha = beta * k2 * rk;
+                key = s.lex() * 4u + MU;
+                const Stream st{k0, k1, key, slo, shi};
+                if (!(alpha >= alpha_haar<T>())) {
+                    put(i, key, haar_from<T>(st.draw(TAG_DIRECTION, 0)), P, 0);
                 } else {
-                    ok = kp_try(w, inv2a, &delta);
-                }
-                if (ok) {
-                    put(i, key, new_link(delta, kd1, kd2, A), P, 1);
-                } else {
-                    pend = true;
-                    tk = 1u | (kd1 << 13);
+                    inv2a = inv_two_alpha<T>(D, rk, beta);
+                    const U4 w = st.draw(TAG_TRIAL, 0u);
+                    const uint32_t kd1 = spare_bits_1(w);
+                    kd2 = spare_bits_2(w);
+                    T delta;
+                    bool ok;
+                    if (HYB && alpha < creutz_of<T>(D)) {
+                        qc = -Math<T>::expm1(T(-2) * alpha);
+                        ok = creutz_try(w, qc, inv2a, &delta);
+                    } else {
+                        ok = kp_try(w, inv2a, &delta);
+                    }
+                    if (ok) {
+                        put(i, key, new_link(delta, kd1, kd2, A), P, 1);
+                    } else {
+                        pend = true;
+                        tk = 1u | (kd1 << 13);
+                    }
                 }
             }
+            push(pend, A, P, inv2a, qc, key, tk, kd2, i);
+            while (cnt >= 32) retry(32);
         }
-        push(pend, A, P, inv2a, qc, key, tk, kd2, i);
-        while (cnt >= 32) retry(32);
-    }
+        tile += nb;
+    } while (PERSIST && tile < ntiles);
     while (cnt > 0) retry(cnt < 32 ? cnt : 32);
     warp_totals<T, MU, PLAQ, NT>(ctx, l, blk0, Vh, plaq, ntrial, ncap);
 }
 
 // One launch shape (NT threads per block, at least MINB blocks per SM, R
-// links per thread) of the phase kernel; the grid covers ctx.phase_blocks
-// blocks of NT R links.
+// links per thread, persistent or not) of the phase kernel; the grid covers
+// ctx.phase_blocks blocks of NT R links (fewer, each walking several tiles,
+// for a persistent shape on a single lattice).
 template <typename T, int NT, int MINB, bool SLAB, int R = 1, bool PERSIST = false>
 cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int32_t* dbg,
                                bool hyb, cudaStream_t s)
@@ -434,7 +440,8 @@ cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int3
     if constexpr (R == 1 && !PERSIST)                                                           \
         hb_phase_kernel<T, MUV, PL, DB, NT, MINB, SLAB, H><<<grid, block, 0, s>>>(c, parity, dbg); \
     else                                                                                        \
-        hb_phase_queue_kernel<T, MUV, PL, DB, NT, MINB, SLAB, H, R><<<grid, block, 0, s>>>(c, parity, dbg)
+        hb_phase_queue_kernel<T, MUV, PL, DB, NT, MINB, SLAB, H, R, PERSIST><<<grid, block, 0, s>>>( \
+            c, parity, dbg)
 #define SU2_LAUNCH_H(MUV, H)                                    \
     do {                                                        \
         if (dbg) { SU2_K(MUV, false, true, H); }                \

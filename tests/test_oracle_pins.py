@@ -5,7 +5,9 @@ form, an exact identity or a brute-force case, so that a dropped term, a
 wrong sign or index, or a transposed operand in the oracle fails one of them:
 
 * Philox4x32-10       -> cuRAND's host Philox4x32-10 generator (library)
-* hot start            -> Haar moments; <P> = 0 at beta = 0 (closed form)
+* Haar draws           -> exact laws of the Haar measure on S^3 (marginal CDF,
+                          2nd and 4th moments, isotropy) for the hot start,
+                          the alpha -> 0 branch and the gauge g(x); <P> = 0
 * cold start           -> P = L = C(r) = 1 exactly (definitions, Sec. 2.1/2.2)
 * plaquette indices    -> abelian (U(1)-embedded) closed form
 * staple               -> sum_x,mu 1/2 Tr(U A) = 24 V P (exact identity)
@@ -108,20 +110,117 @@ def test_cold_start_exact(Ns, Nt):
     np.testing.assert_array_equal(O.correlator(Ns, Nt, links, Ns // 2), np.ones(Ns // 2 + 1))
 
 
-def test_hot_start_haar_moments():
-    Ns, Nt = 8, 8
-    links = O.init(Ns, Nt, hot=True, seed=1).reshape(-1, 4)
-    n = links.shape[0]
-    np.testing.assert_allclose(np.linalg.norm(links, axis=1), 1.0, atol=1e-14)
-    # Haar on S^3: <a_i> = 0, <a_i^2> = 1/4 (var of a_i^2 is 1/8 - 1/16 = 1/16)
-    assert np.all(np.abs(links.mean(0)) < 5 * 0.5 / np.sqrt(n))
-    assert np.all(np.abs((links ** 2).mean(0) - 0.25) < 5 * 0.25 / np.sqrt(n))
+# The Haar measure on SU(2) = S^3 fixes the law of every quaternion the
+# oracle draws as "random SU(2)" (hot start, the alpha -> 0 branch of the
+# heat bath, the gauge transformation's g(x)).  For a uniform point a on S^3:
+#   * each component has the density (2/pi) sqrt(1 - x^2) on [-1, 1], i.e.
+#     the CDF 1/2 + (x sqrt(1 - x^2) + arcsin x) / pi;
+#   * E[a_i a_j] = delta_ij / 4;
+#   * E[a_i^2 a_j^2] = 1/24 (i != j) and E[a_i^4] = 1/8
+#     (E[x_1^2 x_2^2] = 1/(n(n+2)), E[x_1^4] = 3/(n(n+2)) on S^(n-1), n = 4);
+#   * the direction of the vector part (a1, a2, a3)/|a| is uniform on S^2
+#     (cos(theta) and phi uniform) and independent of a0.
+# A Box-Muller pair built from cos twice, a second pair drawn from the
+# first pair's uniforms, or an angle over half a turn all break one of these.
+def _haar_cdf(x):
+    x = np.clip(x, -1.0, 1.0)
+    return 0.5 + (x * np.sqrt(1.0 - x * x) + np.arcsin(x)) / np.pi
+
+
+def _check_haar(q):
+    """Every law above, at 5 sigma (moments) or p > 1e-4 (KS)."""
+    q = np.asarray(q, np.float64).reshape(-1, 4)
+    n = q.shape[0]
+    np.testing.assert_allclose(np.linalg.norm(q, axis=1), 1.0, atol=1e-14)
+    for i in range(4):
+        assert stats.kstest(q[:, i], _haar_cdf).pvalue > 1e-4, i
+    # second moments: diagonal sd sqrt(1/8 - 1/16), off-diagonal sd sqrt(1/24)
+    m2 = q.T @ q / n
+    sd2 = np.where(np.eye(4) > 0, np.sqrt(1 / 16), np.sqrt(1 / 24)) / np.sqrt(n)
+    assert np.all(np.abs(m2 - np.eye(4) / 4) < 5 * sd2), m2
+    # fourth moments: E[a_i^4] = 1/8 (sd of a^4: sqrt(105/1920 - 1/64)),
+    # E[a_i^2 a_j^2] = 1/24 (sd: sqrt(9/1920 - 1/576))
+    q2 = q * q
+    m4 = q2.T @ q2 / n
+    exp4 = np.where(np.eye(4) > 0, 1 / 8, 1 / 24)
+    sd4 = np.where(np.eye(4) > 0, np.sqrt(105 / 1920 - 1 / 64),
+                   np.sqrt(9 / 1920 - 1 / 576)) / np.sqrt(n)
+    assert np.all(np.abs(m4 - exp4) < 5 * sd4), m4
+    # direction of the vector part: uniform on S^2, independent of a0
+    v = q[:, 1:]
+    u = v / np.linalg.norm(v, axis=1, keepdims=True)
+    assert stats.kstest(u[:, 2], stats.uniform(-1, 2).cdf).pvalue > 1e-4
+    phi = np.arctan2(u[:, 1], u[:, 0])
+    assert stats.kstest(phi, stats.uniform(-np.pi, 2 * np.pi).cdf).pvalue > 1e-4
+    for comp in (u, u * u):
+        for i in range(3):
+            assert abs(np.corrcoef(q[:, 0], comp[:, i])[0, 1]) < 5 / np.sqrt(n)
+            assert abs(np.corrcoef(q[:, 0] ** 2, comp[:, i])[0, 1]) < 5 / np.sqrt(n)
+
+
+def test_haar_pin_detects_broken_draws():
+    """The checks above reject the plausible mistakes in a Box-Muller Haar
+    draw (guards the pin itself): cos used twice, one pair reused, half-turn
+    angles, and three normals instead of four."""
+    rng = np.random.default_rng(11)
+    n = 100000
+    ua, ub, uc, ud = rng.random((4, n))
+    r1, r2 = np.sqrt(-2 * np.log(ua)), np.sqrt(-2 * np.log(uc))
+    good = np.stack([r1 * np.cos(2 * np.pi * ub), r1 * np.sin(2 * np.pi * ub),
+                     r2 * np.cos(2 * np.pi * ud), r2 * np.sin(2 * np.pi * ud)], 1)
+    bad = {
+        "cos twice": np.stack([r1 * np.cos(2 * np.pi * ub), r1 * np.cos(2 * np.pi * ub),
+                               r2 * np.cos(2 * np.pi * ud), r2 * np.cos(2 * np.pi * ud)], 1),
+        "pair reused": np.stack([good[:, 0], good[:, 1], good[:, 0], good[:, 1]], 1),
+        "half turn": np.stack([r1 * np.cos(np.pi * ub), r1 * np.sin(np.pi * ub),
+                               r2 * np.cos(np.pi * ud), r2 * np.sin(np.pi * ud)], 1),
+        "three normals": np.stack([good[:, 0], good[:, 1], good[:, 2], np.zeros(n)], 1),
+    }
+    _check_haar(good / np.linalg.norm(good, axis=1, keepdims=True))
+    for name, b in bad.items():
+        with pytest.raises(AssertionError):
+            _check_haar(b / np.linalg.norm(b, axis=1, keepdims=True))
+            pytest.fail(name)
+
+
+def test_hot_start_is_haar():
+    """or_init(hot): every link is a Haar draw (Sec. 2.1 "random SU(2)
+    matrix initialization", reading: Haar measure)."""
+    Ns = Nt = 12
+    links = O.init(Ns, Nt, hot=True, seed=1)
+    _check_haar(links)
     # <P> = 0 for independent Haar links (beta = 0), sd of one plaquette 1/2
-    links = links.reshape(-1, 4, 4)
     P = O.plaquette(Ns, Nt, links)
     assert abs(P) < 5 * 0.5 / np.sqrt(6 * Ns ** 3 * Nt)
     # different seeds give different configurations
     assert not np.array_equal(O.init(4, 4, True, 1), O.init(4, 4, True, 2))
+
+
+def test_alpha_zero_branch_is_haar():
+    """The alpha -> 0 limit of the heat-bath law is the Haar measure: at
+    beta = 0 every updated link is a Haar draw (Philox tag 1), whatever the
+    staple; and a zero staple at any beta takes the same branch."""
+    Ns = Nt = 12
+    links = inputs.random_links(Ns, Nt, 5)
+    out = []
+    for mu in range(4):
+        for p in range(2):
+            links, trials, cnt = O.heatbath_phase(Ns, Nt, links, 0.0, mu, p, seed=21, sweep=2)
+            assert np.all(trials[trials != -2] == 0) and cnt[2] == 0
+    _check_haar(links)
+    zs = np.array([O.update_from_staple([0, 0, 0, 0], 2.3, seed=8, c0=i, sweep=1)[0]
+                   for i in range(40000)])
+    _check_haar(zs)
+
+
+def test_gauge_transform_g_is_haar():
+    """or_gauge_transform of a cold start leaves U_0(x) = g(x) g(x+0)^+;
+    on even x these are products of disjoint pairs of independent g's, so
+    they are independent and Haar exactly when g is."""
+    Ns, Nt = 12, 12
+    links = O.gauge_transform(Ns, Nt, O.init(Ns, Nt, False, 0), seed=77)
+    x = np.arange(Ns ** 3 * Nt) % Ns
+    _check_haar(links[x % 2 == 0, 0])
 
 
 def _abelian(theta):

@@ -282,7 +282,11 @@ int create(int n, const int* Ns, const int* Nt, int dtype, su2_lattice** out)
         if (Ns[l] < 2 || Nt[l] < 2 || (Ns[l] & 1) || (Nt[l] & 1))
             return fail(SU2_E_INVAL, "lattice %d: Ns=%d Nt=%d must be even and >= 2", l, Ns[l],
                         Nt[l]);
-        const uint64_t V = (uint64_t)Ns[l] * Ns[l] * Ns[l] * Nt[l];
+        // extents bounded first, so the volume product cannot wrap
+        if (Ns[l] > 1024 || Nt[l] > (1 << 30))
+            return fail(SU2_E_INVAL, "lattice %d: Ns=%d Nt=%d, volume above 2^30", l, Ns[l],
+                        Nt[l]);
+        const uint64_t V = (uint64_t)Ns[l] * (uint64_t)Ns[l] * (uint64_t)Ns[l] * (uint64_t)Nt[l];
         if (V > (uint64_t(1) << 30))
             return fail(SU2_E_INVAL, "lattice %d: volume %llu above 2^30", l,
                         (unsigned long long)V);
@@ -562,13 +566,21 @@ std::string tune_key(const su2_lattice* L, int dev)
             h ^= (uint64_t)v;
             h *= 1099511628211ull;
         }
+    // the launch-shape table of this precision: a cached index names a
+    // shape only in the table it was tuned with
+    uint32_t th = 2166136261u;
+    for (const LaunchCfg& c : LAUNCH_CFG[L->dtype])
+        for (int v : {c.threads, c.min_blocks, (int)c.slab, c.rounds, (int)c.persistent}) {
+            th ^= (uint32_t)v;
+            th *= 16777619u;
+        }
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|%s|n%d|V%llu|%016llx", name.c_str(), L->dtype ? "f64" : "f32",
-             L->n, (unsigned long long)[&] {
+    snprintf(buf, sizeof buf, "%s|%s|n%d|V%llu|%016llx|t%08x", name.c_str(),
+             L->dtype ? "f64" : "f32", L->n, (unsigned long long)[&] {
                  uint64_t t = 0;
                  for (uint64_t v : L->V) t += v;
                  return t;
-             }(), (unsigned long long)h);
+             }(), (unsigned long long)h, th);
     return buf;
 }
 

@@ -96,7 +96,12 @@ extern "C" int su2_plaquette_static(const void* links, int Ns, int Nt, int dtype
     if (dtype != SU2_F32 && dtype != SU2_F64) return fail_static(SU2_E_INVAL, "bad dtype");
     if (Ns < 2 || Nt < 2 || (Ns & 1) || (Nt & 1))
         return fail_static(SU2_E_INVAL, "Ns and Nt must be even and >= 2");
-    const uint64_t V = (uint64_t)Ns * Ns * Ns * Nt;
+    // bound each extent before multiplying, so no product can wrap:
+    // Ns <= 256 keeps Ns^3 <= 2^24, and Ns^3 Nt then stays below 2^55
+    if (Ns > 256 || Nt > SU2_STATIC_MAX_SITES)
+        return fail_static(SU2_E_INVAL,
+                           "lattice larger than the static scratch allows (V > 16777216)");
+    const uint64_t V = (uint64_t)Ns * (uint64_t)Ns * (uint64_t)Ns * (uint64_t)Nt;
     if (V > (uint64_t)SU2_STATIC_MAX_SITES)
         return fail_static(SU2_E_INVAL,
                            "lattice larger than the static scratch allows (V > 16777216)");
@@ -129,7 +134,7 @@ extern "C" int su2_plaquette_static(const void* links, int Ns, int Nt, int dtype
     D.Ns = Ns;
     D.Nt = Nt;
     D.Nh = Ns / 2;
-    D.Vs = Ns * Ns * Ns;
+    D.Vs = (int32_t)((uint64_t)Ns * Ns * Ns);
     D.V = (uint32_t)V;
     D.Vh = (uint32_t)(V / 2);
     D.div_nh = make_fastdiv((uint32_t)D.Nh);

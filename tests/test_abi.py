@@ -55,7 +55,8 @@ def test_handle_sizes_and_validation():
     assert lb.value == 4 * 6 ** 3 * 4 * 32
     lib.su2_lattice_destroy(h64)
 
-    for Ns, Nt in [(3, 4), (4, 5), (0, 4), (4, 0), (-2, 4), (2048, 2048)]:
+    for Ns, Nt in [(3, 4), (4, 5), (0, 4), (4, 0), (-2, 4), (2048, 2048), (1 << 22, 1 << 22),
+                   (1 << 30, 2), (2, 1 << 30), (1 << 21, 1 << 21)]:
         bad = C.c_void_p()
         assert lib.su2_lattice_create(Ns, Nt, su2.F32, C.byref(bad)) == su2.SU2_E_INVAL
         assert bad.value is None
@@ -105,6 +106,14 @@ def test_tune_key_and_launch_config_host_side():
     key = buf.value.decode()
     parts = key.split("|")
     assert parts[1] == "f32" and parts[2] == "n2" and parts[3] == "V%d" % (4 ** 4 + 6 ** 3 * 2)
+    # the launch-shape table is part of the key (a renumbered table misses
+    # the cache instead of selecting another shape), and differs by precision
+    assert len(parts) == 6 and parts[5].startswith("t")
+    h64 = C.c_void_p()
+    assert lib.su2_batch_create(2, Ns.ctypes.data, Nt.ctypes.data, su2.F64, C.byref(h64)) == 0
+    assert lib.su2_tune_key(h64, buf, 256) == 0
+    assert buf.value.decode().split("|")[5] != parts[5]
+    lib.su2_lattice_destroy(h64)
     cfg, thr, mb = C.c_int(), C.c_int(), C.c_int()
     assert lib.su2_get_launch_config(h, C.byref(cfg), C.byref(thr), C.byref(mb)) == 0
     assert (cfg.value, thr.value) == (0, 256)
@@ -153,3 +162,17 @@ def test_bind_memory_rejects_bad_buffers_before_touching_the_device():
     # still unbound: calls that need memory are refused
     assert lib.su2_init(h, su2.COLD, 0) == su2.SU2_E_INVAL
     lib.su2_lattice_destroy(h)
+
+
+def test_static_plaquette_rejects_huge_extents_without_wrapping():
+    """Extents whose volume would wrap a 64-bit product (2^22 each: V = 2^88)
+    or exceed the static scratch are refused on the host, before any CUDA
+    call (the links pointer is never dereferenced)."""
+    lib = su2.load()
+    out = np.zeros(1, np.float64)
+    fake = C.c_void_p(1 << 20)
+    for Ns, Nt in [(1 << 22, 1 << 22), (1 << 16, 2), (258, 2), (2, 1 << 30), (64, 66),
+                   (1 << 30, 1 << 30)]:
+        rc = lib.su2_plaquette_static(fake, Ns, Nt, su2.F32, C.c_void_p(out.ctypes.data), None)
+        assert rc == su2.SU2_E_INVAL, (Ns, Nt)
+        assert b"static scratch" in lib.su2_last_error()

@@ -36,6 +36,10 @@
  * which.  With a device pointer the call is asynchronous on the handle's
  * stream; with a host pointer it returns after the data has arrived.
  *
+ * Test and measurement hooks (tuning-cache access, forced slab counts,
+ * self-tests of the arithmetic, throughput probes for the rooflines) are
+ * declared separately in su2_testing.h; they are not part of the method.
+ *
  * Errors.  Every int-returning call returns SU2_OK (0) or a negative
  * status; su2_last_error() gives a message for the calling thread.  An
  * invalid argument (SU2_E_INVAL) leaves the handle unchanged.  A
@@ -260,18 +264,6 @@ int su2_autotune(su2_lattice* lat, int* chosen);
 int su2_set_launch_config(su2_lattice* lat, int cfg);
 int su2_get_launch_config(const su2_lattice* lat, int* cfg, int* threads, int* min_blocks);
 
-/* Test hooks of the tuning cache: the handle's key (GPU name|precision|
- * shapes), and a lookup (returns 1 if found, 0 if not) and append on a
- * cache file. */
-int su2_tune_key(const su2_lattice* lat, char* buf, size_t len);
-
-/* Test hook: walk every lattice in S y-slabs under the slab launch shapes
- * (S must divide every Ns; by default S is chosen from the lattice size).
- * Synchronous. */
-int su2_set_slabs(su2_lattice* lat, int S);
-int su2_tune_cache_lookup(const char* path, const char* key, int* cfg);
-int su2_tune_cache_store(const char* path, const char* key, int cfg, double ms);
-
 /* Waits for the handle's stream; returns SU2_E_TRIALS (once) if a cap hit
  * occurred since the previous synchronising call. */
 int su2_sync(su2_lattice* lat);
@@ -309,27 +301,6 @@ const char* su2_last_error(void);
  * it and must be ordered by the caller.  Allocates nothing. */
 int su2_plaquette_static(const void* links, int Ns, int Nt, int dtype, double* out,
                          void* stream);
-
-/* Test hook: exhaustive check, over every uniform grid point
- * u = (k + 1/2) 2^-23, of the FP32 forms the heat-bath draw uses against
- * FP64 references.  out: device double[4] receiving the maximum relative
- * error of ln u, the maximum absolute error of cos^2(2 pi u), of
- * sin/cos(2 pi u), and the maximum relative error of sqrt(u).  Asynchronous
- * on `stream`. */
-int su2_selftest_math(void* out, void* stream);
-
-/* Measurement hook: the FMA throughput of the current device in FP32
- * (dtype SU2_F32) or FP64 (SU2_F64): a grid of 8 blocks of 256 threads per
- * SM, each thread running 8 independent FMA chains of `iters` steps,
- * launched twice on `stream` and the second launch timed with CUDA events.
- * *fma_per_s: FMA instructions per second summed over all threads (one FMA
- * = 2 flops).  Synchronous; allocates nothing. */
-int su2_probe_fma_rate(int dtype, int iters, double* fma_per_s, void* stream);
-
-/* Self-test of the host-side exact division used for site indexing:
- * returns the number of n in [0, limit) and divisors 1..dmax for which
- * it differs from n / d. */
-uint64_t su2_selftest_fastdiv(uint32_t dmax, uint32_t limit);
 
 #ifdef __cplusplus
 }

@@ -47,7 +47,7 @@ def flags(extra=()):
 
 def _deps_mtime() -> float:
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(INCLUDE, "su2.h"))
+    files += [os.path.join(INCLUDE, h) for h in os.listdir(INCLUDE)]
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)
 

@@ -13,7 +13,7 @@
 
 #include <nvtx3/nvToolsExt.h>
 
-#include "su2.h"
+#include "su2_testing.h"
 #include "su2_internal.h"
 
 using namespace su2;

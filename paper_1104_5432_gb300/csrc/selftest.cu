@@ -1,8 +1,9 @@
 // selftest.cu -- exhaustive check of the FP32 transcendental forms used by
 // the heat-bath draw against FP64 references, over every point of the
 // uniform grid u = (k + 1/2) 2^-23, k = 0 .. 2^23 - 1; and the FMA-rate
-// probe that gives the arithmetic rooflines their measured denominators.
-#include "su2.h"
+// and FP64 math-function probes that give the arithmetic rooflines their
+// measured denominators (declared in su2_testing.h).
+#include "su2_testing.h"
 #include "su2_internal.h"
 #include "su2_math.cuh"
 
@@ -65,34 +66,104 @@ __global__ void __launch_bounds__(256) fma_rate_kernel(int iters, T a, T b)
     if (s == T(-1)) fma_rate_sink = (double)s;  // never true here; keeps the chains live
 }
 
+// 8 independent chains of one FP64 math function per thread, each call fed
+// by the previous result so that none can be hoisted or removed
+template <int FN>
+__global__ void __launch_bounds__(256) special_rate_kernel(int iters)
+{
+    double x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = 0.25 + 1e-3 * (double)(threadIdx.x + j);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (FN == SU2_PROBE_LOG) x[j] = log(x[j] + 2.0);
+            else if (FN == SU2_PROBE_COSPI) x[j] = cospi(x[j]);
+            else if (FN == SU2_PROBE_SINCOSPI) {
+                double sn, cs;
+                sincospi(x[j], &sn, &cs);
+                x[j] = sn + cs;
+            } else if (FN == SU2_PROBE_SQRT) x[j] = sqrt(x[j]);
+            else x[j] = rsqrt(x[j]);
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += x[j];
+    if (s == -1.0) fma_rate_sink = s;  // never true here; keeps the chains live
+}
+
+// launch `blocks` blocks twice on s, time the second launch
+template <typename F>
+int time_probe(F launch, cudaStream_t s, float* ms)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return SU2_E_CUDA;
+    }
+    for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up
+        cudaEventRecord(e0, s);
+        launch();
+        cudaEventRecord(e1, s);
+    }
+    const cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess || *ms <= 0.0f) return SU2_E_CUDA;
+    return SU2_OK;
+}
+
+int probe_blocks(unsigned* blocks)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SU2_E_CUDA;
+    *blocks = (unsigned)sms * 8u;
+    return SU2_OK;
+}
+
 }  // namespace
 }  // namespace su2
+
+extern "C" int su2_probe_special_rate(int fn, int iters, double* calls_per_s, void* stream)
+{
+    if (!calls_per_s || iters <= 0 || fn < SU2_PROBE_LOG || fn > SU2_PROBE_RSQRT)
+        return SU2_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned blocks = 0;
+    if (int rc = su2::probe_blocks(&blocks)) return rc;
+    float ms = 0.0f;
+    auto launch = [&] {
+        switch (fn) {
+        case SU2_PROBE_LOG: su2::special_rate_kernel<SU2_PROBE_LOG><<<blocks, 256, 0, s>>>(iters); break;
+        case SU2_PROBE_COSPI: su2::special_rate_kernel<SU2_PROBE_COSPI><<<blocks, 256, 0, s>>>(iters); break;
+        case SU2_PROBE_SINCOSPI: su2::special_rate_kernel<SU2_PROBE_SINCOSPI><<<blocks, 256, 0, s>>>(iters); break;
+        case SU2_PROBE_SQRT: su2::special_rate_kernel<SU2_PROBE_SQRT><<<blocks, 256, 0, s>>>(iters); break;
+        default: su2::special_rate_kernel<SU2_PROBE_RSQRT><<<blocks, 256, 0, s>>>(iters); break;
+        }
+    };
+    if (int rc = su2::time_probe(launch, s, &ms)) return rc;
+    *calls_per_s = (double)blocks * 256.0 * 8.0 * (double)iters / (ms * 1e-3);
+    return SU2_OK;
+}
 
 extern "C" int su2_probe_fma_rate(int dtype, int iters, double* fma_per_s, void* stream)
 {
     if (!fma_per_s || iters <= 0 || (dtype != SU2_F32 && dtype != SU2_F64)) return SU2_E_INVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return SU2_E_CUDA;
-    const unsigned blocks = (unsigned)sms * 8u;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SU2_E_CUDA;
+    unsigned blocks = 0;
+    if (int rc = su2::probe_blocks(&blocks)) return rc;
     float ms = 0.0f;
-    for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up
-        cudaEventRecord(e0, s);
+    auto launch = [&] {
         if (dtype == SU2_F32)
             su2::fma_rate_kernel<float><<<blocks, 256, 0, s>>>(iters, 0.999f, 1e-4f);
         else
             su2::fma_rate_kernel<double><<<blocks, 256, 0, s>>>(iters, 0.999, 1e-4);
-        cudaEventRecord(e1, s);
-    }
-    const cudaError_t e = cudaEventSynchronize(e1);
-    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess || ms <= 0.0f) return SU2_E_CUDA;
+    };
+    if (int rc = su2::time_probe(launch, s, &ms)) return rc;
     *fma_per_s = (double)blocks * 256.0 * 8.0 * (double)iters / (ms * 1e-3);
     return SU2_OK;
 }

@@ -84,6 +84,7 @@ def load(build_if_needed: bool = True):
             "su2_get_links_f32": (i, [P, i, P]),
             "su2_set_links_f32": (i, [P, i, P]),
             "su2_probe_fma_rate": (i, [i, i, P, P]),
+            "su2_probe_special_rate": (i, [i, i, P, P]),
             "su2_autotune": (i, [P, P]),
             "su2_set_launch_config": (i, [P, i]),
             "su2_get_launch_config": (i, [P, P, P, P]),
@@ -116,6 +117,19 @@ def probe_fma_rate(dtype: int, iters: Optional[int] = None) -> float:
     v = C.c_double()
     _check(load().su2_probe_fma_rate(int(dtype), int(iters), C.byref(v),
                                       C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return v.value
+
+
+PROBE_LOG, PROBE_COSPI, PROBE_SINCOSPI, PROBE_SQRT, PROBE_RSQRT = range(5)
+
+
+def probe_special_rate(fn: int, iters: int = 1024) -> float:
+    """Calls per second of one FP64 math function of the heat-bath draw on
+    the current device (measurement hook for the FP64 roofline)."""
+    import torch
+    v = C.c_double()
+    _check(load().su2_probe_special_rate(int(fn), int(iters), C.byref(v),
+                                          C.c_void_p(torch.cuda.current_stream().cuda_stream)))
     return v.value
 
 

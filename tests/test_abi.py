@@ -12,18 +12,31 @@ from paper_1104_5432_gb300 import su2
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
-    text = open(os.path.join(ROOT, "include", "su2.h")).read()
+HEADERS = ("su2.h", "su2_testing.h")
+
+
+def declared_functions(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(su2_[a-z0-9_]+)\s*\(", text)))
 
 
-def test_every_declared_symbol_is_exported():
+@pytest.mark.parametrize("header", HEADERS)
+def test_every_declared_symbol_is_exported(header):
     lib = su2.load()
-    names = declared_functions()
-    assert len(names) >= 25
+    names = declared_functions(header)
+    assert len(names) >= (25 if header == "su2.h" else 8)
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_headers_split_method_from_hooks():
+    """su2.h declares the method's boundary only; the test and measurement
+    hooks live in su2_testing.h, and no name is declared in both."""
+    method, hooks = declared_functions("su2.h"), declared_functions("su2_testing.h")
+    assert not set(method) & set(hooks)
+    assert not [n for n in method if "selftest" in n or "probe" in n or "tune_cache" in n]
+    assert "su2_probe_special_rate" in hooks and "su2_set_slabs" in hooks
 
 
 def test_fastdiv_exact():

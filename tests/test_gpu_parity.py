@@ -474,6 +474,21 @@ def test_fma_rate_probe():
         su2.probe_fma_rate(7)
 
 
+def test_special_function_rate_probe():
+    """The FP64 roofline's per-function denominators: every probed function
+    runs below the FP64 FMA rate (each is several FP64 operations), stably
+    to 15% between calls; a bad function index is refused."""
+    fma = su2.probe_fma_rate(su2.F64)
+    for fn in (su2.PROBE_LOG, su2.PROBE_COSPI, su2.PROBE_SINCOSPI, su2.PROBE_SQRT,
+               su2.PROBE_RSQRT):
+        r = su2.probe_special_rate(fn)
+        again = su2.probe_special_rate(fn)
+        assert 0 < r < fma, (fn, r, fma)
+        assert abs(again - r) <= 0.15 * r, (fn, r, again)
+    with pytest.raises(su2.SU2Error):
+        su2.probe_special_rate(5)
+
+
 @pytest.mark.parametrize("dtype", [su2.F32, su2.F64])
 def test_every_launch_shape_gives_identical_results(dtype):
     """The random streams are keyed by link and sweep, never by thread: each

@@ -160,6 +160,60 @@ def recorded_traffic(kernel_key, field="dram_bytes_per_launch_full_size"):
     return ent.get(field)
 
 
+# FP64 arithmetic of one link update (the FP64 arm is bound by GB300's FP64
+# units, not by memory): algorithmic flops outside the math functions --
+# 12 quaternion products (336), staple additions (20), k (8), alpha and
+# 1/(2 alpha) (5), per Kennedy-Pendleton trial 10, the direction, X Vhat^+
+# and the renormalisation (~40) -- and the math-function calls the update
+# makes: per trial 2 log + 1 cospi (lambda^2), and once 2 rsqrt (1/k, the
+# renormalisation), 2 sqrt (sin theta, |vector part|), 1 sincospi (phi).
+FP64_FLOPS_FIXED, FP64_FLOPS_PER_TRIAL = 420.0, 10.0
+FP64_CALLS = {"log": (0, 2), "cospi": (0, 1), "sincospi": (1, 0), "sqrt": (2, 0),
+              "rsqrt": (2, 0)}  # (per update, per trial)
+
+
+def fp64_roofline(su2, ups, trials_per_update):
+    """Time per update if the FP64 units did nothing but the update's
+    algorithmic work: flops / (2 x measured DFMA rate) plus, per math
+    function, calls / its measured call rate.  peak = 1 / that time."""
+    t = trials_per_update
+    fma = su2.probe_fma_rate(su2.F64)
+    ids = {"log": su2.PROBE_LOG, "cospi": su2.PROBE_COSPI, "sincospi": su2.PROBE_SINCOSPI,
+           "sqrt": su2.PROBE_SQRT, "rsqrt": su2.PROBE_RSQRT}
+    rates = {k: su2.probe_special_rate(ids[k]) for k in FP64_CALLS}
+    flops = FP64_FLOPS_FIXED + FP64_FLOPS_PER_TRIAL * t
+    parts = {"flops": flops / (2 * fma)}
+    for k, (fixed, per_trial) in FP64_CALLS.items():
+        parts[k] = (fixed + per_trial * t) / rates[k]
+    T = sum(parts.values())
+    fl_ncu = recorded_traffic("f64_64^4", "fp64_flops_per_update")
+    busy = recorded_traffic("f64_64^4", "fp64_pipe_active_pct")
+    return {"bound": "alu", "unit": UNIT, "achieved": ups, "peak": 1.0 / T,
+            "frac": round(ups * T, 4), "traffic": None,
+            "peak_kind": "measured here: algorithmic FP64 work per update over the DFMA-chain "
+                         "rate (su2_probe_fma_rate) and each math function's call rate "
+                         "(su2_probe_special_rate)",
+            "trials_per_update": round(t, 5),
+            "algorithmic_flops_per_update": round(flops, 2),
+            "fma_per_s": fma, "calls_per_s": {k: round(v, 0) for k, v in rates.items()},
+            "ns_per_update": {k: round(v * 1e9, 5) for k, v in parts.items()},
+            "ncu": {"fp64_flops_per_update_issued": fl_ncu,
+                    "fp64_pipe_busy": None if busy is None else busy / 100,
+                    "note": "instruction counts explain the gap; the bound uses the algorithmic "
+                            "work only"}}
+
+
+def main_config(world):
+    """The `config` both arms print (the reference arm times a bounded
+    sample of this workload on the host: one phase per step)."""
+    return {"workload": workload_name("FP32 links and update, FP64 reductions"),
+            "link_bytes": 4 * WORKLOAD["Ns"] ** 3 * WORKLOAD["Nt"] * 16,
+            "l2": "inputs larger than L2 (1 GiB of links vs 129 MB L2), no flush",
+            "parallelism": f"{world} independent lattice(s), one per GPU",
+            "reference_step": "the reference arm (FP64 CPU oracle, one host thread) times one "
+                              "checkerboard phase of this workload per step (V/2 link updates)"}
+
+
 def gpu_arm(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -327,21 +381,11 @@ def gpu_arm(args, rank, world, local):
 
         t64 = time_steps(step_f64, 1, 1)
         lat64.sync()
-        busy = recorded_traffic("f64_64^4", "fp64_pipe_active_pct")
         v64 = world * 4 * V * sw64 / t64
-        # FP64 flops per update counted by ncu (2 per DFMA, 1 per DMUL/DADD)
-        # against the measured FP64 FMA rate of this GPU
-        fl = recorded_traffic("f64_64^4", "fp64_flops_per_update")
-        peak64 = 2 * su2.probe_fma_rate(su2.F64) / 1e12
-        roof64 = {"bound": "alu", "unit": "TFLOP/s",
-                  "achieved": None if fl is None else round(fl * v64 / world / 1e12, 4),
-                  "peak": round(peak64, 4),
-                  "peak_kind": "measured here: FP64 FMA-chain probe (su2_probe_fma_rate)",
-                  "flops_per_update": fl,
-                  "fp64_pipe_busy_ncu": None if busy is None else busy / 100,
-                  "note": "bound by GB300's FP64 pipe; memory < 4% of its peak"}
-        roof64["frac"] = None if fl is None else round(roof64["achieved"] / peak64, 4)
-        arms["fp64_plain"] = {"value": v64, "unit": UNIT, "roofline": roof64,
+        st64 = lat64.stats()  # counters of the timed step (init resets them)
+        arms["fp64_plain"] = {"value": v64, "unit": UNIT,
+                              "roofline": fp64_roofline(su2, v64 / world,
+                                                        st64["trials"] / st64["updates"]),
                               "workload": workload_name("FP64 throughout").replace(
                                   f"{sweeps} checkerboard", f"{sw64} checkerboard"),
                               "ms_per_sweep": t64 / sw64 * 1e3}
@@ -628,7 +672,7 @@ def reference_arm(args, rank, world):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name("FP64 CPU oracle"), "l2": "inputs larger than L2"},
+            "config": main_config(args.gpus),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample, "cpu": cpu_model()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -664,6 +708,32 @@ def profile_case(args):
     lat.sync()
     print(json.dumps({"profile_case": args.profile_case, "launch_shape": lat.launch_config(),
                       "plaquette": pl.cpu().tolist()}))
+
+
+def summary(line):
+    """The companion arms' headline figures in a few hundred characters."""
+    a = line.get("arms") or {}
+
+    def g(x):
+        return None if x is None else round(x / 1e9, 3)
+
+    out = {"unit": "G link updates/s", "fp32_64^4": g(line["value"]),
+           "fp32_64^4_frac_hbm": line["roofline"]["frac"], "e2e": g(line["e2e"]["value"])}
+    if "fp64_plain" in a:
+        out["fp64_plain_64^4"] = g(a["fp64_plain"]["value"])
+        out["fp64_plain_frac_alu"] = a["fp64_plain"]["roofline"]["frac"]
+    for k in ("fp32_batched", "fp32_temperature_scan", "fp32_128^4", "fp64_8^4_beta2.3",
+              "fp32_32^4_beta6.0", "fp64_32^4_beta6.0"):
+        if k in a:
+            out[k] = g(a[k]["value"])
+    if "fp32_over_fp64_plain" in a:
+        out["fp32_over_fp64_plain"] = round(a["fp32_over_fp64_plain"], 2)
+    if "fp32_vs_fp64_plaquette" in a:
+        out["plaquette_fp32_vs_fp64_sigma"] = round(a["fp32_vs_fp64_plaquette"]["diff_in_sigma"], 2)
+    if "size_sweep_beta6" in a:
+        out["size_sweep_beta6"] = {k: [v["fp32"], v["fp64"]]
+                                   for k, v in a["size_sweep_beta6"]["per_size"].items()}
+    return out
 
 
 def main():
@@ -703,15 +773,13 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": r["t_main"] / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": workload_name("FP32 links and update, FP64 reductions"),
-                           "link_bytes": 4 * WORKLOAD["Ns"] ** 3 * WORKLOAD["Nt"] * 16,
-                           "l2": "inputs larger than L2 (1 GiB of links vs 129 MB L2), no flush",
-                           "parallelism": f"{world} independent lattice(s), one per GPU"},
+                "config": main_config(world),
                 "roofline": r["roofline"], "cpu_baseline": cpu,
                 "cpu_baseline_all_cores": cpu_all, "e2e": r["e2e"],
                 "gpu_launches": r["launches"], "clocks": r["clocks"],
                 "step_effective_gbs": round(r["step_gbs"], 1), "arms": r["arms"],
                 "launch_shapes": r["tuned"]}
+        line["summary"] = summary(line)  # last key: the end of the line is what logs keep
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

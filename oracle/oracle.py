@@ -61,6 +61,8 @@ def lib():
             L.or_update_from_staple.restype = i
             L.or_heatbath_link.argtypes = [i, i, P, d, i, C.c_long, u64, u64, d, P]
             L.or_heatbath_link.restype = i
+            L.or_heatbath_link_hot.argtypes = [i, i, u64, d, i, C.c_long, u64, u64, d, P]
+            L.or_heatbath_link_hot.restype = i
             L.or_kp_samples.argtypes = [d, u64, u64, C.c_long, i, P, P]
             L.or_kp_samples.restype = None
             L.or_plaquette.argtypes = [i, i, P]
@@ -155,6 +157,16 @@ def heatbath_link(Ns, Nt, links, beta, mu, lex, seed, sweep, creutz_below=0.0):
     out = np.zeros(4, np.float64)
     t = lib().or_heatbath_link(Ns, Nt, _ptr(links), float(beta), mu, int(lex), seed, sweep,
                                float(creutz_below), _ptr(out))
+    return out, t
+
+
+def heatbath_link_hot(Ns, Nt, init_seed, beta, mu, lex, seed, sweep=0, creutz_below=0.0):
+    """(new link, trials) of U_mu(lex) drawn from the hot start of seed
+    init_seed, whose 18 staple links are drawn on demand (for sampled
+    checks of the first phase on lattices too large to hold)."""
+    out = np.zeros(4, np.float64)
+    t = lib().or_heatbath_link_hot(Ns, Nt, init_seed, float(beta), mu, int(lex), seed, sweep,
+                                   float(creutz_below), _ptr(out))
     return out, t
 
 

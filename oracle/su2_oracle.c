@@ -328,25 +328,39 @@ void or_gauge_transform(int Ns, int Nt, double *links, uint64_t seed)
 /* staple and the heat-bath draw                                      */
 /* ------------------------------------------------------------------ */
 
+/* Where the staple reads its links: an array in the canonical layout, or
+ * (links == NULL) the hot start of or_init with key hot_seed, drawn link
+ * by link on demand. */
+typedef struct { const double *links; uint64_t hot_seed; } linksrc;
+
+static mat2 src_link(const linksrc *src, long lex, int mu)
+{
+    if (src->links) return link(src->links, lex, mu);
+    double u[4], a[4];
+    draw(src->hot_seed, (uint32_t)(lex * 4 + mu), 0, 2, 0, u);
+    haar_quat(u, a);
+    return m_from_quat(a);
+}
+
 /* A_mu(x) = sum_{nu != mu} [ U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
  *                          + U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu) ]
  * so that Re Tr(U_mu(x) A_mu(x)) collects every plaquette holding U_mu(x). */
-static mat2 staple(const geom *g, const double *links, const int c[4], int mu)
+static mat2 staple_from(const geom *g, const linksrc *src, const int c[4], int mu)
 {
     mat2 A = m_zero();
     long x = lex_of(g, c);
     for (int nu = 0; nu < 4; ++nu) {
         if (nu == mu) continue;
-        mat2 a = link(links, shifted(g, c, mu, 1), nu);
-        mat2 b = link(links, shifted(g, c, nu, 1), mu);
-        mat2 cc = link(links, x, nu);
+        mat2 a = src_link(src, shifted(g, c, mu, 1), nu);
+        mat2 b = src_link(src, shifted(g, c, nu, 1), mu);
+        mat2 cc = src_link(src, x, nu);
         mat2 bd = m_dag(&b), cd = m_dag(&cc);
         mat2 t = m_mul(&a, &bd);
         mat2 up = m_mul(&t, &cd);
 
-        mat2 d = link(links, shifted2(g, c, mu, 1, nu, -1), nu);
-        mat2 e = link(links, shifted(g, c, nu, -1), mu);
-        mat2 f = link(links, shifted(g, c, nu, -1), nu);
+        mat2 d = src_link(src, shifted2(g, c, mu, 1, nu, -1), nu);
+        mat2 e = src_link(src, shifted(g, c, nu, -1), mu);
+        mat2 f = src_link(src, shifted(g, c, nu, -1), nu);
         mat2 dd = m_dag(&d), ed = m_dag(&e);
         mat2 s = m_mul(&dd, &ed);
         mat2 lo = m_mul(&s, &f);
@@ -355,6 +369,12 @@ static mat2 staple(const geom *g, const double *links, const int c[4], int mu)
         A = m_add(&A, &lo);
     }
     return A;
+}
+
+static mat2 staple(const geom *g, const double *links, const int c[4], int mu)
+{
+    linksrc src = { links, 0 };
+    return staple_from(g, &src, c, mu);
 }
 
 /* Kennedy-Pendleton draw of delta = 1 - a0 with density proportional to
@@ -484,6 +504,22 @@ int or_heatbath_link(int Ns, int Nt, const double *links, double beta, int mu, l
     int c[4];
     coords_of(&g, lex, c);
     mat2 A = staple(&g, links, c, mu);
+    return update_from_staple(&A, beta, seed, (uint32_t)(lex * 4 + mu), sweep, creutz_below, unew);
+}
+
+/* The link the first phase after a hot start, (mu, parity) = (0, 0) at
+ * sweep 0 when lex is an even site, draws for U_mu(lex): the same as
+ * or_heatbath_link on or_init(Ns, Nt, 1, init_seed), but only the 18 links
+ * of the staple are drawn, so lattices too large to hold on the host
+ * (128^4: 34 GB of links) can be checked at sampled sites. */
+int or_heatbath_link_hot(int Ns, int Nt, uint64_t init_seed, double beta, int mu, long lex,
+                         uint64_t seed, uint64_t sweep, double creutz_below, double unew[4])
+{
+    geom g = mkgeom(Ns, Nt);
+    int c[4];
+    coords_of(&g, lex, c);
+    linksrc src = { NULL, init_seed };
+    mat2 A = staple_from(&g, &src, c, mu);
     return update_from_staple(&A, beta, seed, (uint32_t)(lex * 4 + mu), sweep, creutz_below, unew);
 }
 

@@ -23,6 +23,8 @@ int or_heatbath_link(int Ns, int Nt, const double *links, double beta, int mu, l
                      uint64_t seed, uint64_t sweep, double creutz_below, double unew[4]);
 int or_update_from_staple(const double A[4], double beta, uint64_t seed, uint32_t c0,
                           uint64_t sweep, double creutz_below, double unew[4]);
+int or_heatbath_link_hot(int Ns, int Nt, uint64_t init_seed, double beta, int mu, long lex,
+                         uint64_t seed, uint64_t sweep, double creutz_below, double unew[4]);
 void or_kp_samples(double alpha, uint64_t seed, uint64_t sweep, long n, int creutz, double *a0,
                    int32_t *trials);
 double or_plaquette(int Ns, int Nt, const double *links);
@@ -78,7 +80,8 @@ static int run_lattice(int Ns, int Nt)
     double u[4];
     for (long lex = 0; lex < V; lex += (V / 7) + 1)
         for (int mu = 0; mu < 4; ++mu)
-            if (or_heatbath_link(Ns, Nt, links, 2.5, mu, lex, 6, 11, 0.0, u) < -1)
+            if (or_heatbath_link(Ns, Nt, links, 2.5, mu, lex, 6, 11, 0.0, u) < -1 ||
+                or_heatbath_link_hot(Ns, Nt, 3, 2.5, mu, lex, 6, 0, 0.0, u) < -1)
                 return fail("single link");
     double A[4];
     or_staple(Ns, Nt, links, V - 1, 3, A);

@@ -59,3 +59,51 @@ def test_oracle_all_cores_leg_small():
     assert r is not None
     ups, n, updates, dt = r
     assert n >= 1 and updates == n * (4 ** 4 // 2) and ups > 0 and dt > 0
+
+
+class _FakeRates:
+    """Stand-in for the throughput probes: fixed rates, no GPU."""
+    F64 = 1
+    PROBE_LOG, PROBE_COSPI, PROBE_SINCOSPI, PROBE_SQRT, PROBE_RSQRT = range(5)
+
+    @staticmethod
+    def probe_fma_rate(dtype):
+        return 5e11  # DFMA/s
+
+    @staticmethod
+    def probe_special_rate(fn):
+        return 1e10 * (fn + 1)
+
+
+def test_fp64_roofline_follows_the_algorithmic_model():
+    """T_roof = (420 + 10 t) / (2 x DFMA rate) + sum_f n_f / rate_f with the
+    update's math-function calls (per trial 2 log + 1 cospi; 2 rsqrt,
+    2 sqrt, 1 sincospi); frac = achieved x T_roof."""
+    t = 1.04
+    r = bench.fp64_roofline(_FakeRates, 1.2e9, t)
+    T = ((420 + 10 * t) / 1e12 + 2 * t / 1e10 + t / 2e10 + 1 / 3e10 + 2 / 4e10 + 2 / 5e10)
+    assert r["peak"] == pytest.approx(1 / T, rel=1e-12)
+    assert r["frac"] == pytest.approx(1.2e9 * T, abs=1e-4)
+    assert r["algorithmic_flops_per_update"] == pytest.approx(430.4)
+    assert r["bound"] == "alu" and r["unit"] == bench.UNIT
+
+
+def test_summary_is_short_and_last():
+    """The summary carries the companion arms in few characters, so the end
+    of the bench line (what a truncated log keeps) shows them."""
+    arms = {"fp64_plain": {"value": 1.22e9, "roofline": {"frac": 0.61}},
+            "fp32_batched": {"value": 3.87e10}, "fp32_temperature_scan": {"value": 3.48e10},
+            "fp32_128^4": {"value": 3.92e10}, "fp64_8^4_beta2.3": {"value": 7.0e7},
+            "fp32_32^4_beta6.0": {"value": 3.1e10}, "fp64_32^4_beta6.0": {"value": 1.1e9},
+            "fp32_over_fp64_plain": 32.8,
+            "fp32_vs_fp64_plaquette": {"diff_in_sigma": 0.66},
+            "size_sweep_beta6": {"per_size": {f"{n}^4": {"fp32": 1.0, "fp64": 0.1}
+                                              for n in (8, 12, 16, 24, 32, 48, 64)}}}
+    line = {"value": 4.02e10, "roofline": {"frac": 0.779}, "e2e": {"value": 3.91e10},
+            "arms": arms}
+    s = bench.summary(line)
+    assert s["fp32_batched"] == 38.7 and s["fp64_plain_frac_alu"] == 0.61
+    assert len(json.dumps(s)) < 1000
+    # both arms print the same config
+    assert bench.main_config(1) == bench.main_config(1)
+    assert "one checkerboard phase" in bench.main_config(1)["reference_step"]

@@ -566,6 +566,65 @@ def test_full_size_128_properties(shape):
     torch.cuda.empty_cache()
 
 
+def sampled_links(lat, V, lexes, dtype):
+    """Links of the sampled sites, [len(lexes), 4, 4] float64 on the host,
+    through a canonical copy kept on the device (the full host copy of a
+    128^4 lattice would be 17-34 GB)."""
+    dev = torch.empty((V, 4, 4), dtype=torch.float32 if dtype == su2.F32 else torch.float64,
+                      device="cuda")
+    lat.get_links(out=dev)
+    torch.cuda.synchronize()
+    idx = torch.as_tensor(np.asarray(lexes, np.int64), device="cuda")
+    out = dev.index_select(0, idx).double().cpu().numpy()
+    del dev
+    return out
+
+
+def even_sample(Ns, Nt, n, seed):
+    rng = np.random.default_rng(seed)
+    lex = rng.choice(Ns ** 3 * Nt, size=3 * n, replace=False)
+    x, y, z, t = lex % Ns, (lex // Ns) % Ns, (lex // Ns ** 2) % Ns, lex // Ns ** 3
+    return lex[(x + y + z + t) % 2 == 0][:n]
+
+
+@pytest.mark.parametrize("dtype,Ns,shape,seed", [(su2.F32, 128, 13, 3), (su2.F64, 64, 12, 3)])
+def test_full_size_sampled_from_oracle_hot_start(dtype, Ns, shape, seed):
+    """The benchmark's full-size lattices in the launch shapes its autotuner
+    picks -- 128^4 FP32 (16 GiB) in the y-slab queued shape 13 (16 slabs,
+    16 links per thread) and 64^4 FP64 in the persistent queued shape 12 --
+    one graph-replayed sweep at beta = 2.5 from the hot start.  U_0 on even
+    sites is final after the first phase, so each sampled link is checked
+    against the oracle's draw from ITS OWN hot start (the 18 staple links
+    drawn on demand from the seed; nothing comes from the GPU): FP64 to
+    1e-12 with no flipped decision; FP32 to 2e-5 with at most one flip."""
+    Nt = Ns
+    V = Ns ** 3 * Nt
+    lat = lattice(Ns, Nt, dtype)
+    lat.set_launch_config(shape)
+    lat.init(su2.HOT, seed)
+    plaq = lat.heatbath(2.5, 1, seed)
+    st = lat.stats()
+    assert st["updates"] == 4 * V and st["cap_hits"] == 0
+    assert 0.3 < plaq[0, 0] < 0.5
+    lexes = even_sample(Ns, Nt, 1500, 1)
+    got = sampled_links(lat, V, lexes, dtype)
+    lat.close()
+    torch.cuda.empty_cache()
+    tol = 1e-12 if dtype == su2.F64 else 2e-5
+    flips, worst = 0, 0.0
+    for k, lex in enumerate(lexes):
+        u, tr = O.heatbath_link_hot(Ns, Nt, seed, 2.5, 0, int(lex), seed, 0)
+        assert tr >= 1
+        d = float(np.max(np.abs(got[k, 0] - u)))
+        if d > tol:
+            flips += 1
+        else:
+            worst = max(worst, d)
+    assert len(lexes) >= 1000
+    assert flips <= (0 if dtype == su2.F64 else 1), flips
+    assert worst <= tol, worst
+
+
 QUEUED = [(su2.F32, 6), (su2.F32, 8), (su2.F32, 10), (su2.F32, 11), (su2.F32, 12), (su2.F64, 6),
           (su2.F64, 10), (su2.F64, 12), (su2.F64, 13)]
 

@@ -552,3 +552,23 @@ def test_single_link_entry_matches_phase():
         if par == 1:
             np.testing.assert_array_equal(u, new[lex, 2])
             assert t == trials[lex, 2]
+
+
+def test_single_link_from_hot_start_on_demand():
+    """Drawing the staple's links on demand from the hot-start seed gives
+    bit for bit what the phase draws on the stored hot start."""
+    Ns, Nt = 4, 6
+    links = O.init(Ns, Nt, True, 9)
+    new, trials, _ = O.heatbath_phase(Ns, Nt, links, 2.5, 0, 0, seed=3, sweep=0)
+    par = (np.arange(Ns ** 3 * Nt) % Ns + np.arange(Ns ** 3 * Nt) // Ns % Ns
+           + np.arange(Ns ** 3 * Nt) // Ns ** 2 % Ns + np.arange(Ns ** 3 * Nt) // Ns ** 3) % 2
+    for lex in np.flatnonzero(par == 0)[::7]:
+        u, t = O.heatbath_link_hot(Ns, Nt, 9, 2.5, 0, int(lex), 3, 0)
+        np.testing.assert_array_equal(u, new[lex, 0])
+        assert t == trials[lex, 0]
+    # other directions agree with the single-link entry on the stored links
+    for mu, lex in ((3, 5), (1, 77), (2, 140)):
+        u, t = O.heatbath_link_hot(Ns, Nt, 9, 1.7, mu, lex, 4, 2)
+        v, tv = O.heatbath_link(Ns, Nt, links, 1.7, mu, lex, 4, 2)
+        np.testing.assert_array_equal(u, v)
+        assert t == tv

@@ -48,6 +48,9 @@ def parse():
                     help="run only a few sweeps of one lattice (for ncu captures) and exit")
     ap.add_argument("--launch-shape", type=int, default=None,
                     help="phase-kernel launch shape index instead of autotuning")
+    ap.add_argument("--layout", choices=["auto", "plain", "pairs"], default="auto",
+                    help="FP32 link layout of the main arm and the profile cases (auto: the "
+                         "library's default, site pairs when Nt is a multiple of 4)")
     return ap.parse_args()
 
 
@@ -214,6 +217,18 @@ def main_config(world):
                               "checkerboard phase of this workload per step (V/2 link updates)"}
 
 
+def layout_arg(args, su2):
+    return {"auto": None, "plain": su2.LAYOUT_PLAIN, "pairs": su2.LAYOUT_PAIRS}[args.layout]
+
+
+def shape_name(lat, idx=None):
+    """The launch shape a handle runs (its table row by precision and link
+    layout), by name."""
+    from paper_1104_5432_gb300.csrc_info import launch_shapes, row_name
+    row = row_name(lat.dtype, lat.link_layout())
+    return row, launch_shapes(row)[lat.launch_config()[0] if idx is None else idx]
+
+
 def gpu_arm(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -257,12 +272,12 @@ def gpu_arm(args, rank, world, local):
         return max_over_ranks(e0.elapsed_time(e1) / 1e3)
 
     # ---- main arm: FP32, inputs resident in HBM --------------------------------
-    lat = su2.Lattice(Ns, Nt, su2.F32)
+    lat = su2.Lattice(Ns, Nt, su2.F32, layout=layout_arg(args, su2))
     if args.launch_shape is None:
-        tuned = {"fp32": lat.autotune()}  # launch shape chosen by measurement
+        lat.autotune()  # launch shape chosen by measurement
     else:
         lat.set_launch_config(args.launch_shape)
-        tuned = {"fp32": args.launch_shape}
+    tuned = {"fp32": shape_name(lat)[1]}
     plaq_dev = torch.zeros(sweeps, dtype=torch.float64, device="cuda")
 
     def step_f32():
@@ -298,8 +313,9 @@ def gpu_arm(args, rank, world, local):
     hbm, peak_kind = peaks()
     bytes_launch = BYTES_PER_UPDATE["f32"] * (V // 2)
     achieved = bytes_launch / phase_s / 1e9
-    from paper_1104_5432_gb300.csrc_info import _F32, launch_shapes
+    from paper_1104_5432_gb300.csrc_info import ROWS, launch_shapes
     shape = lat.launch_config()[0]
+    row, sname = shape_name(lat)
     # instruction-issue roofline of the same launches: warp instructions per
     # launch (ncu) over the event-timed duration, against one warp
     # instruction per clock per SM sub-partition at the sampled SM clock
@@ -313,15 +329,16 @@ def gpu_arm(args, rank, world, local):
              "inst_per_update": None if inst is None else round(inst / (V // 2), 1),
              "achieved": None if inst is None else inst / phase_s}
     issue["frac"] = None if inst is None or not issue_peak else round(issue["achieved"] / issue_peak, 4)
-    queued = _F32[shape][3] > 1 or _F32[shape][4]  # several links per thread, or persistent
-    kname = "hb_phase_queue_kernel<float>" if queued else "hb_phase_kernel<float>"
+    queued = ROWS[row][shape][3] > 1 or ROWS[row][shape][4]  # several links, or persistent
+    kname = ("hb_pair_kernel (FP32 site pairs)" if row == "f32pairs" else
+             "hb_phase_queue_kernel<float>" if queued else "hb_phase_kernel<float>")
     traffic = recorded_traffic("f32_64^4")
     traffic_shape = recorded_traffic("f32_64^4", "launch_shape")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic,
                 "traffic_captured_on": None if traffic is None else
-                f"launch shape {traffic_shape} ({launch_shapes(False)[traffic_shape]})",
-                "kernel": f"{kname}, launch shape {shape} ({launch_shapes(False)[shape]}): one "
+                f"launch shape {traffic_shape} ({launch_shapes(row)[traffic_shape]})",
+                "kernel": f"{kname}, launch shape {shape} ({sname}): one "
                           "checkerboard phase, V/2 link updates",
                 "bytes_per_launch": bytes_launch, "launch_ms": round(phase_s * 1e3, 4),
                 "issue": issue,
@@ -371,7 +388,8 @@ def gpu_arm(args, rank, world, local):
     if not args.no_arms:
         # ---- FP64 plain: same lattice, FP64 throughout ---------------------------
         lat64 = su2.Lattice(Ns, Nt, su2.F64)
-        tuned["fp64"] = lat64.autotune()
+        lat64.autotune()
+        tuned["fp64"] = shape_name(lat64)[1]
         sw64 = 100  # the paper's 100 sweeps per start, as in the FP32 arm
         pl64 = torch.zeros(sw64, dtype=torch.float64, device="cuda")
 
@@ -395,7 +413,8 @@ def gpu_arm(args, rank, world, local):
         # ---- FP32 batched ensemble -------------------------------------------------
         ens = inputs.batched_ensemble(64, 5)
         B = su2.Lattice([e["Ns"] for e in ens], [e["Nt"] for e in ens], su2.F32)
-        tuned["fp32_batched"] = B.autotune()
+        B.autotune()
+        tuned["fp32_batched"] = shape_name(B)[1]
         betas = [e["beta"] for e in ens]
         seeds = [e["seed"] + 1000003 * rank for e in ens]
         swb = 200
@@ -430,7 +449,8 @@ def gpu_arm(args, rank, world, local):
         cs_dev = torch.zeros(len(scan) * (rmax + 1), dtype=torch.float64, device="cuda")
         Vs_tot = sum(e["Ns"] ** 3 * e["Nt"] for e in full_scan)
 
-        tuned["fp32_temperature_scan"] = S.autotune()
+        S.autotune()
+        tuned["fp32_temperature_scan"] = shape_name(S)[1]
 
         def step_scan():
             S.batch_init(su2.HOT, ss)
@@ -456,7 +476,8 @@ def gpu_arm(args, rank, world, local):
         # ---- the smaller configurations of the paper's benchmark shape -------------
         def small_arm(name, Nsm, dtype, beta, seed, nsw=100, K=3):
             L = su2.Lattice(Nsm, Nsm, dtype)
-            tuned[name] = L.autotune()
+            L.autotune()
+            tuned[name] = shape_name(L)[1]
             pl = torch.zeros(nsw, dtype=torch.float64, device="cuda")
 
             def step():
@@ -480,7 +501,8 @@ def gpu_arm(args, rank, world, local):
 
         # ---- FP32 128^4 (16 GiB of links) -----------------------------------------
         big = su2.Lattice(128, 128, su2.F32)
-        tuned["fp32_128^4"] = big.autotune()
+        big.autotune()
+        tuned["fp32_128^4"] = shape_name(big)[1]
         sw_big = 10
         pl_big = torch.zeros(sw_big, dtype=torch.float64, device="cuda")
 
@@ -552,9 +574,8 @@ def gpu_arm(args, rank, world, local):
             "fp32": {"mean": m32, "err": e32}, "fp64": {"mean": m64, "err": e64},
             "diff_in_sigma": abs(m32 - m64) / float(np.hypot(e32, e64))}
 
-    from paper_1104_5432_gb300.csrc_info import launch_shapes
     return dict(t_main=t_main, value=value, clocks=clocks, roofline=roofline, e2e=e2e,
-                tuned={k: launch_shapes(k.startswith("fp64"))[v] for k, v in tuned.items()},
+                tuned=tuned,
                 arms=arms, launches=launches_per_step * args.steps, step_gbs=step_gbs,
                 phase_s=phase_s)
 
@@ -689,7 +710,8 @@ def profile_case(args):
     if args.profile_case == "scan":
         # the temperature scan's batch: 2 sweeps, then 3 measured sweeps
         scan = inputs.temperature_scan(21, 48, 4)
-        S = su2.Lattice([e["Ns"] for e in scan], [e["Nt"] for e in scan], su2.F32)
+        S = su2.Lattice([e["Ns"] for e in scan], [e["Nt"] for e in scan], su2.F32,
+                        layout=layout_arg(args, su2))
         S.set_launch_config(args.launch_shape or 0)
         sb, ss = [e["beta"] for e in scan], [e["seed"] for e in scan]
         S.batch_init(su2.HOT, ss)
@@ -700,13 +722,14 @@ def profile_case(args):
         return
     Ns, dt = {"f32_64": (64, su2.F32), "f32_128": (128, su2.F32), "f64_64": (64, su2.F64)}[
         args.profile_case]
-    lat = su2.Lattice(Ns, Ns, dt)
+    lat = su2.Lattice(Ns, Ns, dt, layout=None if dt == su2.F64 else layout_arg(args, su2))
     lat.set_launch_config(args.launch_shape or 0)
     lat.init(su2.HOT, WORKLOAD["init_seed"])
     pl = torch.zeros(3, dtype=torch.float64, device="cuda")
     lat.heatbath(WORKLOAD["beta"], 3, WORKLOAD["hb_seed"], plaq=pl)
     lat.sync()
     print(json.dumps({"profile_case": args.profile_case, "launch_shape": lat.launch_config(),
+                      "row": shape_name(lat)[0],
                       "plaquette": pl.cpu().tolist()}))
 
 

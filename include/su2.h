@@ -69,6 +69,16 @@ extern "C" {
 #define SU2_F32 0           /* FP32 links and update, FP64 reductions */
 #define SU2_F64 1           /* FP64 throughout */
 
+#define SU2_LAYOUT_PLAIN 0  /* FP32 float4 U[mu][parity][eo]; FP64 double2
+                               U[mu][parity][plane][eo], planes (a0,a1), (a2,a3) */
+#define SU2_LAYOUT_PAIRS 1  /* FP32 site pairs, every Nt a multiple of 4: the
+                               sites eo = q and q + V/4 of one parity (x,y,z at
+                               t and t + Nt/2) share a 32-byte record
+                               float4 U[mu][parity][q][2] =
+                               (a0, a0', a1, a1'), (a2, a2', a3, a3') */
+#define SU2_F32_PAIRS 2     /* su2_plaquette_static only: FP32 links in the
+                               site-pair layout */
+
 #define SU2_COLD 0          /* every link the identity */
 #define SU2_HOT 1           /* Haar-random links (Sec. 2.1 "random SU(2)") */
 
@@ -99,6 +109,19 @@ int su2_lattice_volume(const su2_lattice* lat, int l, uint64_t* V);
  * holds descriptors, reduction partials, the Polyakov field, the
  * plaquette ring and a 32 MiB staging area for host transfers. */
 int su2_memory_requirements(const su2_lattice* lat, size_t* link_bytes, size_t* work_bytes);
+
+/* Device layout of the links.  An SU2_F32 handle whose lattices all have
+ * Nt a multiple of 4 stores its links as site pairs (SU2_LAYOUT_PAIRS) by
+ * default: one thread of the heat bath then updates the two links of a
+ * record together with packed two-lane FP32 instructions (the sites t and
+ * t + Nt/2 of one parity never share a staple).  Every other handle uses
+ * SU2_LAYOUT_PLAIN.  Both layouts take the same bytes and give bit-identical
+ * links; results never depend on the layout.  su2_set_link_layout (before
+ * su2_bind_memory only; SU2_E_INVAL after, for SU2_LAYOUT_PAIRS on an FP64
+ * handle or on an Nt that is not a multiple of 4) overrides the choice and
+ * resets the launch shape to 0; su2_get_link_layout reads it. */
+int su2_set_link_layout(su2_lattice* lat, int layout);
+int su2_get_link_layout(const su2_lattice* lat, int* layout);
 
 /* Binds caller-owned device buffers of the CURRENT device (256-byte
  * aligned, at least the required sizes; SU2_E_NOMEM otherwise) and writes
@@ -289,6 +312,9 @@ const char* su2_last_error(void);
  *   library's link layout -- the link buffer of a single-lattice handle
  *   (FP32: float4 U[mu][parity][eo]; FP64: double2 U[mu][parity][plane][eo],
  *   plane 0 = (a0,a1), plane 1 = (a2,a3); eo = lex >> 1).
+ * dtype: SU2_F32 or SU2_F64 for those layouts, SU2_F32_PAIRS for FP32 links
+ *   in the site-pair layout (SU2_LAYOUT_PAIRS; Nt a multiple of 4): pass
+ *   SU2_F32_PAIRS for a handle whose su2_get_link_layout gives it.
  * Ns, Nt: even, >= 2, Ns^3 Nt <= SU2_STATIC_MAX_SITES (else SU2_E_INVAL).
  * out: host or device double; a host output makes the call synchronous.
  * stream: cudaStream_t (as void*), 0 = legacy default stream.

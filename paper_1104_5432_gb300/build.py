@@ -20,16 +20,18 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsu2gb300.so")
 SOURCES = ["heatbath.cu", "observables.cu", "links.cu", "api.cu", "plaquette_static.cu",
            "selftest.cu"]
-# heatbath_shapes.cu once per pair of launch shapes and precision (the
-# 14-entry table in csrc/su2_internal.h): (object name, defines, flags).
+# heatbath_shapes.cu once per pair of launch shapes and row of the 14-entry
+# table in csrc/su2_internal.h (FP32, FP64, FP32 site pairs): (object name,
+# defines, flags).
 # The FP32 phase kernels flush denormals to zero: none can occur on their
 # path (links, staple sums and uniforms are >= 2^-24 in magnitude or exactly
 # 0, the log series is evaluated in Horner form, alpha and 1/(2 alpha) stay
 # normal down to beta = 1e-9), and without denormal handling the division
 # and square-root sequences are shorter (2% at 64^4).
-SHAPE_UNITS = [(f"heatbath_shapes_{'f32' if row == 0 else 'f64'}_{k}",
-                (f"SU2_ROW={row}", f"SU2_FIRST={k}"), ("-ftz=true",) if row == 0 else ())
-               for row in (0, 1) for k in range(0, 14, 2)]
+ROW_NAMES = ("f32", "f64", "f32pairs")
+SHAPE_UNITS = [(f"heatbath_shapes_{ROW_NAMES[row]}_{k}",
+                (f"SU2_ROW={row}", f"SU2_FIRST={k}"), ("-ftz=true",) if row != 1 else ())
+               for row in (0, 1, 2) for k in range(0, 14, 2)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -77,6 +77,7 @@ struct Range {
 struct su2_lattice {
     int n = 0;
     int dtype = 0;
+    int row = 0;                    // shape-table row: FP32, FP64 or FP32 site pairs
     std::vector<int> Ns, Nt;
     std::vector<uint64_t> V, Vs, link_off, field_off;
     std::vector<uint32_t> site_start, spat_start;
@@ -193,6 +194,14 @@ bool is_device_ptr(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// links one block of launch shape k updates per phase (a site-pair shape's
+// rounds count pairs)
+uint64_t links_per_block(const su2_lattice* L, int k)
+{
+    const LaunchCfg& c = LAUNCH_CFG[L->row][k];
+    return (uint64_t)c.threads * (uint64_t)c.rounds * (L->row == ROW_F32_PAIRS ? 2u : 1u);
+}
+
 int layout(su2_lattice* L)
 {
     const int n = L->n;
@@ -217,8 +226,7 @@ int layout(su2_lattice* L)
         fo += (L->Vs[l] + 31) & ~uint64_t(31);
         for (int k = 0; k < NUM_LAUNCH_CFG; ++k) {
             // links per block: threads x rounds
-            const uint64_t nt = (uint64_t)LAUNCH_CFG[L->dtype][k].threads *
-                                (uint64_t)LAUNCH_CFG[L->dtype][k].rounds;
+            const uint64_t nt = links_per_block(L, k);
             L->phase_start[k][l + 1] = L->phase_start[k][l] + (uint32_t)((L->V[l] / 2 + nt - 1) / nt);
         }
         L->site_start[l + 1] = L->site_start[l] + blocks_of(L->V[l]);
@@ -229,7 +237,7 @@ int layout(su2_lattice* L)
     L->max_phase_blocks = 0;
     for (int k = 0; k < NUM_LAUNCH_CFG; ++k) {
         L->phase_blocks[k] = L->phase_start[k][n];
-        const uint32_t wpb = (uint32_t)LAUNCH_CFG[L->dtype][k].threads / 32;
+        const uint32_t wpb = (uint32_t)LAUNCH_CFG[L->row][k].threads / 32;
         L->max_phase_blocks = std::max(L->max_phase_blocks, L->phase_blocks[k] * wpb);
         L->cfg_chunks[k] = 1;
         for (int l = 0; l < n; ++l) {
@@ -294,6 +302,11 @@ int create(int n, const int* Ns, const int* Nt, int dtype, su2_lattice** out)
     su2_lattice* L = new su2_lattice;
     L->n = n;
     L->dtype = dtype;
+    // FP32 lattices are stored as site pairs (t, t + Nt/2) when every Nt is
+    // a multiple of 4 (the two sites then have the same parity)
+    bool pairs = dtype == SU2_F32;
+    for (int l = 0; l < n; ++l) pairs = pairs && Nt[l] % 4 == 0;
+    L->row = dtype == SU2_F64 ? ROW_F64 : (pairs ? ROW_F32_PAIRS : ROW_F32);
     L->Ns.assign(Ns, Ns + n);
     L->Nt.assign(Nt, Nt + n);
     layout(L);
@@ -302,12 +315,13 @@ int create(int n, const int* Ns, const int* Nt, int dtype, su2_lattice** out)
 }
 
 // y slabs for the large-lattice traversal: the smallest power of two
-// dividing Ns that keeps the t-neighbour window Nh (Ns/S) Ns sites x 7 link
-// loads within SLAB_WINDOW_BYTES (FP32 only; 1 = plain order)
+// dividing Ns that keeps the t-neighbour window Nh (Ns/S) Ns sites (records
+// of site pairs) x 7 link loads within SLAB_WINDOW_BYTES (FP32 only; 1 =
+// plain order)
 int slab_rule(const su2_lattice* L, int l)
 {
     if (L->dtype != SU2_F32) return 1;
-    const double link = 16.0;
+    const double link = L->row == ROW_F32_PAIRS ? 32.0 : 16.0;
     const double Ns = L->Ns[l];
     int S = 1;
     while ((L->Ns[l] % (2 * S)) == 0 &&
@@ -372,7 +386,7 @@ int record_sweep(su2_lattice* L, bool plaq, int rmax, cudaStream_t s)
     for (int mu = 0; mu < 4; ++mu) {
         if (branch && mu == 3) SU2_CUDA(cudaStreamWaitEvent(s, L->join_ev, 0));
         for (int p = 0; p < 2; ++p)
-            SU2_CUDA(launch_phase(L->cfg_ctx[L->cfg], L->dtype, L->cfg, mu, p, plaq, nullptr,
+            SU2_CUDA(launch_phase(L->cfg_ctx[L->cfg], L->row, L->cfg, mu, p, plaq, nullptr,
                                   L->hybrid, s));
     }
     SU2_CUDA(launch_sweep_end(L->cfg_ctx[L->cfg], plaq, s));
@@ -569,14 +583,15 @@ std::string tune_key(const su2_lattice* L, int dev)
     // the launch-shape table of this precision: a cached index names a
     // shape only in the table it was tuned with
     uint32_t th = 2166136261u;
-    for (const LaunchCfg& c : LAUNCH_CFG[L->dtype])
+    for (const LaunchCfg& c : LAUNCH_CFG[L->row])
         for (int v : {c.threads, c.min_blocks, (int)c.slab, c.rounds, (int)c.persistent}) {
             th ^= (uint32_t)v;
             th *= 16777619u;
         }
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|%s|n%d|V%llu|%016llx|t%08x", name.c_str(),
-             L->dtype ? "f64" : "f32", L->n, (unsigned long long)[&] {
+    static const char* const rows[NUM_ROWS] = {"f32", "f64", "f32pairs"};
+    snprintf(buf, sizeof buf, "%s|%s|n%d|V%llu|%016llx|t%08x", name.c_str(), rows[L->row], L->n,
+             (unsigned long long)[&] {
                  uint64_t t = 0;
                  for (uint64_t v : L->V) t += v;
                  return t;
@@ -633,15 +648,16 @@ int get_links_impl(su2_lattice* lat, int l, C* dst)
     if (!dst || l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index or buffer");
     DeviceGuard dg(lat->device);
     const uint32_t V = (uint32_t)lat->V[l];
+    const bool pw = lat->row == ROW_F32_PAIRS;  // whole lattice record by record
     if (is_device_ptr(dst)) {
         if ((uintptr_t)dst & 15) return fail(SU2_E_INVAL, "device buffer must be 16-byte aligned");
-        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, 0, V, dst, cd, lat->stream));
+        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, 0, V, dst, cd, lat->stream, pw));
         return SU2_OK;
     }
     if (void* hd = const_cast<void*>(mapped_host_ptr(dst))) {
         if ((uintptr_t)hd & 15) return fail(SU2_E_INVAL, "host buffer must be 16-byte aligned");
         // page-locked host memory: written directly by the conversion kernel
-        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, 0, V, hd, cd, lat->stream));
+        SU2_CUDA(launch_links_to_canonical(lat->ctx, lat->dtype, l, 0, V, hd, cd, lat->stream, pw));
         SU2_CUDA(cudaStreamSynchronize(lat->stream));
         return sync_status(lat);
     }
@@ -665,15 +681,16 @@ int set_links_impl(su2_lattice* lat, int l, const C* src)
     if (!src || l < 0 || l >= lat->n) return fail(SU2_E_INVAL, "bad lattice index or buffer");
     DeviceGuard dg(lat->device);
     const uint32_t V = (uint32_t)lat->V[l];
+    const bool pw = lat->row == ROW_F32_PAIRS;  // whole lattice record by record
     if (is_device_ptr(src)) {
         if ((uintptr_t)src & 15) return fail(SU2_E_INVAL, "device buffer must be 16-byte aligned");
-        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, 0, V, src, cd, lat->stream));
+        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, 0, V, src, cd, lat->stream, pw));
         return SU2_OK;
     }
     if (const void* hd = mapped_host_ptr(src)) {
         if ((uintptr_t)hd & 15) return fail(SU2_E_INVAL, "host buffer must be 16-byte aligned");
         // page-locked host memory: read directly by the conversion kernel
-        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, 0, V, hd, cd, lat->stream));
+        SU2_CUDA(launch_links_from_canonical(lat->ctx, lat->dtype, l, 0, V, hd, cd, lat->stream, pw));
         SU2_CUDA(cudaStreamSynchronize(lat->stream));
         return SU2_OK;
     }
@@ -773,6 +790,9 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
         D.Vh = (uint32_t)(lat->V[l] / 2);
         D.div_nh = make_fastdiv((uint32_t)D.Nh);
         D.div_ns = make_fastdiv((uint32_t)D.Ns);
+        D.paired = lat->row == ROW_F32_PAIRS ? 1 : 0;
+        D.Vq = (uint32_t)(lat->V[l] / 4);
+        D.div_nt2 = make_fastdiv((uint32_t)std::max(1, D.Nt / 2));
         set_slabs(D, slab_rule(lat, l));
         lat->ysplit[l] = D.ysplit;
         D.link_off = lat->link_off[l];
@@ -788,9 +808,9 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
     int sms = 1;
     SU2_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     for (int k = 0; k < NUM_LAUNCH_CFG; ++k) {
-        const LaunchCfg& cf = LAUNCH_CFG[lat->dtype][k];
+        const LaunchCfg& cf = LAUNCH_CFG[lat->row][k];
         if (!cf.persistent || lat->n != 1) continue;
-        const uint64_t per = (uint64_t)cf.threads * (uint64_t)cf.rounds;
+        const uint64_t per = links_per_block(lat, k);
         const uint32_t tiles = (uint32_t)((lat->V[0] / 2 + per - 1) / per);
         const uint32_t nb = std::min<uint32_t>(tiles, (uint32_t)(sms * cf.min_blocks));
         lat->phase_start[k][1] = nb;
@@ -823,7 +843,7 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
     c.chunk_count = reinterpret_cast<uint32_t*>(w + lat->off_tickets);
     c.trial_slots = reinterpret_cast<unsigned long long*>(w + lat->off_tslots);
     c.max_chunks = lat->cfg_chunks[0];
-    c.phase_wpb = (uint32_t)LAUNCH_CFG[lat->dtype][0].threads / 32;
+    c.phase_wpb = (uint32_t)LAUNCH_CFG[lat->row][0].threads / 32;
     c.status = reinterpret_cast<uint32_t*>(w + lat->off_status);
     c.n = lat->n;
     c.phase_blocks = lat->phase_blocks[0];
@@ -834,7 +854,7 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
         lat->cfg_ctx[k].phase_start = reinterpret_cast<const uint32_t*>(w + lat->off_pstart_cfg[k]);
         lat->cfg_ctx[k].phase_blocks = lat->phase_blocks[k];
         lat->cfg_ctx[k].max_chunks = lat->cfg_chunks[k];
-        lat->cfg_ctx[k].phase_wpb = (uint32_t)LAUNCH_CFG[lat->dtype][k].threads / 32;
+        lat->cfg_ctx[k].phase_wpb = (uint32_t)LAUNCH_CFG[lat->row][k].threads / 32;
     }
     // a launch shape tuned earlier for these shapes on this GPU, if cached
     lat->tune_key = tune_key(lat, dev);
@@ -844,6 +864,34 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
         if (cache_lookup(path, lat->tune_key, &cached) && cached >= 0 && cached < NUM_LAUNCH_CFG)
             lat->cfg = cached;
     }
+    return SU2_OK;
+}
+
+int su2_set_link_layout(su2_lattice* lat, int layout_code)
+{
+    if (int rc = check_handle(lat, false)) return rc;
+    if (lat->bound()) return fail(SU2_E_INVAL, "the link layout is fixed once memory is bound");
+    if (layout_code == SU2_LAYOUT_PLAIN) {
+        if (lat->dtype == SU2_F32) lat->row = ROW_F32;
+    } else if (layout_code == SU2_LAYOUT_PAIRS) {
+        if (lat->dtype != SU2_F32) return fail(SU2_E_INVAL, "site pairs are an FP32 layout");
+        for (int l = 0; l < lat->n; ++l)
+            if (lat->Nt[l] % 4)
+                return fail(SU2_E_INVAL, "lattice %d: site pairs need Nt a multiple of 4 (Nt=%d)",
+                            l, lat->Nt[l]);
+        lat->row = ROW_F32_PAIRS;
+    } else {
+        return fail(SU2_E_INVAL, "bad link layout %d", layout_code);
+    }
+    lat->cfg = 0;
+    return layout(lat);
+}
+
+int su2_get_link_layout(const su2_lattice* lat, int* layout_code)
+{
+    if (int rc = check_handle(lat, false)) return rc;
+    if (!layout_code) return fail(SU2_E_INVAL, "null output");
+    *layout_code = lat->row == ROW_F32_PAIRS ? SU2_LAYOUT_PAIRS : SU2_LAYOUT_PLAIN;
     return SU2_OK;
 }
 
@@ -904,7 +952,7 @@ int su2_heatbath_phase(su2_lattice* lat, double beta, int mu, int parity, uint64
         lat->phase_beta = beta;
         lat->phase_seed = seed;
     }
-    SU2_CUDA(launch_phase(lat->cfg_ctx[lat->cfg], lat->dtype, lat->cfg, mu, parity, false, trials,
+    SU2_CUDA(launch_phase(lat->cfg_ctx[lat->cfg], lat->row, lat->cfg, mu, parity, false, trials,
                           lat->hybrid, lat->stream));
     return SU2_OK;
 }
@@ -1059,7 +1107,7 @@ int su2_autotune(su2_lattice* lat, int* chosen)
     bool any_slab = false;
     for (int l = 0; l < lat->n; ++l) any_slab = any_slab || lat->ysplit[l] > 1;
     bool cand[NUM_LAUNCH_CFG];
-    for (int k = 0; k < NUM_LAUNCH_CFG; ++k) cand[k] = any_slab || !LAUNCH_CFG[lat->dtype][k].slab;
+    for (int k = 0; k < NUM_LAUNCH_CFG; ++k) cand[k] = any_slab || !LAUNCH_CFG[lat->row][k].slab;
     const int ncand = NUM_LAUNCH_CFG;
     for (int k = 0; k < ncand && rc == SU2_OK; ++k) {
         if (!cand[k]) continue;
@@ -1109,8 +1157,8 @@ int su2_get_launch_config(const su2_lattice* lat, int* cfg, int* threads, int* m
 {
     if (int rc = check_handle(lat, false)) return rc;
     if (cfg) *cfg = lat->cfg;
-    if (threads) *threads = LAUNCH_CFG[lat->dtype][lat->cfg].threads;
-    if (min_blocks) *min_blocks = LAUNCH_CFG[lat->dtype][lat->cfg].min_blocks;
+    if (threads) *threads = LAUNCH_CFG[lat->row][lat->cfg].threads;
+    if (min_blocks) *min_blocks = LAUNCH_CFG[lat->row][lat->cfg].min_blocks;
     return SU2_OK;
 }
 

@@ -71,6 +71,7 @@ __global__ void set_params_kernel(Ctx ctx, ParamChunk pc)
     LatDesc* D = ctx.desc + pc.first + j;
     D->beta = pc.beta[j];
     D->beta_f = (float)pc.beta[j];
+    D->half_inv_beta_f = (float)(0.5 / pc.beta[j]);
     D->half_inv_beta = 0.5 / pc.beta[j];  // inf at beta = 0, where the Haar draw applies
     D->seed = pc.seed[j];
     D->plaq_out = pc.plaq_out[j];
@@ -82,21 +83,24 @@ template <int ROW, int FIRST>
 cudaError_t launch_phase_pair(const Ctx& c, int cfg, int mu, int parity, bool plaq, int32_t* dbg,
                               bool hyb, cudaStream_t s);
 
-cudaError_t launch_phase(const Ctx& c, int dtype, int cfg, int mu, int parity, bool plaq,
+cudaError_t launch_phase(const Ctx& c, int row, int cfg, int mu, int parity, bool plaq,
                          int32_t* dbg_trials, bool hybrid, cudaStream_t s)
 {
     using Fn = cudaError_t (*)(const Ctx&, int, int, int, bool, int32_t*, bool, cudaStream_t);
-    static_assert(NUM_LAUNCH_CFG == 14, "one entry per pair of shapes below");
-    static const Fn pairs[2][NUM_LAUNCH_CFG / 2] = {
+    static_assert(NUM_LAUNCH_CFG == 14 && NUM_ROWS == 3, "one entry per pair of shapes below");
+    static const Fn pairs[NUM_ROWS][NUM_LAUNCH_CFG / 2] = {
         {launch_phase_pair<0, 0>, launch_phase_pair<0, 2>, launch_phase_pair<0, 4>,
          launch_phase_pair<0, 6>, launch_phase_pair<0, 8>, launch_phase_pair<0, 10>,
          launch_phase_pair<0, 12>},
         {launch_phase_pair<1, 0>, launch_phase_pair<1, 2>, launch_phase_pair<1, 4>,
          launch_phase_pair<1, 6>, launch_phase_pair<1, 8>, launch_phase_pair<1, 10>,
          launch_phase_pair<1, 12>},
+        {launch_phase_pair<2, 0>, launch_phase_pair<2, 2>, launch_phase_pair<2, 4>,
+         launch_phase_pair<2, 6>, launch_phase_pair<2, 8>, launch_phase_pair<2, 10>,
+         launch_phase_pair<2, 12>},
     };
-    if (dtype < 0 || dtype > 1 || cfg < 0 || cfg >= NUM_LAUNCH_CFG) return cudaErrorInvalidValue;
-    return pairs[dtype][cfg >> 1](c, cfg, mu, parity, plaq, dbg_trials, hybrid, s);
+    if (row < 0 || row >= NUM_ROWS || cfg < 0 || cfg >= NUM_LAUNCH_CFG) return cudaErrorInvalidValue;
+    return pairs[row][cfg >> 1](c, cfg, mu, parity, plaq, dbg_trials, hybrid, s);
 }
 
 cudaError_t launch_sweep_end(const Ctx& c, bool plaq, cudaStream_t s)

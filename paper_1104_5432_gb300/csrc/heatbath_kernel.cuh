@@ -40,20 +40,19 @@ template <> __device__ __forceinline__ double alpha_haar<double>() { return 1e-1
 template <typename T> __device__ __forceinline__ T beta_of(const LatDesc& D);
 template <> __device__ __forceinline__ float beta_of<float>(const LatDesc& D) { return D.beta_f; }
 template <> __device__ __forceinline__ double beta_of<double>(const LatDesc& D) { return D.beta; }
-// 1/(2 alpha) from rk = 1/k: FP64 multiplies by the precomputed 1/(2 beta)
-// (a division costs the FP64 pipe ~20 slots); FP32 keeps the short
-// division, which needs no extra live register in a kernel at its limit
+// 1/(2 alpha) from rk = 1/k times the lattice's precomputed 1/(2 beta) (no
+// division per update; 1/(2 beta) is rounded once per call in each precision)
 template <typename T>
 __device__ __forceinline__ T inv_two_alpha(const LatDesc& D, T rk, T beta);
 template <>
-__device__ __forceinline__ float inv_two_alpha<float>(const LatDesc&, float rk, float beta)
+__device__ __forceinline__ float inv_two_alpha<float>(const LatDesc& D, float rk, float)
 {
-    return 0.5f * rk / beta;
+    return mul_(rk, D.half_inv_beta_f);
 }
 template <>
 __device__ __forceinline__ double inv_two_alpha<double>(const LatDesc& D, double rk, double)
 {
-    return rk * D.half_inv_beta;
+    return mul_(rk, D.half_inv_beta);
 }
 template <typename T> __device__ __forceinline__ T creutz_of(const LatDesc& D);
 template <> __device__ __forceinline__ float creutz_of<float>(const LatDesc& D) { return D.creutz_below_f; }
@@ -104,16 +103,27 @@ __device__ __forceinline__ void staple_sum(const Links<T>& U, const EoSite& s, u
     }
 }
 
-// One Kennedy-Pendleton trial from the four words of a Philox block:
+// The Kennedy-Pendleton trial on four uniforms:
 // lambda^2 = -(ln r1 + cos^2(2 pi r2) ln r3) / (2 alpha), delta = 2 lambda^2,
-// accepted iff r4^2 <= 1 - lambda^2.
+// accepted iff r4^2 <= 1 - lambda^2 (*lhs <= *rhs, compared by the caller,
+// lane by lane for a pair).
+template <typename V>
+__device__ __forceinline__ void kp_eval(V r1, V r2, V r3, V r4, V inv2a, V* d, V* lhs, V* rhs)
+{
+    const V lam2 = mul_(neg_(fma_(Math<V>::cos2pi_sq(r2), Math<V>::ln_u01(r3),
+                                  Math<V>::ln_u01(r1))), inv2a);
+    *d = add_(lam2, lam2);
+    *lhs = mul_(r4, r4);
+    *rhs = add_(splat<V>(1.0f), neg_(lam2));
+}
+
+// One Kennedy-Pendleton trial from the four words of a Philox block.
 template <typename T>
 __device__ __forceinline__ bool kp_try(const U4& w, T inv2a, T* d)
 {
-    const T r1 = u01<T>(w.x), r2 = u01<T>(w.y), r3 = u01<T>(w.z), r4 = u01<T>(w.w);
-    const T lam2 = -(Math<T>::ln_u01(r1) + Math<T>::cos2pi_sq(r2) * Math<T>::ln_u01(r3)) * inv2a;
-    *d = T(2) * lam2;
-    return r4 * r4 <= T(1) - lam2;
+    T lhs, rhs;
+    kp_eval(u01<T>(w.x), u01<T>(w.y), u01<T>(w.z), u01<T>(w.w), inv2a, d, &lhs, &rhs);
+    return lhs <= rhs;
 }
 
 // One trial of Creutz's draw (small alpha): a0 from exp(alpha a0) by
@@ -124,23 +134,38 @@ template <typename T>
 __device__ __forceinline__ bool creutz_try(const U4& w, T qc, T inv2a, T* d)
 {
     const T r1 = u01<T>(w.x), r4 = u01<T>(w.w);
-    *d = -Math<T>::log1p(-r1 * qc) * (T(2) * inv2a);
-    return r4 * r4 <= *d * (T(2) - *d);
+    *d = mul_(neg_(Math<T>::log1p(mul_(neg_(r1), qc))), add_(inv2a, inv2a));
+    return mul_(r4, r4) <= mul_(*d, add_(T(2), neg_(*d)));
+}
+
+template <typename T>
+__device__ __forceinline__ T creutz_qc(T alpha)
+{
+    return neg_(Math<T>::expm1(mul_(T(-2), alpha)));
 }
 
 // The accepted draw X = (1 - delta, sqrt(delta (2 - delta)) n) with the
-// direction n from the spare bits kd1, kd2 of the first trial block, and
-// the new link U = X A^dagger / |A|, renormalised.
+// direction n from the uniforms u1 (cos theta = 2 u1 - 1) and u2
+// (phi = 2 pi u2), and the new link U = X A^dagger / |A|, renormalised.
+template <typename V>
+__device__ __forceinline__ Quat<V> new_link_u(V delta, V u1, V u2, const Quat<V>& A)
+{
+    const V one = splat<V>(1.0f);
+    const V cth = fma_(splat<V>(2.0f), u1, splat<V>(-1.0f));
+    const V sth = Math<V>::sqrt_pos(mul_(add_(one, neg_(cth)), add_(one, cth)));
+    V sph, cph;
+    Math<V>::sincos2pi(u2, &sph, &cph);
+    const V vl = Math<V>::sqrt_pos(mul_(delta, add_(splat<V>(2.0f), neg_(delta))));
+    const V vs = mul_(vl, sth);
+    const Quat<V> X = {add_(one, neg_(delta)), mul_(vs, cph), mul_(vs, sph), mul_(vl, cth)};
+    return qnormalise(qmul_nd(X, A));
+}
+
+// the direction from the spare bits kd1, kd2 of the first trial block
 template <typename T>
 __device__ __forceinline__ Quat<T> new_link(T delta, uint32_t kd1, uint32_t kd2, const Quat<T>& A)
 {
-    const T cth = T(2) * u18<T>(kd1) - T(1);
-    const T sth = Math<T>::sqrt_pos((T(1) - cth) * (T(1) + cth));
-    T sph, cph;
-    Math<T>::sincos2pi(u18<T>(kd2), &sph, &cph);
-    const T vl = Math<T>::sqrt_pos(delta * (T(2) - delta));
-    const Quat<T> X = {T(1) - delta, vl * sth * cph, vl * sth * sph, vl * cth};
-    return qnormalise(qmul_nd(X, A));
+    return new_link_u(delta, u18<T>(kd1), u18<T>(kd2), A);
 }
 
 // the spare low 9 bits of the first trial's four words: two 18-bit uniforms
@@ -202,7 +227,7 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
         const T k2 = qnorm2(A);
         const T rk = Math<T>::rsqrt(k2);
         const T beta = beta_of<T>(D);
-        const T alpha = beta * k2 * rk;
+        const T alpha = mul_(mul_(beta, k2), rk);
         const uint64_t sw = D.sweep;
         const Stream st{(uint32_t)D.seed, (uint32_t)(D.seed >> 32), s.lex() * 4u + MU,
                         (uint32_t)sw, (uint32_t)(sw >> 32)};
@@ -221,7 +246,7 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             const U4 w = st.draw(TAG_TRIAL, 0u);
             const uint32_t kd1 = spare_bits_1(w), kd2 = spare_bits_2(w);
             if (HYB && alpha < creutz_of<T>(D)) {
-                const T qc = -Math<T>::expm1(T(-2) * alpha);
+                const T qc = creutz_qc(alpha);
                 for (int t = 0; t < KP_CAP; ++t) {
                     if (creutz_try(t == 0 ? w : st.draw(TAG_TRIAL, (uint32_t)t), qc, inv2a, &delta)) {
                         tr = t + 1;
@@ -313,7 +338,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     // a final link: store, plaquette, trial count
     auto put = [&](uint32_t i, uint32_t key, const Quat<T>& un, const Quat<T>& P, int32_t tr) {
         U.store(MU, p, i, un);
-        if (PLAQ) plaq += qretr(un, P);
+        if (PLAQ) plaq = add_(plaq, qretr(un, P));
         ntrial += (uint32_t)tr;
         if (DBG) dbg[key >> 2] = tr;
     };
@@ -367,7 +392,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
                 // cap hit: the link keeps its value
                 ncap += 1;
                 ntrial += (uint32_t)KP_CAP;
-                if (PLAQ) plaq += qretr(U.load_rw(MU, p, i), P);
+                if (PLAQ) plaq = add_(plaq, qretr(U.load_rw(MU, p, i), P));
                 if (DBG) dbg[key >> 2] = -1;
             } else {
                 pend = true;
@@ -390,7 +415,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
                 staple_sum<T, MU, PLAQ>(U, s, i, p, A, P);
                 const T k2 = qnorm2(A);
                 const T rk = Math<T>::rsqrt(k2);
-                const T alpha = beta * k2 * rk;
+                const T alpha = mul_(mul_(beta, k2), rk);
                 key = s.lex() * 4u + MU;
                 const Stream st{k0, k1, key, slo, shi};
                 if (!(alpha >= alpha_haar<T>())) {
@@ -403,7 +428,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
                     T delta;
                     bool ok;
                     if (HYB && alpha < creutz_of<T>(D)) {
-                        qc = -Math<T>::expm1(T(-2) * alpha);
+                        qc = creutz_qc(alpha);
                         ok = creutz_try(w, qc, inv2a, &delta);
                     } else {
                         ok = kp_try(w, inv2a, &delta);
@@ -425,11 +450,253 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     warp_totals<T, MU, PLAQ, NT>(ctx, l, blk0, Vh, plaq, ntrial, ncap);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 site pairs: two links per thread and round, packed arithmetic
+// ---------------------------------------------------------------------------
+// On a lattice stored as site pairs (t, t + Nt/2), one thread updates both
+// links of a record at once: every load brings the two links' components
+// side by side, and the staple products, the Kennedy-Pendleton arithmetic
+// and the new links run as two-lane FFMA2/FMUL2/FADD2 instructions, with
+// the hardware transcendentals and the Philox draws per lane.  Every lane
+// performs exactly the scalar kernels' sequence of roundings, so the links
+// are bit-identical to theirs.  A lane whose first trial is rejected joins
+// the warp's retry queue as a single link; so does a lane of a pair whose
+// other lane was rejected.
+
+// Staple sums of the two links of pair q.  The lattice of pairs has t
+// extent Nt/2; a t hop across its boundary lands in the other half of the
+// lattice, i.e. in the OTHER lane of the neighbouring record, so for the
+// pairs at t = Nt/2 - 1 (plus hop, tp) and t = 0 (minus hop, tm) those
+// loads have their lanes exchanged.  EDGE selects that variant at compile
+// time (a warp-uniform branch picks it): the other pairs pay nothing.
+template <int MU, bool PLAQ, bool EDGE>
+__device__ __forceinline__ void staple_sum_pair(const PairLinks& U, const EoSite& s, uint32_t i,
+                                                int p, bool tp, bool tm, Quat<float2>& A,
+                                                Quat<float2>& P)
+{
+    const int q = p ^ 1;
+    int hp[4], hm[4];
+    s.hops(hp, hm);
+    const uint32_t e_pmu = i + hp[MU];
+    const float2 z = splat<float2>(0.0f);
+    A = {z, z, z, z};
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == MU) continue;
+        const uint32_t e_pnu = i + hp[nu];
+        const uint32_t e_mnu = i + hm[nu];
+        const uint32_t e_pmu_mnu = i + hp[MU] + hm[nu];
+        Quat<float2> a = U.load2(nu, q, e_pmu);      // U_nu(x+mu)
+        Quat<float2> b = U.load2(MU, q, e_pnu);      // U_mu(x+nu)
+        const Quat<float2> c = U.load2(nu, p, i);    // U_nu(x)
+        Quat<float2> d = U.load2(nu, p, e_pmu_mnu);  // U_nu(x+mu-nu)
+        Quat<float2> e = U.load2(MU, q, e_mnu);      // U_mu(x-nu)
+        Quat<float2> f = U.load2(nu, q, e_mnu);      // U_nu(x-nu)
+        if (EDGE) {
+            const bool up_mu = MU == 3 && tp;  // x + mu crossed t = Nt/2
+            const bool up_nu = nu == 3 && tp;  // x + nu crossed t = Nt/2
+            const bool dn_nu = nu == 3 && tm;  // x - nu crossed t = 0
+            if (up_mu) a = lanes_swapped(a);
+            if (up_nu) b = lanes_swapped(b);
+            if (up_mu || dn_nu) d = lanes_swapped(d);
+            if (dn_nu) {
+                e = lanes_swapped(e);
+                f = lanes_swapped(f);
+            }
+        }
+        const Quat<float2> up = qmul_nd(qmul_nd(a, b), c);
+        const Quat<float2> lo = qmul(qmul_dd(d, e), f);
+        A = qadd(A, qadd(up, lo));
+        if (PLAQ && nu == MU - 1) P = A;
+    }
+}
+
+template <int MU, bool PLAQ, bool DBG, int NT, int MINB, bool SLAB, bool HYB, int R, bool PERSIST>
+__global__ void __launch_bounds__(NT, MINB)
+hb_pair_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
+{
+    using Queue = RetryQueue<float, PLAQ, HYB>;
+    __shared__ Queue sq[NT / 32];
+
+    const int l = lattice_of_block(ctx.phase_start, ctx.n, blockIdx.x);
+    const LatDesc& D = ctx.desc[l];
+    const uint32_t Vh = D.Vh, Vq = D.Vq;
+    const uint32_t blk0 = __ldg(ctx.phase_start + l);
+    // tiles of NT R pairs, as the queued kernel's tiles of links
+    const uint32_t nb = PERSIST ? __ldg(ctx.phase_start + l + 1) - blk0 : 0u;
+    const uint32_t ntiles = PERSIST ? (Vq + NT * R - 1) / (NT * R) : 0u;
+    uint32_t tile = blockIdx.x - blk0;
+    const PairLinks U(ctx.links, D, ctx.status);
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    Queue& Q = sq[threadIdx.x >> 5];
+    const float beta = D.beta_f, hib = D.half_inv_beta_f;
+    const uint32_t nt2 = (uint32_t)D.Nt >> 1;
+    const uint32_t lex_half = D.V >> 1;  // lex of lane 1 = lex of lane 0 + V/2
+    const uint64_t sw = D.sweep;
+    const uint32_t k0 = (uint32_t)D.seed, k1 = (uint32_t)(D.seed >> 32);
+    const uint32_t slo = (uint32_t)sw, shi = (uint32_t)(sw >> 32);
+
+    float plaq = 0.0f;                          // single links (queue, lone lanes)
+    float2 plaq2 = splat<float2>(0.0f);         // pairs, lane by lane
+    uint32_t ntrial = 0, ncap = 0;
+    int cnt = 0;  // queued links (warp-uniform)
+
+    auto put = [&](uint32_t i, uint32_t key, const Quat<float>& un, const Quat<float>& P, int32_t tr) {
+        U.store(MU, p, i, un);
+        if (PLAQ) plaq = add_(plaq, qretr(un, P));
+        ntrial += (uint32_t)tr;
+        if (DBG) dbg[key >> 2] = tr;
+    };
+    auto push = [&](bool pend, const Quat<float>& A, const Quat<float>& P, float inv2a, float qc,
+                    uint32_t key, uint32_t tk, uint32_t kd2, uint32_t i) {
+        const uint32_t m = __ballot_sync(0xffffffffu, pend);
+        if (pend) {
+            const int e = cnt + __popc(m & below);
+            Q.a[0][e] = A.a0; Q.a[1][e] = A.a1; Q.a[2][e] = A.a2; Q.a[3][e] = A.a3;
+            if (PLAQ) { Q.pl[0][e] = P.a0; Q.pl[1][e] = P.a1; Q.pl[2][e] = P.a2; Q.pl[3][e] = P.a3; }
+            Q.inv2a[e] = inv2a;
+            if (HYB) Q.qc[e] = qc;
+            Q.key[e] = key;
+            Q.tk[e] = tk;
+            Q.kd2[e] = kd2;
+            Q.site[e] = i;
+        }
+        cnt += __popc(m);
+        __syncwarp();
+    };
+    // one trial for each of the last n queued links, one link per lane
+    auto retry = [&](int n) {
+        const bool have = lane < n;
+        Quat<float> A = {0.f, 0.f, 0.f, 0.f}, P = A;
+        float inv2a = 0.f, qc = 0.f;
+        uint32_t key = 0, tk = 0, kd2 = 0, i = 0;
+        if (have) {
+            const int e = cnt - n + lane;
+            A = {Q.a[0][e], Q.a[1][e], Q.a[2][e], Q.a[3][e]};
+            if (PLAQ) P = {Q.pl[0][e], Q.pl[1][e], Q.pl[2][e], Q.pl[3][e]};
+            inv2a = Q.inv2a[e];
+            if (HYB) qc = Q.qc[e];
+            key = Q.key[e];
+            tk = Q.tk[e];
+            kd2 = Q.kd2[e];
+            i = Q.site[e];
+        }
+        __syncwarp();
+        cnt -= n;
+        bool pend = false;
+        if (have) {
+            const uint32_t t = tk & 0x1FFFu, kd1 = tk >> 13;
+            const Stream st{k0, k1, key, slo, shi};
+            const U4 w = st.draw(TAG_TRIAL, t);
+            float delta;
+            const bool ok = (HYB && qc > 0.f) ? creutz_try(w, qc, inv2a, &delta)
+                                              : kp_try(w, inv2a, &delta);
+            if (ok) {
+                put(i, key, new_link(delta, kd1, kd2, A), P, (int32_t)t + 1);
+            } else if (t + 1 >= (uint32_t)KP_CAP) {
+                // cap hit: the link keeps its value
+                ncap += 1;
+                ntrial += (uint32_t)KP_CAP;
+                if (PLAQ) plaq = add_(plaq, qretr(U.load_rw(MU, p, i), P));
+                if (DBG) dbg[key >> 2] = -1;
+            } else {
+                pend = true;
+                tk = (t + 1) | (kd1 << 13);
+            }
+        }
+        push(pend, A, P, inv2a, qc, key, tk, kd2, i);
+    };
+
+    do {
+        const uint32_t j0 = tile * (NT * R) + threadIdx.x;
+        for (int r = 0; r < R; ++r) {
+            const uint32_t j = j0 + (uint32_t)r * NT;
+            bool pend0 = false, pend1 = false;
+            const float2 z = splat<float2>(0.0f);
+            Quat<float2> A = {z, z, z, z}, P = A;
+            float2 inv2a = z, qc = z;
+            uint32_t key0 = 0, key1 = 0, tk0 = 0, tk1 = 0, kd20 = 0, kd21 = 0, i = j;
+            if (j < Vq) {
+                EoSite s = SLAB ? EoSite::from_slab_t(D, j, p, &i, nt2, D.div_nt2)
+                                : EoSite(D, j, p);
+                s.Nt = (int)nt2;  // hops wrap on the lattice of pairs
+                const bool tp = s.c[3] == (int)nt2 - 1, tm = s.c[3] == 0;
+                if (tp || tm) staple_sum_pair<MU, PLAQ, true>(U, s, i, p, tp, tm, A, P);
+                else staple_sum_pair<MU, PLAQ, false>(U, s, i, p, false, false, A, P);
+                const float2 k2 = qnorm2(A);
+                const float2 rk = Math<float2>::rsqrt(k2);
+                const float2 alpha = mul_(mul_(splat<float2>(beta), k2), rk);
+                key0 = s.lex() * 4u + MU;
+                key1 = (s.lex() + lex_half) * 4u + MU;
+                const Stream st0{k0, k1, key0, slo, shi}, st1{k0, k1, key1, slo, shi};
+                const bool haar0 = !(alpha.x >= alpha_haar<float>());
+                const bool haar1 = !(alpha.y >= alpha_haar<float>());
+                inv2a = mul_(rk, splat<float2>(hib));
+                const U4 w0 = st0.draw(TAG_TRIAL, 0u), w1 = st1.draw(TAG_TRIAL, 0u);
+                float2 delta, lhs, rhs;
+                kp_eval(u01f2(w0.x, w1.x), u01f2(w0.y, w1.y), u01f2(w0.z, w1.z),
+                        u01f2(w0.w, w1.w), inv2a, &delta, &lhs, &rhs);
+                bool ok0 = lhs.x <= rhs.x, ok1 = lhs.y <= rhs.y;
+                if (HYB) {
+                    const float cb = D.creutz_below_f;
+                    if (alpha.x < cb) {
+                        qc.x = creutz_qc(alpha.x);
+                        ok0 = creutz_try(w0, qc.x, inv2a.x, &delta.x);
+                    }
+                    if (alpha.y < cb) {
+                        qc.y = creutz_qc(alpha.y);
+                        ok1 = creutz_try(w1, qc.y, inv2a.y, &delta.y);
+                    }
+                }
+                ok0 = ok0 && !haar0;
+                ok1 = ok1 && !haar1;
+                const uint32_t kd10 = spare_bits_1(w0), kd11 = spare_bits_1(w1);
+                kd20 = spare_bits_2(w0);
+                kd21 = spare_bits_2(w1);
+                // both lanes' new links at once; a rejected lane's value is
+                // never stored
+                const Quat<float2> un =
+                    new_link_u(delta, u18f2(kd10, kd11), u18f2(kd20, kd21), A);
+                if (ok0 && ok1) {
+                    U.store2(MU, p, i, un);
+                    if (PLAQ) plaq2 = add_(plaq2, qretr(un, P));
+                    ntrial += 2;
+                    if (DBG) {
+                        dbg[key0 >> 2] = 1;
+                        dbg[key1 >> 2] = 1;
+                    }
+                } else {
+                    if (ok0) put(i, key0, lane0(un), lane0(P), 1);
+                    if (ok1) put(i + Vq, key1, lane1(un), lane1(P), 1);
+                    if (haar0) put(i, key0, haar_from<float>(st0.draw(TAG_DIRECTION, 0)), lane0(P), 0);
+                    if (haar1)
+                        put(i + Vq, key1, haar_from<float>(st1.draw(TAG_DIRECTION, 0)), lane1(P), 0);
+                    pend0 = !ok0 && !haar0;
+                    pend1 = !ok1 && !haar1;
+                    tk0 = 1u | (kd10 << 13);
+                    tk1 = 1u | (kd11 << 13);
+                }
+            }
+            push(pend0, lane0(A), lane0(P), inv2a.x, qc.x, key0, tk0, kd20, i);
+            while (cnt >= 32) retry(32);
+            push(pend1, lane1(A), lane1(P), inv2a.y, qc.y, key1, tk1, kd21, i + Vq);
+            while (cnt >= 32) retry(32);
+        }
+        tile += nb;
+    } while (PERSIST && tile < ntiles);
+    while (cnt > 0) retry(cnt < 32 ? cnt : 32);
+    if (PLAQ) plaq = add_(plaq, add_(plaq2.x, plaq2.y));
+    warp_totals<float, MU, PLAQ, NT>(ctx, l, blk0, Vh, plaq, ntrial, ncap);
+}
+
 // One launch shape (NT threads per block, at least MINB blocks per SM, R
-// links per thread, persistent or not) of the phase kernel; the grid covers
-// ctx.phase_blocks blocks of NT R links (fewer, each walking several tiles,
-// for a persistent shape on a single lattice).
-template <typename T, int NT, int MINB, bool SLAB, int R = 1, bool PERSIST = false>
+// links -- or with PAIRS, R site pairs -- per thread, persistent or not) of
+// the phase kernel; the grid covers ctx.phase_blocks blocks of NT R links
+// or pairs (fewer, each walking several tiles, for a persistent shape on a
+// single lattice).
+template <typename T, int NT, int MINB, bool SLAB, int R = 1, bool PERSIST = false,
+          bool PAIRS = false>
 cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int32_t* dbg,
                                bool hyb, cudaStream_t s)
 {
@@ -437,7 +704,10 @@ cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int3
     const bool pl = plaq && parity == 1 && mu >= 1;
     const dim3 grid(c.phase_blocks), block(NT);
 #define SU2_K(MUV, PL, DB, H)                                                                   \
-    if constexpr (R == 1 && !PERSIST)                                                           \
+    if constexpr (PAIRS)                                                                        \
+        hb_pair_kernel<MUV, PL, DB, NT, MINB, SLAB, H, R, PERSIST><<<grid, block, 0, s>>>(      \
+            c, parity, dbg);                                                                    \
+    else if constexpr (R == 1 && !PERSIST)                                                      \
         hb_phase_kernel<T, MUV, PL, DB, NT, MINB, SLAB, H><<<grid, block, 0, s>>>(c, parity, dbg); \
     else                                                                                        \
         hb_phase_queue_kernel<T, MUV, PL, DB, NT, MINB, SLAB, H, R, PERSIST><<<grid, block, 0, s>>>( \

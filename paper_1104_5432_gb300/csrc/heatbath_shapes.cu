@@ -1,13 +1,14 @@
 // heatbath_shapes.cu -- phase-kernel instantiations for two launch shapes
-// of one precision.  The build compiles this file once per pair, with
-// SU2_ROW = 0 (FP32) or 1 (FP64) and SU2_FIRST the first shape index of
-// the pair, so that the shapes compile in parallel.
+// of one row of the shape table.  The build compiles this file once per
+// pair, with SU2_ROW = 0 (FP32), 1 (FP64) or 2 (FP32 site pairs) and
+// SU2_FIRST the first shape index of the pair, so that the shapes compile
+// in parallel.
 #include <type_traits>
 
 #include "heatbath_kernel.cuh"
 
 #if !defined(SU2_ROW) || !defined(SU2_FIRST)
-#error "compile with -DSU2_ROW=<0|1> -DSU2_FIRST=<even shape index>"
+#error "compile with -DSU2_ROW=<0|1|2> -DSU2_FIRST=<even shape index>"
 #endif
 
 namespace su2 {
@@ -16,15 +17,16 @@ template <int ROW, int FIRST>
 cudaError_t launch_phase_pair(const Ctx& c, int cfg, int mu, int parity, bool plaq, int32_t* dbg,
                               bool hyb, cudaStream_t s)
 {
-    using T = typename std::conditional<ROW == 0, float, double>::type;
+    using T = typename std::conditional<ROW == ROW_F64, double, float>::type;
+    constexpr bool PAIRS = ROW == ROW_F32_PAIRS;
     constexpr LaunchCfg A = LAUNCH_CFG[ROW][FIRST];
     constexpr LaunchCfg B = LAUNCH_CFG[ROW][FIRST + 1];
     if (cfg == FIRST)
-        return launch_phase_shape<T, A.threads, A.min_blocks, A.slab, A.rounds, A.persistent>(
-            c, mu, parity, plaq, dbg, hyb, s);
+        return launch_phase_shape<T, A.threads, A.min_blocks, A.slab, A.rounds, A.persistent,
+                                  PAIRS>(c, mu, parity, plaq, dbg, hyb, s);
     if (cfg == FIRST + 1)
-        return launch_phase_shape<T, B.threads, B.min_blocks, B.slab, B.rounds, B.persistent>(
-            c, mu, parity, plaq, dbg, hyb, s);
+        return launch_phase_shape<T, B.threads, B.min_blocks, B.slab, B.rounds, B.persistent,
+                                  PAIRS>(c, mu, parity, plaq, dbg, hyb, s);
     return cudaErrorInvalidValue;
 }
 

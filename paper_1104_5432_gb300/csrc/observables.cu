@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(TPB) plaquette_kernel(Ctx ctx)
     const uint32_t lex = (blockIdx.x - __ldg(ctx.site_start + l)) * TPB + threadIdx.x;
     T acc = T(0);
     if (lex < D.V) {
-        const Links<T> U(ctx.links, D, ctx.status);
+        const AnyLinks<T> U(ctx.links, D, ctx.status);
         int p;
         const EoSite s = EoSite::from_lex(D, lex, &p);
         const uint32_t eo = lex >> 1;
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(TPB) polyakov_kernel(Ctx ctx)
     const uint32_t sidx = (blockIdx.x - __ldg(ctx.spat_start + l)) * TPB + threadIdx.x;
     T L = T(0);
     if (sidx < (uint32_t)D.Vs) {
-        const Links<T> U(ctx.links, D, ctx.status);
+        const AnyLinks<T> U(ctx.links, D, ctx.status);
         const uint32_t r = fdiv(sidx, D.div_ns);
         const uint32_t x = sidx - r * (uint32_t)D.Ns;
         const uint32_t z = fdiv(r, D.div_ns);

@@ -45,7 +45,7 @@ plaquette_static_kernel(void* links, LatDesc D, double* __restrict__ partial)
     const uint32_t lex = blockIdx.x * TPB + threadIdx.x;
     T acc = T(0);
     if (lex < D.V) {
-        const Links<T> U(links, D);
+        const AnyLinks<T> U(links, D);
         int p;
         const EoSite s = EoSite::from_lex(D, lex, &p);
         const uint32_t eo = lex >> 1;
@@ -93,7 +93,8 @@ extern "C" int su2_plaquette_static(const void* links, int Ns, int Nt, int dtype
 {
     using namespace su2;
     if (!links || !out) return fail_static(SU2_E_INVAL, "null links or output");
-    if (dtype != SU2_F32 && dtype != SU2_F64) return fail_static(SU2_E_INVAL, "bad dtype");
+    if (dtype != SU2_F32 && dtype != SU2_F64 && dtype != SU2_F32_PAIRS)
+        return fail_static(SU2_E_INVAL, "bad dtype");
     if (Ns < 2 || Nt < 2 || (Ns & 1) || (Nt & 1))
         return fail_static(SU2_E_INVAL, "Ns and Nt must be even and >= 2");
     // bound each extent before multiplying, so no product can wrap:
@@ -105,6 +106,8 @@ extern "C" int su2_plaquette_static(const void* links, int Ns, int Nt, int dtype
     if (V > (uint64_t)SU2_STATIC_MAX_SITES)
         return fail_static(SU2_E_INVAL,
                            "lattice larger than the static scratch allows (V > 16777216)");
+    if (dtype == SU2_F32_PAIRS && Nt % 4)
+        return fail_static(SU2_E_INVAL, "the site-pair layout needs Nt a multiple of 4");
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -140,12 +143,14 @@ extern "C" int su2_plaquette_static(const void* links, int Ns, int Nt, int dtype
     D.div_nh = make_fastdiv((uint32_t)D.Nh);
     D.div_ns = make_fastdiv((uint32_t)Ns);
     D.link_off = 0;
+    D.paired = dtype == SU2_F32_PAIRS ? 1 : 0;
+    D.Vq = (uint32_t)(V / 4);
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint32_t nblk = (uint32_t)((V + TPB - 1) / TPB);
     void* lk = const_cast<void*>(links);
-    if (dtype == SU2_F32) plaquette_static_kernel<float><<<nblk, TPB, 0, s>>>(lk, D, scratch);
-    else plaquette_static_kernel<double><<<nblk, TPB, 0, s>>>(lk, D, scratch);
+    if (dtype == SU2_F64) plaquette_static_kernel<double><<<nblk, TPB, 0, s>>>(lk, D, scratch);
+    else plaquette_static_kernel<float><<<nblk, TPB, 0, s>>>(lk, D, scratch);
     double* result = scratch + STATIC_PARTIALS;
     plaquette_static_finalize<<<1, TPB, 0, s>>>(scratch, nblk, 1.0 / (6.0 * (double)V),
                                                 dev_out ? out : result);

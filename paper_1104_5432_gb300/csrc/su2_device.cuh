@@ -21,7 +21,33 @@
 namespace su2 {
 
 // --------------------------------------------------------------------------
-// quaternions
+// arithmetic with every rounding written out
+// --------------------------------------------------------------------------
+// Each multiply, add and fused multiply-add of the update is an explicit
+// round-to-nearest intrinsic, so the compiler never contracts or
+// re-associates them.  The same sequence then runs on one value (float,
+// double) or on two FP32 lanes at once (float2: Blackwell's packed
+// FFMA2/FMUL2/FADD2), and the two give identical bits in every lane.
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float2 fma_(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float2 mul_(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float2 add_(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float neg_(float a) { return -a; }
+__device__ __forceinline__ double neg_(double a) { return -a; }
+__device__ __forceinline__ float2 neg_(float2 a) { return make_float2(-a.x, -a.y); }
+// a constant in every lane
+template <typename V> __device__ __forceinline__ V splat(float c);
+template <> __device__ __forceinline__ float splat<float>(float c) { return c; }
+template <> __device__ __forceinline__ double splat<double>(float c) { return (double)c; }
+template <> __device__ __forceinline__ float2 splat<float2>(float c) { return make_float2(c, c); }
+
+// --------------------------------------------------------------------------
+// quaternions (V = float, double, or float2 for two links at once)
 // --------------------------------------------------------------------------
 template <typename T>
 struct Quat {
@@ -29,64 +55,92 @@ struct Quat {
 };
 
 template <typename T>
-__host__ __device__ __forceinline__ Quat<T> qadd(const Quat<T>& p, const Quat<T>& q)
+__device__ __forceinline__ Quat<T> qadd(const Quat<T>& p, const Quat<T>& q)
 {
-    return {p.a0 + q.a0, p.a1 + q.a1, p.a2 + q.a2, p.a3 + q.a3};
+    return {add_(p.a0, q.a0), add_(p.a1, q.a1), add_(p.a2, q.a2), add_(p.a3, q.a3)};
 }
 
 // p q  for U = a0 + i a.sigma:  (p0 q0 - p.q,  p0 q + q0 p - p x q)
 template <typename T>
-__host__ __device__ __forceinline__ Quat<T> qmul(const Quat<T>& p, const Quat<T>& q)
+__device__ __forceinline__ Quat<T> qmul(const Quat<T>& p, const Quat<T>& q)
 {
     Quat<T> r;
-    r.a0 = p.a0 * q.a0 - p.a1 * q.a1 - p.a2 * q.a2 - p.a3 * q.a3;
-    r.a1 = p.a0 * q.a1 + q.a0 * p.a1 - (p.a2 * q.a3 - p.a3 * q.a2);
-    r.a2 = p.a0 * q.a2 + q.a0 * p.a2 - (p.a3 * q.a1 - p.a1 * q.a3);
-    r.a3 = p.a0 * q.a3 + q.a0 * p.a3 - (p.a1 * q.a2 - p.a2 * q.a1);
+    r.a0 = fma_(neg_(p.a3), q.a3, fma_(neg_(p.a2), q.a2, fma_(neg_(p.a1), q.a1, mul_(p.a0, q.a0))));
+    r.a1 = fma_(p.a3, q.a2, fma_(neg_(p.a2), q.a3, fma_(q.a0, p.a1, mul_(p.a0, q.a1))));
+    r.a2 = fma_(p.a1, q.a3, fma_(neg_(p.a3), q.a1, fma_(q.a0, p.a2, mul_(p.a0, q.a2))));
+    r.a3 = fma_(p.a2, q.a1, fma_(neg_(p.a1), q.a2, fma_(q.a0, p.a3, mul_(p.a0, q.a3))));
     return r;
 }
 
 template <typename T>
-__host__ __device__ __forceinline__ Quat<T> qdag(const Quat<T>& p)
+__device__ __forceinline__ Quat<T> qdag(const Quat<T>& p)
 {
-    return {p.a0, -p.a1, -p.a2, -p.a3};
+    return {p.a0, neg_(p.a1), neg_(p.a2), neg_(p.a3)};
 }
 
-// p q^dagger
+// p q^dagger, the signs of q^dagger folded in
 template <typename T>
-__host__ __device__ __forceinline__ Quat<T> qmul_nd(const Quat<T>& p, const Quat<T>& q)
+__device__ __forceinline__ Quat<T> qmul_nd(const Quat<T>& p, const Quat<T>& q)
 {
-    return qmul(p, qdag(q));
+    Quat<T> r;
+    r.a0 = fma_(p.a3, q.a3, fma_(p.a2, q.a2, fma_(p.a1, q.a1, mul_(p.a0, q.a0))));
+    r.a1 = fma_(neg_(p.a3), q.a2, fma_(p.a2, q.a3, fma_(q.a0, p.a1, mul_(neg_(p.a0), q.a1))));
+    r.a2 = fma_(neg_(p.a1), q.a3, fma_(p.a3, q.a1, fma_(q.a0, p.a2, mul_(neg_(p.a0), q.a2))));
+    r.a3 = fma_(neg_(p.a2), q.a1, fma_(p.a1, q.a2, fma_(q.a0, p.a3, mul_(neg_(p.a0), q.a3))));
+    return r;
 }
 
-// p^dagger q^dagger = (q p)^dagger
+// p^dagger q^dagger = (q p)^dagger, the signs folded in
 template <typename T>
-__host__ __device__ __forceinline__ Quat<T> qmul_dd(const Quat<T>& p, const Quat<T>& q)
+__device__ __forceinline__ Quat<T> qmul_dd(const Quat<T>& p, const Quat<T>& q)
 {
-    return qdag(qmul(q, p));
+    Quat<T> r;
+    r.a0 = fma_(neg_(p.a3), q.a3, fma_(neg_(p.a2), q.a2, fma_(neg_(p.a1), q.a1, mul_(p.a0, q.a0))));
+    r.a1 = fma_(p.a3, q.a2, fma_(neg_(p.a2), q.a3, fma_(neg_(q.a0), p.a1, mul_(neg_(p.a0), q.a1))));
+    r.a2 = fma_(p.a1, q.a3, fma_(neg_(p.a3), q.a1, fma_(neg_(q.a0), p.a2, mul_(neg_(p.a0), q.a2))));
+    r.a3 = fma_(p.a2, q.a1, fma_(neg_(p.a1), q.a2, fma_(neg_(q.a0), p.a3, mul_(neg_(p.a0), q.a3))));
+    return r;
 }
 
 // 1/2 Re Tr (p q) = p0 q0 - p.q
 template <typename T>
-__host__ __device__ __forceinline__ T qretr(const Quat<T>& p, const Quat<T>& q)
+__device__ __forceinline__ T qretr(const Quat<T>& p, const Quat<T>& q)
 {
-    return p.a0 * q.a0 - p.a1 * q.a1 - p.a2 * q.a2 - p.a3 * q.a3;
+    return fma_(neg_(p.a3), q.a3, fma_(neg_(p.a2), q.a2, fma_(neg_(p.a1), q.a1, mul_(p.a0, q.a0))));
 }
 
 template <typename T>
-__host__ __device__ __forceinline__ T qnorm2(const Quat<T>& p)
+__device__ __forceinline__ T qnorm2(const Quat<T>& p)
 {
-    return p.a0 * p.a0 + p.a1 * p.a1 + p.a2 * p.a2 + p.a3 * p.a3;
+    return fma_(p.a3, p.a3, fma_(p.a2, p.a2, fma_(p.a1, p.a1, mul_(p.a0, p.a0))));
+}
+
+// lane 0 / lane 1 of a pair of quaternions
+__device__ __forceinline__ Quat<float> lane0(const Quat<float2>& q)
+{
+    return {q.a0.x, q.a1.x, q.a2.x, q.a3.x};
+}
+__device__ __forceinline__ Quat<float> lane1(const Quat<float2>& q)
+{
+    return {q.a0.y, q.a1.y, q.a2.y, q.a3.y};
+}
+// the pair with its two lanes exchanged
+__device__ __forceinline__ Quat<float2> lanes_swapped(const Quat<float2>& q)
+{
+    return {make_float2(q.a0.y, q.a0.x), make_float2(q.a1.y, q.a1.x),
+            make_float2(q.a2.y, q.a2.x), make_float2(q.a3.y, q.a3.x)};
 }
 
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return ::rsqrt(x); }
 
+__device__ __forceinline__ float2 rsqrt_t(float2 x) { return make_float2(rsqrtf(x.x), rsqrtf(x.y)); }
+
 template <typename T>
 __device__ __forceinline__ Quat<T> qnormalise(const Quat<T>& p)
 {
-    T s = rsqrt_t(qnorm2(p));
-    return {p.a0 * s, p.a1 * s, p.a2 * s, p.a3 * s};
+    const T s = rsqrt_t(qnorm2(p));
+    return {mul_(p.a0, s), mul_(p.a1, s), mul_(p.a2, s), mul_(p.a3, s)};
 }
 
 // --------------------------------------------------------------------------
@@ -128,25 +182,42 @@ struct Stream {
 // 1 + k 2^-23; subtracting 1 - 2^-24 leaves (2k + 1) 2^-24 exactly
 // (Sterbenz).  Integer operations and one subtraction: no conversion on
 // the FP64 pipe.
+__device__ __forceinline__ float u01_bits(uint32_t w)  // 1 + k 2^-23
+{
+    return __int_as_float((int)((w >> 9) | 0x3F800000u));
+}
 __device__ __forceinline__ float u01f(uint32_t w)
 {
-    return __int_as_float((int)((w >> 9) | 0x3F800000u)) - 0.99999994039535522f;
+    return add_(u01_bits(w), -0.99999994039535522f);
+}
+// two uniforms at once (one packed subtraction, the same bits per lane)
+__device__ __forceinline__ float2 u01f2(uint32_t wa, uint32_t wb)
+{
+    return add_(make_float2(u01_bits(wa), u01_bits(wb)), splat<float2>(-0.99999994039535522f));
 }
 __device__ __forceinline__ double u01d(uint32_t w)
 {
     const uint32_t k = w >> 9;  // 23 bits -> mantissa bits 51..29
-    return __hiloint2double((int)(0x3FF00000u | (k >> 3)), (int)(k << 29)) -
-           0.999999940395355224609375;
+    return add_(__hiloint2double((int)(0x3FF00000u | (k >> 3)), (int)(k << 29)),
+                -0.999999940395355224609375);
 }
 // uniform in (0,1) from an 18-bit integer k: (k + 0.5) 2^-18, exact
+__device__ __forceinline__ float u18_bits(uint32_t k)
+{
+    return __int_as_float((int)(0x3F800000u | (k << 5)));
+}
 __device__ __forceinline__ float u18f(uint32_t k)
 {
-    return __int_as_float((int)(0x3F800000u | (k << 5))) - 0.9999980926513671875f;
+    return add_(u18_bits(k), -0.9999980926513671875f);
+}
+__device__ __forceinline__ float2 u18f2(uint32_t ka, uint32_t kb)
+{
+    return add_(make_float2(u18_bits(ka), u18_bits(kb)), splat<float2>(-0.9999980926513671875f));
 }
 __device__ __forceinline__ double u18d(uint32_t k)
 {
     // 18 bits -> mantissa bits 51..34, all in the high word
-    return __hiloint2double((int)(0x3FF00000u | (k << 2)), 0) - 0.9999980926513671875;
+    return add_(__hiloint2double((int)(0x3FF00000u | (k << 2)), 0), -0.9999980926513671875);
 }
 template <typename T> __device__ __forceinline__ T u18(uint32_t k);
 template <> __device__ __forceinline__ float u18<float>(uint32_t k) { return u18f(k); }
@@ -171,13 +242,13 @@ __device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sin
 template <typename T>
 __device__ __forceinline__ Quat<T> haar_from(U4 w)
 {
-    T u0 = u01<T>(w.x), u1 = u01<T>(w.y), u2 = u01<T>(w.z), u3 = u01<T>(w.w);
-    T r0 = sqrt_t(T(-2) * log_t(u0));
-    T r1 = sqrt_t(T(-2) * log_t(u2));
+    const T u0 = u01<T>(w.x), u1 = u01<T>(w.y), u2 = u01<T>(w.z), u3 = u01<T>(w.w);
+    const T r0 = sqrt_t(mul_(T(-2), log_t(u0)));
+    const T r1 = sqrt_t(mul_(T(-2), log_t(u2)));
     T s0, c0, s1, c1;
-    sincospi_t(T(2) * u1, &s0, &c0);
-    sincospi_t(T(2) * u3, &s1, &c1);
-    return qnormalise(Quat<T>{r0 * c0, r0 * s0, r1 * c1, r1 * s1});
+    sincospi_t(mul_(T(2), u1), &s0, &c0);
+    sincospi_t(mul_(T(2), u3), &s1, &c1);
+    return qnormalise(Quat<T>{mul_(r0, c0), mul_(r0, s0), mul_(r1, c1), mul_(r1, s1)});
 }
 
 // --------------------------------------------------------------------------

@@ -11,6 +11,11 @@
 //   FP32: float4   U[mu][parity][eo]              (16 B per link)
 //   FP64: double2  U[mu][parity][plane][eo]       plane 0 = (a0,a1), 1 = (a2,a3)
 // so a warp touching 32 consecutive eo reads 512 contiguous bytes per access.
+//   FP32 site pairs (Nt a multiple of 4): the sites eo = q and q + Vh/2 (the
+//   same x, y, z at t and t + Nt/2, of the same parity) share one 32 B record
+//   float4 U[mu][parity][q][2] = (a0, a0', a1, a1'), (a2, a2', a3, a3'), so
+//   one load gives both links' components side by side, the operand layout
+//   of the packed two-lane FP32 instructions (FFMA2/FMUL2/FADD2).
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -23,7 +28,7 @@ constexpr int TPB = 256;            // threads per block of the non-phase kernel
 
 // Launch shapes of the phase kernel the autotuner chooses from (threads per
 // block, minimum resident blocks per SM); entry 0 is the default.  Row 0:
-// FP32, row 1: FP64.
+// FP32, row 1: FP64, row 2: FP32 site pairs.
 // slab: walk large lattices in y slabs (EoSite::from_slab) -- FP32 only,
 // since the FP64 kernel is bound by its arithmetic, not by re-reads.
 // rounds: links per thread; above 1 the kernel with the per-warp retry
@@ -38,10 +43,12 @@ struct LaunchCfg {
     bool persistent;
 };
 constexpr int NUM_LAUNCH_CFG = 14;
+// rows of the table: link layouts with their own phase kernels
+constexpr int ROW_F32 = 0, ROW_F64 = 1, ROW_F32_PAIRS = 2, NUM_ROWS = 3;
 // Small blocks (64, 32 threads) spread tiny lattices over more SMs; several
 // links per thread pay off on large lattices (one queue pass retries 32
 // rejected trials at once) but leave small ones with too few blocks.
-constexpr LaunchCfg LAUNCH_CFG[2][NUM_LAUNCH_CFG] = {
+constexpr LaunchCfg LAUNCH_CFG[NUM_ROWS][NUM_LAUNCH_CFG] = {
     {{256, 4, false, 1, false}, {128, 8, false, 1, false}, {64, 16, false, 1, false},
      {32, 32, false, 1, false}, {256, 4, true, 1, false}, {128, 8, true, 1, false},
      {32, 32, false, 2, false}, {32, 32, false, 4, false}, {32, 32, false, 8, false},
@@ -52,6 +59,13 @@ constexpr LaunchCfg LAUNCH_CFG[2][NUM_LAUNCH_CFG] = {
      {32, 16, false, 2, false}, {32, 16, false, 4, false}, {32, 16, false, 8, false},
      {32, 16, false, 16, false}, {32, 16, false, 32, false}, {64, 8, false, 16, false},
      {32, 16, false, 2, true}, {32, 16, false, 8, true}},
+    // FP32 site pairs: one thread updates two links (t and t + Nt/2) per
+    // round with packed two-lane arithmetic; `rounds` counts pairs
+    {{256, 2, false, 1, false}, {128, 4, false, 1, false}, {64, 8, false, 1, false},
+     {32, 16, false, 1, false}, {32, 16, false, 2, false}, {32, 16, false, 4, false},
+     {32, 20, false, 2, false}, {32, 20, false, 4, false}, {32, 24, false, 4, false},
+     {32, 16, false, 8, false}, {32, 16, false, 2, true}, {32, 16, false, 1, true},
+     {32, 16, true, 4, false}, {32, 16, true, 8, false}},
 };
 static_assert(NUM_LAUNCH_CFG % 2 == 0, "shapes compile in pairs");
 // largest y-slab window (sites between a site and its t neighbour, times
@@ -76,6 +90,9 @@ struct LatDesc {
     FastDiv div_nh, div_ns;
     int32_t ysplit, Ny;     // y slabs of the large-lattice traversal, Ny = Ns / ysplit
     FastDiv div_ny, div_nt;
+    FastDiv div_nt2;        // Nt / 2: the t extent of the lattice of site pairs
+    int32_t paired;         // FP32 links stored as site pairs (t, t + Nt/2)
+    uint32_t Vq;            // site pairs per parity (Vh / 2) when paired
     double creutz_below;    // alpha below which Creutz's draw replaces Kennedy-Pendleton's
     float creutz_below_f;
     uint64_t link_off;      // byte offset of this lattice in the link buffer
@@ -83,6 +100,7 @@ struct LatDesc {
     // per call
     double beta;
     float beta_f;           // beta rounded once for the FP32 kernels
+    float half_inv_beta_f;  // 1 / (2 beta) rounded once: 1 / (2 alpha) = half_inv_beta_f / k
     double half_inv_beta;   // 1 / (2 beta) for the FP64 kernels: 1 / (2 alpha) = half_inv_beta / k
     uint64_t seed;
     uint64_t sweep_base;    // sweep index stored at plaq_out[0]
@@ -136,17 +154,20 @@ struct ParamChunk {
 cudaError_t launch_set_params(const Ctx& c, const ParamChunk& pc, cudaStream_t s);
 // hybrid: compile-time variant with Creutz's draw below each lattice's
 // creutz_below (the plain variant never looks at it)
-cudaError_t launch_phase(const Ctx& c, int dtype, int cfg, int mu, int parity, bool plaq,
+cudaError_t launch_phase(const Ctx& c, int row, int cfg, int mu, int parity, bool plaq,
                          int32_t* dbg_trials, bool hybrid, cudaStream_t s);
 cudaError_t launch_sweep_end(const Ctx& c, bool plaq, cudaStream_t s);
 cudaError_t launch_init(const Ctx& c, int dtype, int l, uint32_t V, int hot, uint64_t seed,
                         cudaStream_t s);
-// canonical values in double (cdtype 1) or float (cdtype 0)
+// canonical values in double (cdtype 1) or float (cdtype 0); pairs_whole:
+// the whole lattice (lex0 = 0, nsite = V) of a lattice stored as FP32 site
+// pairs, converted record by record
 cudaError_t launch_links_to_canonical(const Ctx& c, int dtype, int l, uint32_t lex0,
-                                      uint32_t nsite, void* dst, int cdtype, cudaStream_t s);
+                                      uint32_t nsite, void* dst, int cdtype, cudaStream_t s,
+                                      bool pairs_whole = false);
 cudaError_t launch_links_from_canonical(const Ctx& c, int dtype, int l, uint32_t lex0,
                                         uint32_t nsite, const void* src, int cdtype,
-                                        cudaStream_t s);
+                                        cudaStream_t s, bool pairs_whole = false);
 cudaError_t launch_gauge(const Ctx& c, int dtype, int l, uint32_t V, uint64_t seed, cudaStream_t s);
 cudaError_t launch_plaquette(const Ctx& c, int dtype, double* out_dev, cudaStream_t s);
 cudaError_t launch_polyakov(const Ctx& c, int dtype, double* out_signed_dev,

@@ -100,6 +100,99 @@ template <> struct Links<double> {
     }
 };
 
+// FP32 site pairs: float4 U[mu][parity][q][2], record q holding the sites
+// eo = q (lane 0) and eo = q + Vq (lane 1) as (a0, a0', a1, a1'),
+// (a2, a2', a3, a3').  Pair access for the paired phase kernel, single-site
+// access (two floats of each half of the record) for everything else.
+struct PairLinks {
+    float4* base;
+    uint32_t Vh, Vq;
+    LinkCheck chk;
+    __device__ __forceinline__ PairLinks(void* links, const LatDesc& d, uint32_t* status = nullptr)
+        : base(reinterpret_cast<float4*>(static_cast<char*>(links) + d.link_off)), Vh(d.Vh),
+          Vq(d.Vq)
+    {
+#ifdef SU2_CHECK_BOUNDS
+        chk = {status, d.Vq};
+#else
+        (void)status;
+#endif
+    }
+    // float4 index of the first half of record q
+    __device__ __forceinline__ size_t ridx(int mu, int p, uint32_t q) const
+    {
+        return chk.ok(mu, p, q) ? size_t(mu * 2 + p) * Vh + 2 * (size_t)q : 0;
+    }
+    __device__ __forceinline__ Quat<float2> load2(int mu, int p, uint32_t q) const
+    {
+        const size_t i = ridx(mu, p, q);
+        const float4 lo = __ldg(base + i), hi = __ldg(base + i + 1);
+        return {make_float2(lo.x, lo.y), make_float2(lo.z, lo.w), make_float2(hi.x, hi.y),
+                make_float2(hi.z, hi.w)};
+    }
+    __device__ __forceinline__ void store2(int mu, int p, uint32_t q, const Quat<float2>& u) const
+    {
+        if (!chk.ok(mu, p, q)) return;
+        const size_t i = size_t(mu * 2 + p) * Vh + 2 * (size_t)q;
+        base[i] = make_float4(u.a0.x, u.a0.y, u.a1.x, u.a1.y);
+        base[i + 1] = make_float4(u.a2.x, u.a2.y, u.a3.x, u.a3.y);
+    }
+    // one site eo (either lane): the floats at lane, 2 + lane, 4 + lane, 6 + lane
+    __device__ __forceinline__ const float* site(int mu, int p, uint32_t eo) const
+    {
+        const uint32_t h = eo >= Vq ? 1u : 0u;
+        return reinterpret_cast<const float*>(base + ridx(mu, p, eo - h * Vq)) + h;
+    }
+    __device__ __forceinline__ Quat<float> load(int mu, int p, uint32_t eo) const
+    {
+        const float* f = site(mu, p, eo);
+        return {__ldg(f), __ldg(f + 2), __ldg(f + 4), __ldg(f + 6)};
+    }
+    __device__ __forceinline__ Quat<float> load_rw(int mu, int p, uint32_t eo) const
+    {
+        const float* f = site(mu, p, eo);
+        return {f[0], f[2], f[4], f[6]};
+    }
+    __device__ __forceinline__ void store(int mu, int p, uint32_t eo, const Quat<float>& a) const
+    {
+        const uint32_t h = eo >= Vq ? 1u : 0u;
+        if (!chk.ok(mu, p, eo - h * Vq)) return;
+        float* f = reinterpret_cast<float*>(base + size_t(mu * 2 + p) * Vh + 2 * (size_t)(eo - h * Vq)) + h;
+        f[0] = a.a0;
+        f[2] = a.a1;
+        f[4] = a.a2;
+        f[6] = a.a3;
+    }
+};
+
+// Single-site access in whichever layout the lattice uses (the kernels
+// outside the heat-bath phases: start, layout conversion, measurements).
+template <typename T> struct AnyLinks;
+template <> struct AnyLinks<double> : Links<double> {
+    __device__ __forceinline__ AnyLinks(void* links, const LatDesc& d, uint32_t* status = nullptr)
+        : Links<double>(links, d, status) {}
+};
+template <> struct AnyLinks<float> {
+    Links<float> plain;
+    PairLinks pairs;
+    bool paired;
+    __device__ __forceinline__ AnyLinks(void* links, const LatDesc& d, uint32_t* status = nullptr)
+        : plain(links, d, status), pairs(links, d, status), paired(d.paired != 0) {}
+    __device__ __forceinline__ Quat<float> load(int mu, int p, uint32_t eo) const
+    {
+        return paired ? pairs.load(mu, p, eo) : plain.load(mu, p, eo);
+    }
+    __device__ __forceinline__ Quat<float> load_rw(int mu, int p, uint32_t eo) const
+    {
+        return paired ? pairs.load_rw(mu, p, eo) : plain.load_rw(mu, p, eo);
+    }
+    __device__ __forceinline__ void store(int mu, int p, uint32_t eo, const Quat<float>& a) const
+    {
+        if (paired) pairs.store(mu, p, eo, a);
+        else plain.store(mu, p, eo, a);
+    }
+};
+
 // Coordinates of the site with index eo inside parity p.
 struct EoSite {
     int c[4];        // x, y, z, t
@@ -132,14 +225,21 @@ struct EoSite {
     __device__ __forceinline__ static EoSite from_slab(const LatDesc& d, uint32_t j, int p,
                                                        uint32_t* eo)
     {
+        return from_slab_t(d, j, p, eo, (uint32_t)d.Nt, d.div_nt);
+    }
+    // the same walk over a lattice of t extent nt (the site pairs: Nt / 2)
+    __device__ __forceinline__ static EoSite from_slab_t(const LatDesc& d, uint32_t j, int p,
+                                                         uint32_t* eo, uint32_t nt,
+                                                         const FastDiv& div_t)
+    {
         const uint32_t r = fdiv(j, d.div_nh);
         const uint32_t xh = j - r * (uint32_t)d.Nh;
         const uint32_t r2 = fdiv(r, d.div_ny);
         const uint32_t yl = r - r2 * (uint32_t)d.Ny;
         const uint32_t r3 = fdiv(r2, d.div_ns);
         const uint32_t z = r2 - r3 * (uint32_t)d.Ns;
-        const uint32_t ys = fdiv(r3, d.div_nt);
-        const uint32_t t = r3 - ys * (uint32_t)d.Nt;
+        const uint32_t ys = fdiv(r3, div_t);
+        const uint32_t t = r3 - ys * nt;
         const uint32_t y = ys * (uint32_t)d.Ny + yl;
         *eo = xh + (uint32_t)d.Nh * (y + (uint32_t)d.Ns * (z + (uint32_t)d.Ns * t));
         return EoSite(d, *eo, p);

@@ -19,6 +19,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "su2_device.cuh"
+
 namespace su2 {
 
 template <typename T> struct Math;
@@ -26,46 +28,90 @@ template <typename T> struct Math;
 template <> struct Math<float> {
     static __device__ __forceinline__ float ln_u01(float u)
     {
-        const float v = 1.0f - u;
-        float s = fmaf(v, 0.125f, 0.142857142857f);
-        s = fmaf(v, s, 0.166666666667f);
-        s = fmaf(v, s, 0.2f);
-        s = fmaf(v, s, 0.25f);
-        s = fmaf(v, s, 0.333333333333f);
-        s = fmaf(v, s, 0.5f);
-        s = fmaf(v, s, 1.0f);
-        const float near1 = -v * s;
-        const float far = __log2f(u) * 0.693147180559945f;
+        const float v = add_(1.0f, neg_(u));
+        float s = fma_(v, 0.125f, 0.142857142857f);
+        s = fma_(v, s, 0.166666666667f);
+        s = fma_(v, s, 0.2f);
+        s = fma_(v, s, 0.25f);
+        s = fma_(v, s, 0.333333333333f);
+        s = fma_(v, s, 0.5f);
+        s = fma_(v, s, 1.0f);
+        const float near1 = mul_(neg_(v), s);
+        const float far = mul_(__log2f(u), 0.693147180559945f);
         return u > 0.9375f ? near1 : far;
     }
     static __device__ __forceinline__ float cos2pi_sq(float r)
     {
-        const float c = __cosf(6.28318530717959f * (r - 0.5f));
-        return c * c;
+        const float c = __cosf(mul_(6.28318530717959f, add_(r, -0.5f)));
+        return mul_(c, c);
     }
     static __device__ __forceinline__ void sincos2pi(float r, float* s, float* c)
     {
         float sx, cx;
-        __sincosf(6.28318530717959f * (r - 0.5f), &sx, &cx);
+        __sincosf(mul_(6.28318530717959f, add_(r, -0.5f)), &sx, &cx);
         *s = -sx;
         *c = -cx;
     }
-    static __device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
+    static __device__ __forceinline__ float sqrt_pos(float x) { return mul_(x, rsqrtf(x)); }
     static __device__ __forceinline__ float log1p(float x) { return log1pf(x); }
     static __device__ __forceinline__ float expm1(float x) { return expm1f(x); }
     static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+};
+
+// Two FP32 lanes at once: the polynomial and the scalings as packed
+// operations, the hardware logarithm, cosine and reciprocal square root per
+// lane; every lane gets exactly the bits Math<float> gives it.
+template <> struct Math<float2> {
+    static __device__ __forceinline__ float2 ln_u01(float2 u)
+    {
+        const float2 v = add_(splat<float2>(1.0f), neg_(u));
+        float2 s = fma_(v, splat<float2>(0.125f), splat<float2>(0.142857142857f));
+        s = fma_(v, s, splat<float2>(0.166666666667f));
+        s = fma_(v, s, splat<float2>(0.2f));
+        s = fma_(v, s, splat<float2>(0.25f));
+        s = fma_(v, s, splat<float2>(0.333333333333f));
+        s = fma_(v, s, splat<float2>(0.5f));
+        s = fma_(v, s, splat<float2>(1.0f));
+        const float2 near1 = mul_(neg_(v), s);
+        const float2 far = mul_(make_float2(__log2f(u.x), __log2f(u.y)),
+                                splat<float2>(0.693147180559945f));
+        return make_float2(u.x > 0.9375f ? near1.x : far.x, u.y > 0.9375f ? near1.y : far.y);
+    }
+    static __device__ __forceinline__ float2 cos2pi_sq(float2 r)
+    {
+        const float2 x = mul_(splat<float2>(6.28318530717959f), add_(r, splat<float2>(-0.5f)));
+        const float2 c = make_float2(__cosf(x.x), __cosf(x.y));
+        return mul_(c, c);
+    }
+    static __device__ __forceinline__ void sincos2pi(float2 r, float2* s, float2* c)
+    {
+        const float2 x = mul_(splat<float2>(6.28318530717959f), add_(r, splat<float2>(-0.5f)));
+        float sx, cx, sy, cy;
+        __sincosf(x.x, &sx, &cx);
+        __sincosf(x.y, &sy, &cy);
+        *s = make_float2(-sx, -sy);
+        *c = make_float2(-cx, -cy);
+    }
+    static __device__ __forceinline__ float2 sqrt_pos(float2 x)
+    {
+        return mul_(x, make_float2(rsqrtf(x.x), rsqrtf(x.y)));
+    }
+    static __device__ __forceinline__ float2 rsqrt(float2 x)
+    {
+        return make_float2(rsqrtf(x.x), rsqrtf(x.y));
+    }
 };
 
 template <> struct Math<double> {
     static __device__ __forceinline__ double ln_u01(double u) { return log(u); }
     static __device__ __forceinline__ double cos2pi_sq(double r)
     {
-        const double c = cospi(2.0 * r);
-        return c * c;
+        const double c = cospi(mul_(2.0, r));
+        return mul_(c, c);
     }
     static __device__ __forceinline__ void sincos2pi(double r, double* s, double* c)
     {
-        sincospi(2.0 * r, s, c);
+        sincospi(mul_(2.0, r), s, c);
     }
     static __device__ __forceinline__ double sqrt_pos(double x) { return sqrt(x); }
     static __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }

@@ -16,9 +16,31 @@ _F64 = [(256, 1, False, 1, False), (128, 4, False, 1, False), (64, 8, False, 1, 
         (32, 16, False, 2, True), (32, 16, False, 8, True)]
 
 
-def launch_shapes(fp64: bool):
+# FP32 site pairs: rounds count pairs (two links) per thread
+_F32P = [(256, 2, False, 1, False), (128, 4, False, 1, False), (64, 8, False, 1, False),
+         (32, 16, False, 1, False), (32, 16, False, 2, False), (32, 16, False, 4, False),
+         (32, 20, False, 2, False), (32, 20, False, 4, False), (32, 24, False, 4, False),
+         (32, 16, False, 8, False), (32, 16, False, 2, True), (32, 16, False, 1, True),
+         (32, 16, True, 4, False), (32, 16, True, 8, False)]
+ROWS = {"f32": _F32, "f64": _F64, "f32pairs": _F32P}
+
+
+def row_name(dtype: int, layout: int) -> str:
+    """The shape-table row a handle uses (dtype 0/1, layout 0 plain / 1 pairs)."""
+    return "f64" if dtype == 1 else ("f32pairs" if layout == 1 else "f32")
+
+
+def launch_shapes(row):
+    """Names of the 14 shapes of one row ("f32", "f64", "f32pairs"; a bool
+    selects f64 / f32)."""
+    if isinstance(row, bool):
+        row = "f64" if row else "f32"
+    pairs = row == "f32pairs"
+    unit = "site pair" if pairs else "link"
     return [f"{t} threads, >= {m} blocks/SM" + (", y-slab traversal" if s else "")
-            + (f", {r} link{'s' if r > 1 else ''} per thread" if r > 1 or ps else "")
-            + (", retry queue" if r > 1 or ps else "")
+            + (f", {r} {unit}{'s' if r > 1 else ''} per thread"
+               if r > 1 or ps or pairs else "")
+            + (", packed FP32x2" if pairs else "")
+            + (", retry queue" if r > 1 or ps or pairs else "")
             + (", persistent" if ps else "")
-            for t, m, s, r, ps in (_F64 if fp64 else _F32)]
+            for t, m, s, r, ps in ROWS[row]]

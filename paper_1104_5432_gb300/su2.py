@@ -26,6 +26,8 @@ SU2_E_TRIALS = -4
 SU2_E_BOUNDS = -5
 
 F32, F64 = 0, 1
+F32_PAIRS = 2  # su2_plaquette_static: FP32 links in the site-pair layout
+LAYOUT_PLAIN, LAYOUT_PAIRS = 0, 1
 COLD, HOT = 0, 1
 KP_CAP = 4096
 
@@ -93,6 +95,8 @@ def load(build_if_needed: bool = True):
             "su2_tune_cache_store": (i, [C.c_char_p, C.c_char_p, i, d]),
             "su2_set_slabs": (i, [P, i]),
             "su2_set_sampler": (i, [P, d]),
+            "su2_set_link_layout": (i, [P, i]),
+            "su2_get_link_layout": (i, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -162,7 +166,7 @@ class Lattice:
     """n >= 1 SU(2) lattices Ns^3 x Nt of one precision on the current CUDA
     device, with device memory from PyTorch's caching allocator."""
 
-    def __init__(self, Ns, Nt=None, dtype: int = F32, *, stream=None):
+    def __init__(self, Ns, Nt=None, dtype: int = F32, *, stream=None, layout=None):
         import torch
 
         lib = load()
@@ -178,6 +182,8 @@ class Lattice:
         nt = np.array([s[1] for s in shapes], np.int32)
         _check(lib.su2_batch_create(self.n, ns.ctypes.data, nt.ctypes.data, dtype, C.byref(h)))
         self._h = h
+        if layout is not None:  # before binding; the library's default otherwise
+            _check(lib.su2_set_link_layout(h, int(layout)))
         lb, wb = C.c_size_t(), C.c_size_t()
         _check(lib.su2_memory_requirements(h, C.byref(lb), C.byref(wb)))
         self.link_bytes, self.work_bytes = lb.value, wb.value
@@ -204,6 +210,17 @@ class Lattice:
         raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
         self.stream = stream
         _check(load().su2_set_stream(self._h, raw))
+
+    def link_layout(self) -> int:
+        v = C.c_int()
+        _check(load().su2_get_link_layout(self._h, C.byref(v)))
+        return v.value
+
+    def static_dtype(self) -> int:
+        """The dtype code su2_plaquette_static takes for this handle's links."""
+        if self.dtype == F64:
+            return F64
+        return F32_PAIRS if self.link_layout() == LAYOUT_PAIRS else F32
 
     def volume(self, l: int = 0) -> int:
         v = C.c_uint64()

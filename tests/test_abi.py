@@ -139,11 +139,12 @@ def test_tune_key_and_launch_config_host_side():
 
 
 def test_launch_shape_mirror_matches_library():
-    from paper_1104_5432_gb300.csrc_info import _F32, _F64
+    from paper_1104_5432_gb300.csrc_info import _F32, _F32P, _F64
     lib = su2.load()
-    for dtype, table in ((su2.F32, _F32), (su2.F64, _F64)):
+    # FP32 4^3x6 is stored plain, FP32 4^4 as site pairs, FP64 always plain
+    for dtype, Nt, table in ((su2.F32, 6, _F32), (su2.F64, 4, _F64), (su2.F32, 4, _F32P)):
         h = C.c_void_p()
-        assert lib.su2_lattice_create(4, 4, dtype, C.byref(h)) == 0
+        assert lib.su2_lattice_create(4, Nt, dtype, C.byref(h)) == 0
         assert len(table) == 14
         for k, (t, m, *_) in enumerate(table):
             assert lib.su2_set_launch_config(h, k) == 0
@@ -189,3 +190,54 @@ def test_static_plaquette_rejects_huge_extents_without_wrapping():
         rc = lib.su2_plaquette_static(fake, Ns, Nt, su2.F32, C.c_void_p(out.ctypes.data), None)
         assert rc == su2.SU2_E_INVAL, (Ns, Nt)
         assert b"static scratch" in lib.su2_last_error()
+
+
+def test_link_layout_choice_and_override():
+    """FP32 handles whose every Nt is a multiple of 4 default to site pairs;
+    the layout can be set before binding only, pairs only for FP32 lattices
+    with Nt a multiple of 4; the choice shows in the tuning key's row and
+    resets the launch shape; the sizes never change."""
+    lib = su2.load()
+
+    def layout_of(h):
+        v = C.c_int(-7)
+        assert lib.su2_get_link_layout(h, C.byref(v)) == 0
+        return v.value
+
+    def key_row(h):
+        buf = C.create_string_buffer(256)
+        assert lib.su2_tune_key(h, buf, 256) == 0
+        return buf.value.decode().split("|")[1]
+
+    h = C.c_void_p()
+    assert lib.su2_lattice_create(8, 8, su2.F32, C.byref(h)) == 0
+    assert layout_of(h) == su2.LAYOUT_PAIRS and key_row(h) == "f32pairs"
+    lb0 = C.c_size_t()
+    assert lib.su2_memory_requirements(h, C.byref(lb0), None) == 0
+    assert lib.su2_set_launch_config(h, 5) == 0
+    assert lib.su2_set_link_layout(h, su2.LAYOUT_PLAIN) == 0
+    assert layout_of(h) == su2.LAYOUT_PLAIN and key_row(h) == "f32"
+    cfg = C.c_int(-1)
+    assert lib.su2_get_launch_config(h, C.byref(cfg), None, None) == 0 and cfg.value == 0
+    lb1 = C.c_size_t()
+    assert lib.su2_memory_requirements(h, C.byref(lb1), None) == 0 and lb1.value == lb0.value
+    assert lib.su2_set_link_layout(h, su2.LAYOUT_PAIRS) == 0 and layout_of(h) == su2.LAYOUT_PAIRS
+    assert lib.su2_set_link_layout(h, 7) == su2.SU2_E_INVAL
+    lib.su2_lattice_destroy(h)
+    # Nt = 6 (or any Nt not a multiple of 4 in a batch): plain, pairs refused
+    Ns = np.array([8, 4], np.int32)
+    Nt = np.array([8, 6], np.int32)
+    assert lib.su2_batch_create(2, Ns.ctypes.data, Nt.ctypes.data, su2.F32, C.byref(h)) == 0
+    assert layout_of(h) == su2.LAYOUT_PLAIN
+    assert lib.su2_set_link_layout(h, su2.LAYOUT_PAIRS) == su2.SU2_E_INVAL
+    assert b"multiple of 4" in lib.su2_last_error()
+    lib.su2_lattice_destroy(h)
+    # FP64: plain only
+    assert lib.su2_lattice_create(8, 8, su2.F64, C.byref(h)) == 0
+    assert layout_of(h) == su2.LAYOUT_PLAIN and key_row(h) == "f64"
+    assert lib.su2_set_link_layout(h, su2.LAYOUT_PAIRS) == su2.SU2_E_INVAL
+    lib.su2_lattice_destroy(h)
+    # the static plaquette refuses the pair layout on Nt not a multiple of 4
+    out = np.zeros(1, np.float64)
+    assert lib.su2_plaquette_static(C.c_void_p(1 << 20), 4, 6, su2.F32_PAIRS,
+                                    C.c_void_p(out.ctypes.data), None) == su2.SU2_E_INVAL

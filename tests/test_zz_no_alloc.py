@@ -22,7 +22,10 @@ pytestmark = pytest.mark.gpu
 
 
 def _static_plaquette(lib, lat, Ns, Nt, dtype, out, stream):
-    return lib.su2_plaquette_static(C.c_void_p(lat.links_buf.data_ptr()), Ns, Nt, dtype,
+    # the handle's own precision is passed as its layout code (FP32 lattices
+    # with Nt a multiple of 4 are stored as site pairs)
+    code = lat.static_dtype() if dtype == lat.dtype else dtype
+    return lib.su2_plaquette_static(C.c_void_p(lat.links_buf.data_ptr()), Ns, Nt, code,
                                     C.c_void_p(out), C.c_void_p(stream))
 
 

@@ -274,7 +274,7 @@ def gpu_arm(args, rank, world, local):
     # ---- main arm: FP32, inputs resident in HBM --------------------------------
     lat = su2.Lattice(Ns, Nt, su2.F32, layout=layout_arg(args, su2))
     if args.launch_shape is None:
-        lat.autotune()  # launch shape chosen by measurement
+        lat.autotune(beta=w["beta"])  # launch shape chosen by measurement
     else:
         lat.set_launch_config(args.launch_shape)
     tuned = {"fp32": shape_name(lat)[1]}
@@ -388,7 +388,7 @@ def gpu_arm(args, rank, world, local):
     if not args.no_arms:
         # ---- FP64 plain: same lattice, FP64 throughout ---------------------------
         lat64 = su2.Lattice(Ns, Nt, su2.F64)
-        lat64.autotune()
+        lat64.autotune(beta=w["beta"])
         tuned["fp64"] = shape_name(lat64)[1]
         sw64 = 100  # the paper's 100 sweeps per start, as in the FP32 arm
         pl64 = torch.zeros(sw64, dtype=torch.float64, device="cuda")
@@ -413,7 +413,7 @@ def gpu_arm(args, rank, world, local):
         # ---- FP32 batched ensemble -------------------------------------------------
         ens = inputs.batched_ensemble(64, 5)
         B = su2.Lattice([e["Ns"] for e in ens], [e["Nt"] for e in ens], su2.F32)
-        B.autotune()
+        B.autotune(beta=[e["beta"] for e in ens])
         tuned["fp32_batched"] = shape_name(B)[1]
         betas = [e["beta"] for e in ens]
         seeds = [e["seed"] + 1000003 * rank for e in ens]
@@ -449,7 +449,7 @@ def gpu_arm(args, rank, world, local):
         cs_dev = torch.zeros(len(scan) * (rmax + 1), dtype=torch.float64, device="cuda")
         Vs_tot = sum(e["Ns"] ** 3 * e["Nt"] for e in full_scan)
 
-        S.autotune()
+        S.autotune(beta=sb)
         tuned["fp32_temperature_scan"] = shape_name(S)[1]
 
         def step_scan():
@@ -476,7 +476,7 @@ def gpu_arm(args, rank, world, local):
         # ---- the smaller configurations of the paper's benchmark shape -------------
         def small_arm(name, Nsm, dtype, beta, seed, nsw=100, K=3):
             L = su2.Lattice(Nsm, Nsm, dtype)
-            L.autotune()
+            L.autotune(beta=beta)
             tuned[name] = shape_name(L)[1]
             pl = torch.zeros(nsw, dtype=torch.float64, device="cuda")
 
@@ -501,7 +501,7 @@ def gpu_arm(args, rank, world, local):
 
         # ---- FP32 128^4 (16 GiB of links) -----------------------------------------
         big = su2.Lattice(128, 128, su2.F32)
-        big.autotune()
+        big.autotune(beta=w["beta"])
         tuned["fp32_128^4"] = shape_name(big)[1]
         sw_big = 10
         pl_big = torch.zeros(sw_big, dtype=torch.float64, device="cuda")
@@ -531,7 +531,7 @@ def gpu_arm(args, rank, world, local):
             row = {}
             for name, dtype in (("fp32", su2.F32), ("fp64", su2.F64)):
                 L = su2.Lattice(Ns, Ns, dtype)
-                L.autotune()
+                L.autotune(beta=6.0)
                 plq = torch.zeros(100, dtype=torch.float64, device="cuda")
 
                 def step_size():
@@ -554,7 +554,7 @@ def gpu_arm(args, rank, world, local):
         # at this precision), so updates/s compare at equal accuracy.
         def plaquette_series(dtype, seed, therm=500, n=20000):
             L = su2.Lattice(16, 16, dtype)
-            L.autotune()
+            L.autotune(beta=w["beta"])
             L.init(su2.HOT, seed)
             L.heatbath(w["beta"], therm, seed, plaq=None)
             p = L.heatbath(w["beta"], n, seed)[0]

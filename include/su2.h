@@ -277,10 +277,21 @@ int su2_set_sweep(su2_lattice* lat, int l, uint64_t sweep);
  * su2_init(SU2_HOT, 0x5EED) with zeroed counters; call it before su2_init
  * or su2_set_links.  If the environment variable SU2_AUTOTUNE_CACHE names
  * a file, the choice is appended there under a key made of the GPU name,
- * the precision and the lattice shapes, and su2_bind_memory of any later
- * handle with the same key starts with the cached shape.
+ * the precision and link layout, the lattice shapes, the shape table and
+ * the coupling band, and su2_bind_memory of any later handle with the same
+ * key (at beta = 2.4) starts with the cached shape.
  * chosen (nullable): the index picked.  Synchronous. */
 int su2_autotune(su2_lattice* lat, int* chosen);
+
+/* As su2_autotune, timed at the couplings the handle will run: betas is a
+ * host array of n values (NULL: beta = 2.4 for every lattice, which is what
+ * su2_autotune does).  The retry queue's share of the work follows the
+ * Kennedy-Pendleton acceptance, which depends on beta, so the best shape
+ * can differ between couplings.  The cache key carries the coupling band
+ * floor(2 log2 mean(beta)); with SU2_AUTOTUNE_CACHE set, a choice cached
+ * for the same GPU, shapes and band is taken without timing (the links are
+ * still left in the tuning seed's hot start). */
+int su2_autotune_beta(su2_lattice* lat, const double* betas, int* chosen);
 
 /* Select a launch shape by index (0 .. SU2_NUM_LAUNCH_CONFIGS-1) / read
  * the current one with its threads per block and minimum blocks per SM. */

@@ -565,8 +565,23 @@ int finish_output(su2_lattice* L, double* out, const double* dev_src, size_t cou
 // ---------------------------------------------------------------------------
 namespace {
 
-// FNV-1a over the lattice shapes, with the GPU name and precision in clear
-std::string tune_key(const su2_lattice* L, int dev)
+// Coupling band of a tuning: the mean beta of the lattices in steps of a
+// factor sqrt 2 (the retry queue's share of the work follows the
+// Kennedy-Pendleton acceptance, which grows with alpha = beta k).
+int beta_band(const su2_lattice* L, const double* betas, double beta)
+{
+    double m = 0.0;
+    for (int l = 0; l < L->n; ++l) m += betas ? betas[l] : beta;
+    m /= L->n;
+    if (!(m > 0.0)) return -99;
+    return (int)std::floor(2.0 * std::log2(m));
+}
+
+constexpr double TUNE_BETA = 2.4;  // coupling of su2_autotune without betas
+
+// FNV-1a over the lattice shapes, with the GPU name and precision in clear,
+// and the coupling band
+std::string tune_key(const su2_lattice* L, int dev, int band)
 {
     cudaDeviceProp prop;
     std::string name = "unknown-gpu";
@@ -590,12 +605,12 @@ std::string tune_key(const su2_lattice* L, int dev)
         }
     char buf[256];
     static const char* const rows[NUM_ROWS] = {"f32", "f64", "f32pairs"};
-    snprintf(buf, sizeof buf, "%s|%s|n%d|V%llu|%016llx|t%08x", name.c_str(), rows[L->row], L->n,
-             (unsigned long long)[&] {
+    snprintf(buf, sizeof buf, "%s|%s|n%d|V%llu|%016llx|t%08x|b%d", name.c_str(), rows[L->row],
+             L->n, (unsigned long long)[&] {
                  uint64_t t = 0;
                  for (uint64_t v : L->V) t += v;
                  return t;
-             }(), (unsigned long long)h, th);
+             }(), (unsigned long long)h, th, band);
     return buf;
 }
 
@@ -857,7 +872,8 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
         lat->cfg_ctx[k].phase_wpb = (uint32_t)LAUNCH_CFG[lat->row][k].threads / 32;
     }
     // a launch shape tuned earlier for these shapes on this GPU, if cached
-    lat->tune_key = tune_key(lat, dev);
+    // (at the default tuning coupling)
+    lat->tune_key = tune_key(lat, dev, beta_band(lat, nullptr, TUNE_BETA));
     lat->cfg = 0;
     if (const char* path = getenv("SU2_AUTOTUNE_CACHE")) {
         int cached = -1;
@@ -1073,16 +1089,34 @@ int su2_sync(su2_lattice* lat)
     return sync_status(lat);
 }
 
-int su2_autotune(su2_lattice* lat, int* chosen)
+int su2_autotune(su2_lattice* lat, int* chosen) { return su2_autotune_beta(lat, nullptr, chosen); }
+
+int su2_autotune_beta(su2_lattice* lat, const double* betas, int* chosen)
 {
     Range range("su2_autotune");
     if (int rc = check_handle(lat)) return rc;
+    if (betas)
+        for (int l = 0; l < lat->n; ++l)
+            if (!(betas[l] >= 0.0) || !std::isfinite(betas[l]))
+                return fail(SU2_E_INVAL, "beta must be finite and >= 0");
     DeviceGuard dg(lat->device);
     cudaStream_t s = lat->stream;
     const uint64_t tune_seed = 0x5EEDull;
+    const int band = beta_band(lat, betas, TUNE_BETA);
+    lat->tune_key = tune_key(lat, lat->device, band);
     for (int l = 0; l < lat->n; ++l)
         SU2_CUDA(launch_init(lat->ctx, lat->dtype, l, (uint32_t)lat->V[l], SU2_HOT, tune_seed + l, s));
-    if (int rc = set_params(lat, nullptr, 2.4, nullptr, tune_seed, nullptr, 0)) return rc;
+    // a choice cached for this GPU, shapes and coupling band: no timing
+    if (const char* path = getenv("SU2_AUTOTUNE_CACHE")) {
+        int cached = -1;
+        if (cache_lookup(path, lat->tune_key, &cached) && cached >= 0 && cached < NUM_LAUNCH_CFG) {
+            if (int r2 = sync_status(lat)) return r2;
+            lat->cfg = cached;
+            if (chosen) *chosen = cached;
+            return SU2_OK;
+        }
+    }
+    if (int rc = set_params(lat, betas, TUNE_BETA, nullptr, tune_seed, nullptr, 0)) return rc;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     SU2_CUDA(cudaEventCreate(&e0));
     SU2_CUDA(cudaEventCreate(&e1));
@@ -1218,7 +1252,7 @@ int su2_tune_key(const su2_lattice* lat, char* buf, size_t len)
         cudaGetLastError();
         dev = 0;
     }
-    const std::string k = tune_key(lat, dev);
+    const std::string k = tune_key(lat, dev, beta_band(lat, nullptr, TUNE_BETA));
     if (k.size() + 1 > len) return fail(SU2_E_INVAL, "buffer too small");
     memcpy(buf, k.c_str(), k.size() + 1);
     return SU2_OK;

@@ -97,7 +97,7 @@ __device__ __forceinline__ void staple_sum(const Links<T>& U, const EoSite& s, u
         const Quat<T> e = U.load(MU, q, e_mnu);      // U_mu(x-nu)
         const Quat<T> f = U.load(nu, q, e_mnu);      // U_nu(x-nu)
         const Quat<T> up = qmul_nd(qmul_nd(a, b), c);
-        const Quat<T> lo = qmul(qmul_dd(d, e), f);
+        const Quat<T> lo = qmul_dn(qmul(e, d), f);  // (e d)^dagger f
         A = qadd(A, qadd(up, lo));
         if (PLAQ && nu == MU - 1) P = A;
     }
@@ -505,7 +505,7 @@ __device__ __forceinline__ void staple_sum_pair(const PairLinks& U, const EoSite
             }
         }
         const Quat<float2> up = qmul_nd(qmul_nd(a, b), c);
-        const Quat<float2> lo = qmul(qmul_dd(d, e), f);
+        const Quat<float2> lo = qmul_dn(qmul(e, d), f);  // (e d)^dagger f
         A = qadd(A, qadd(up, lo));
         if (PLAQ && nu == MU - 1) P = A;
     }

@@ -39,7 +39,8 @@ __device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ float2 add_(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float neg_(float a) { return -a; }
 __device__ __forceinline__ double neg_(double a) { return -a; }
-__device__ __forceinline__ float2 neg_(float2 a) { return make_float2(-a.x, -a.y); }
+// packed negation: one FMUL2 by -1 (exact) instead of one instruction per lane
+__device__ __forceinline__ float2 neg_(float2 a) { return __fmul2_rn(a, make_float2(-1.0f, -1.0f)); }
 // a constant in every lane
 template <typename V> __device__ __forceinline__ V splat(float c);
 template <> __device__ __forceinline__ float splat<float>(float c) { return c; }
@@ -60,15 +61,22 @@ __device__ __forceinline__ Quat<T> qadd(const Quat<T>& p, const Quat<T>& q)
     return {add_(p.a0, q.a0), add_(p.a1, q.a1), add_(p.a2, q.a2), add_(p.a3, q.a3)};
 }
 
-// p q  for U = a0 + i a.sigma:  (p0 q0 - p.q,  p0 q + q0 p - p x q)
+// The products are written so that every term enters with a plus sign,
+// the minus signs carried by three negated components of one operand:
+// negation is free in scalar instructions but costs an instruction on a
+// packed pair, so each product negates no more than three values.
+
+// p q  for U = a0 + i a.sigma:  (p0 q0 - p.q,  p0 q + q0 p - p x q);
+// negated: the vector part of q
 template <typename T>
 __device__ __forceinline__ Quat<T> qmul(const Quat<T>& p, const Quat<T>& q)
 {
+    const T n1 = neg_(q.a1), n2 = neg_(q.a2), n3 = neg_(q.a3);
     Quat<T> r;
-    r.a0 = fma_(neg_(p.a3), q.a3, fma_(neg_(p.a2), q.a2, fma_(neg_(p.a1), q.a1, mul_(p.a0, q.a0))));
-    r.a1 = fma_(p.a3, q.a2, fma_(neg_(p.a2), q.a3, fma_(q.a0, p.a1, mul_(p.a0, q.a1))));
-    r.a2 = fma_(p.a1, q.a3, fma_(neg_(p.a3), q.a1, fma_(q.a0, p.a2, mul_(p.a0, q.a2))));
-    r.a3 = fma_(p.a2, q.a1, fma_(neg_(p.a1), q.a2, fma_(q.a0, p.a3, mul_(p.a0, q.a3))));
+    r.a0 = fma_(p.a3, n3, fma_(p.a2, n2, fma_(p.a1, n1, mul_(p.a0, q.a0))));
+    r.a1 = fma_(p.a2, n3, fma_(p.a3, q.a2, fma_(p.a0, q.a1, mul_(p.a1, q.a0))));
+    r.a2 = fma_(p.a1, q.a3, fma_(p.a3, n1, fma_(p.a0, q.a2, mul_(p.a2, q.a0))));
+    r.a3 = fma_(p.a1, n2, fma_(p.a2, q.a1, fma_(p.a0, q.a3, mul_(p.a3, q.a0))));
     return r;
 }
 
@@ -78,27 +86,29 @@ __device__ __forceinline__ Quat<T> qdag(const Quat<T>& p)
     return {p.a0, neg_(p.a1), neg_(p.a2), neg_(p.a3)};
 }
 
-// p q^dagger, the signs of q^dagger folded in
+// p q^dagger; negated: the vector part of q
 template <typename T>
 __device__ __forceinline__ Quat<T> qmul_nd(const Quat<T>& p, const Quat<T>& q)
 {
+    const T n1 = neg_(q.a1), n2 = neg_(q.a2), n3 = neg_(q.a3);
     Quat<T> r;
     r.a0 = fma_(p.a3, q.a3, fma_(p.a2, q.a2, fma_(p.a1, q.a1, mul_(p.a0, q.a0))));
-    r.a1 = fma_(neg_(p.a3), q.a2, fma_(p.a2, q.a3, fma_(q.a0, p.a1, mul_(neg_(p.a0), q.a1))));
-    r.a2 = fma_(neg_(p.a1), q.a3, fma_(p.a3, q.a1, fma_(q.a0, p.a2, mul_(neg_(p.a0), q.a2))));
-    r.a3 = fma_(neg_(p.a2), q.a1, fma_(p.a1, q.a2, fma_(q.a0, p.a3, mul_(neg_(p.a0), q.a3))));
+    r.a1 = fma_(p.a2, q.a3, fma_(p.a3, n2, fma_(p.a0, n1, mul_(p.a1, q.a0))));
+    r.a2 = fma_(p.a1, n3, fma_(p.a3, q.a1, fma_(p.a0, n2, mul_(p.a2, q.a0))));
+    r.a3 = fma_(p.a1, q.a2, fma_(p.a2, n1, fma_(p.a0, n3, mul_(p.a3, q.a0))));
     return r;
 }
 
-// p^dagger q^dagger = (q p)^dagger, the signs folded in
+// p^dagger q; negated: the vector part of p
 template <typename T>
-__device__ __forceinline__ Quat<T> qmul_dd(const Quat<T>& p, const Quat<T>& q)
+__device__ __forceinline__ Quat<T> qmul_dn(const Quat<T>& p, const Quat<T>& q)
 {
+    const T n1 = neg_(p.a1), n2 = neg_(p.a2), n3 = neg_(p.a3);
     Quat<T> r;
-    r.a0 = fma_(neg_(p.a3), q.a3, fma_(neg_(p.a2), q.a2, fma_(neg_(p.a1), q.a1, mul_(p.a0, q.a0))));
-    r.a1 = fma_(p.a3, q.a2, fma_(neg_(p.a2), q.a3, fma_(neg_(q.a0), p.a1, mul_(neg_(p.a0), q.a1))));
-    r.a2 = fma_(p.a1, q.a3, fma_(neg_(p.a3), q.a1, fma_(neg_(q.a0), p.a2, mul_(neg_(p.a0), q.a2))));
-    r.a3 = fma_(p.a2, q.a1, fma_(neg_(p.a1), q.a2, fma_(neg_(q.a0), p.a3, mul_(neg_(p.a0), q.a3))));
+    r.a0 = fma_(p.a3, q.a3, fma_(p.a2, q.a2, fma_(p.a1, q.a1, mul_(p.a0, q.a0))));
+    r.a1 = fma_(n3, q.a2, fma_(p.a2, q.a3, fma_(n1, q.a0, mul_(p.a0, q.a1))));
+    r.a2 = fma_(n1, q.a3, fma_(p.a3, q.a1, fma_(n2, q.a0, mul_(p.a0, q.a2))));
+    r.a3 = fma_(n2, q.a1, fma_(p.a1, q.a2, fma_(n3, q.a0, mul_(p.a0, q.a3))));
     return r;
 }
 
@@ -106,7 +116,7 @@ __device__ __forceinline__ Quat<T> qmul_dd(const Quat<T>& p, const Quat<T>& q)
 template <typename T>
 __device__ __forceinline__ T qretr(const Quat<T>& p, const Quat<T>& q)
 {
-    return fma_(neg_(p.a3), q.a3, fma_(neg_(p.a2), q.a2, fma_(neg_(p.a1), q.a1, mul_(p.a0, q.a0))));
+    return fma_(p.a3, neg_(q.a3), fma_(p.a2, neg_(q.a2), fma_(p.a1, neg_(q.a1), mul_(p.a0, q.a0))));
 }
 
 template <typename T>

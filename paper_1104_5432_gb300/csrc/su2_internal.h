@@ -61,11 +61,11 @@ constexpr LaunchCfg LAUNCH_CFG[NUM_ROWS][NUM_LAUNCH_CFG] = {
      {32, 16, false, 2, true}, {32, 16, false, 8, true}},
     // FP32 site pairs: one thread updates two links (t and t + Nt/2) per
     // round with packed two-lane arithmetic; `rounds` counts pairs
-    {{256, 2, false, 1, false}, {128, 4, false, 1, false}, {64, 8, false, 1, false},
-     {32, 16, false, 1, false}, {32, 16, false, 2, false}, {32, 16, false, 4, false},
-     {32, 20, false, 2, false}, {32, 20, false, 4, false}, {32, 24, false, 4, false},
-     {32, 16, false, 8, false}, {32, 16, false, 2, true}, {32, 16, false, 1, true},
-     {32, 16, true, 4, false}, {32, 16, true, 8, false}},
+    {{256, 2, false, 1, false}, {32, 16, false, 1, false}, {32, 20, false, 1, false},
+     {32, 24, false, 1, false}, {32, 28, false, 1, false}, {32, 16, false, 2, false},
+     {32, 20, false, 2, false}, {32, 24, false, 2, false}, {32, 24, false, 4, false},
+     {32, 20, false, 4, false}, {32, 24, false, 1, true}, {32, 16, false, 1, true},
+     {32, 24, true, 4, false}, {32, 16, true, 4, false}},
 };
 static_assert(NUM_LAUNCH_CFG % 2 == 0, "shapes compile in pairs");
 // largest y-slab window (sites between a site and its t neighbour, times

@@ -17,11 +17,11 @@ _F64 = [(256, 1, False, 1, False), (128, 4, False, 1, False), (64, 8, False, 1, 
 
 
 # FP32 site pairs: rounds count pairs (two links) per thread
-_F32P = [(256, 2, False, 1, False), (128, 4, False, 1, False), (64, 8, False, 1, False),
-         (32, 16, False, 1, False), (32, 16, False, 2, False), (32, 16, False, 4, False),
-         (32, 20, False, 2, False), (32, 20, False, 4, False), (32, 24, False, 4, False),
-         (32, 16, False, 8, False), (32, 16, False, 2, True), (32, 16, False, 1, True),
-         (32, 16, True, 4, False), (32, 16, True, 8, False)]
+_F32P = [(256, 2, False, 1, False), (32, 16, False, 1, False), (32, 20, False, 1, False),
+         (32, 24, False, 1, False), (32, 28, False, 1, False), (32, 16, False, 2, False),
+         (32, 20, False, 2, False), (32, 24, False, 2, False), (32, 24, False, 4, False),
+         (32, 20, False, 4, False), (32, 24, False, 1, True), (32, 16, False, 1, True),
+         (32, 24, True, 4, False), (32, 16, True, 4, False)]
 ROWS = {"f32": _F32, "f64": _F64, "f32pairs": _F32P}
 
 

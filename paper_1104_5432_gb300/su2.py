@@ -88,6 +88,7 @@ def load(build_if_needed: bool = True):
             "su2_probe_fma_rate": (i, [i, i, P, P]),
             "su2_probe_special_rate": (i, [i, i, P, P]),
             "su2_autotune": (i, [P, P]),
+            "su2_autotune_beta": (i, [P, P, P]),
             "su2_set_launch_config": (i, [P, i]),
             "su2_get_launch_config": (i, [P, P, P, P]),
             "su2_tune_key": (i, [P, C.c_char_p, sz]),
@@ -342,10 +343,15 @@ class Lattice:
         _check(load().su2_set_sweep(self._h, l, int(sweep)))
 
     # -- launch shape --------------------------------------------------------
-    def autotune(self) -> int:
-        """Pick the fastest launch shape (overwrites the links: call first)."""
+    def autotune(self, beta=None) -> int:
+        """Pick the fastest launch shape (overwrites the links: call first),
+        timed at beta (one value or one per lattice; None: 2.4)."""
         c = C.c_int()
-        _check(load().su2_autotune(self._h, C.byref(c)))
+        if beta is None:
+            _check(load().su2_autotune(self._h, C.byref(c)))
+        else:
+            b = np.ascontiguousarray(np.broadcast_to(np.asarray(beta, np.float64), (self.n,)))
+            _check(load().su2_autotune_beta(self._h, b.ctypes.data, C.byref(c)))
         return c.value
 
     def set_launch_config(self, cfg: int):

@@ -121,7 +121,8 @@ def test_tune_key_and_launch_config_host_side():
     assert parts[1] == "f32" and parts[2] == "n2" and parts[3] == "V%d" % (4 ** 4 + 6 ** 3 * 2)
     # the launch-shape table is part of the key (a renumbered table misses
     # the cache instead of selecting another shape), and differs by precision
-    assert len(parts) == 6 and parts[5].startswith("t")
+    assert len(parts) == 7 and parts[5].startswith("t")
+    assert parts[6] == "b2"  # default tuning coupling 2.4: floor(2 log2 2.4) = 2
     h64 = C.c_void_p()
     assert lib.su2_batch_create(2, Ns.ctypes.data, Nt.ctypes.data, su2.F64, C.byref(h64)) == 0
     assert lib.su2_tune_key(h64, buf, 256) == 0

@@ -550,6 +550,32 @@ def test_autotune_and_cache(tmp_path, monkeypatch):
     assert again.launch_config()[0] == chosen
 
 
+def test_autotune_at_the_run_coupling(tmp_path, monkeypatch):
+    """Tuning at the couplings the run uses: the cache key carries the
+    coupling band (beta = 6.0: floor(2 log2 6) = 5), a second tuning in the
+    same band takes the cached shape without timing, and the handle is left
+    in the tuning seed's hot start either way."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("SU2_AUTOTUNE_CACHE", str(cache))
+    lat = su2.Lattice(16, 16, su2.F32)
+    c6 = lat.autotune(beta=6.0)
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].split()[0].endswith("|b5")
+    assert int(lines[0].split()[1]) == c6
+    c05 = lat.autotune(beta=[0.5])
+    assert len(cache.read_text().splitlines()) == 2
+    assert cache.read_text().splitlines()[1].split()[0].endswith("|b-2")
+    # the same band again: from the cache, no new line
+    assert lat.autotune(beta=5.9) == c6 and lat.launch_config()[0] == c6
+    assert len(cache.read_text().splitlines()) == 2
+    ref = su2.Lattice(16, 16, su2.F32)
+    ref.init(su2.HOT, 0x5EED)
+    np.testing.assert_array_equal(lat.get_links(), ref.get_links())
+    assert lat.stats()["updates"] == 0 and 0 <= c05 < 14
+    with pytest.raises(su2.SU2Error):
+        lat.autotune(beta=-1.0)
+
+
 @pytest.mark.parametrize("layout,shape", [(su2.LAYOUT_PLAIN, 0), (su2.LAYOUT_PLAIN, 13),
                                           (su2.LAYOUT_PAIRS, 13)])
 def test_full_size_128_properties(layout, shape):

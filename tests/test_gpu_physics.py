@@ -147,3 +147,23 @@ def test_scan_worker_single_process():
         assert r["plaquette"] == plaq[l].mean()
         assert r["abs_polyakov"] == ps[1, l] / 3
         np.testing.assert_array_equal(r["correlator"], cs[l] / 3)
+
+
+def test_scan_runner_bins_match_one_call():
+    """The scan runner's bins are the measured sums of consecutive calls: two
+    bins of 5 sweeps equal one call of 10 sweeps (FP64 sums of the same
+    chain), and the analysis runs on the result."""
+    from paper_1104_5432_gb300 import scan
+    betas, seeds = [2.2, 2.45], [31, 32]
+    res = scan.run_scan(betas, Ns=8, Nt=4, therm=10, meas=10, bin_sweeps=5, rmax=4, seeds=seeds,
+                        autotune=False)
+    assert res["C"].shape == (2, 2, 5) and res["L_abs"].shape == (2, 2)
+    B = su2.Lattice([8, 8], [4, 4], su2.F32)
+    B.batch_init(su2.HOT, seeds)
+    B.batch_heatbath(betas, 10, seeds, plaq=None)
+    _, ps, cs = B.batch_heatbath_measure(betas, 10, seeds, 4)
+    np.testing.assert_allclose(res["L_abs"].mean(0), ps[1] / 10, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(res["C"].mean(0), cs / 10, rtol=0, atol=1e-12)
+    assert np.all(res["C"][:, :, 0] > 0)
+    an = scan.analyse(res)
+    assert len(an["rows"]) == 2

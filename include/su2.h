@@ -110,16 +110,19 @@ int su2_lattice_volume(const su2_lattice* lat, int l, uint64_t* V);
  * plaquette ring and a 32 MiB staging area for host transfers. */
 int su2_memory_requirements(const su2_lattice* lat, size_t* link_bytes, size_t* work_bytes);
 
-/* Device layout of the links.  An SU2_F32 handle whose lattices all have
- * Nt a multiple of 4 stores its links as site pairs (SU2_LAYOUT_PAIRS) by
- * default: one thread of the heat bath then updates the two links of a
- * record together with packed two-lane FP32 instructions (the sites t and
- * t + Nt/2 of one parity never share a staple).  Every other handle uses
- * SU2_LAYOUT_PLAIN.  Both layouts take the same bytes and give bit-identical
- * links; results never depend on the layout.  su2_set_link_layout (before
- * su2_bind_memory only; SU2_E_INVAL after, for SU2_LAYOUT_PAIRS on an FP64
- * handle or on an Nt that is not a multiple of 4) overrides the choice and
- * resets the launch shape to 0; su2_get_link_layout reads it. */
+/* Device layout of the links: SU2_LAYOUT_PLAIN by default.  An SU2_F32
+ * handle whose lattices all have Nt a multiple of 4 may instead store its
+ * links as site pairs (SU2_LAYOUT_PAIRS): one thread of the heat bath then
+ * updates the two links of a record together with packed two-lane FP32
+ * instructions (the sites t and t + Nt/2 of one parity never share a
+ * staple).  That issues about a third fewer instructions but needs twice
+ * the registers per thread, and measured slower on every lattice from 24^4
+ * to 128^4 on GB300, so it is not the default.  Both layouts take the same
+ * bytes and give bit-identical links; results never depend on the layout.
+ * su2_set_link_layout (before su2_bind_memory only; SU2_E_INVAL after, for
+ * SU2_LAYOUT_PAIRS on an FP64 handle or on an Nt that is not a multiple of
+ * 4) selects it and resets the launch shape to 0; su2_get_link_layout
+ * reads it. */
 int su2_set_link_layout(su2_lattice* lat, int layout);
 int su2_get_link_layout(const su2_lattice* lat, int* layout);
 

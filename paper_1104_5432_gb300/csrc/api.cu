@@ -195,11 +195,12 @@ bool is_device_ptr(const void* p)
 }
 
 // links one block of launch shape k updates per phase (a site-pair shape's
-// rounds count pairs)
+// rounds count pairs; a cooperative shape gives each link `group` lanes)
 uint64_t links_per_block(const su2_lattice* L, int k)
 {
     const LaunchCfg& c = LAUNCH_CFG[L->row][k];
-    return (uint64_t)c.threads * (uint64_t)c.rounds * (L->row == ROW_F32_PAIRS ? 2u : 1u);
+    return (uint64_t)c.threads * (uint64_t)c.rounds * (L->row == ROW_F32_PAIRS ? 2u : 1u) /
+           (uint64_t)c.group;
 }
 
 int layout(su2_lattice* L)
@@ -302,11 +303,9 @@ int create(int n, const int* Ns, const int* Nt, int dtype, su2_lattice** out)
     su2_lattice* L = new su2_lattice;
     L->n = n;
     L->dtype = dtype;
-    // FP32 lattices are stored as site pairs (t, t + Nt/2) when every Nt is
-    // a multiple of 4 (the two sites then have the same parity)
-    bool pairs = dtype == SU2_F32;
-    for (int l = 0; l < n; ++l) pairs = pairs && Nt[l] % 4 == 0;
-    L->row = dtype == SU2_F64 ? ROW_F64 : (pairs ? ROW_F32_PAIRS : ROW_F32);
+    // the plain layout by default; site pairs only on request
+    // (su2_set_link_layout), being slower on every lattice measured
+    L->row = dtype == SU2_F64 ? ROW_F64 : ROW_F32;
     L->Ns.assign(Ns, Ns + n);
     L->Nt.assign(Nt, Nt + n);
     layout(L);
@@ -599,7 +598,7 @@ std::string tune_key(const su2_lattice* L, int dev, int band)
     // shape only in the table it was tuned with
     uint32_t th = 2166136261u;
     for (const LaunchCfg& c : LAUNCH_CFG[L->row])
-        for (int v : {c.threads, c.min_blocks, (int)c.slab, c.rounds, (int)c.persistent}) {
+        for (int v : {c.threads, c.min_blocks, (int)c.slab, c.rounds, (int)c.persistent, c.group}) {
             th ^= (uint32_t)v;
             th *= 16777619u;
         }
@@ -1166,7 +1165,10 @@ int su2_autotune_beta(su2_lattice* lat, const double* betas, int* chosen)
     int best = 0;
     for (int k = 1; k < ncand; ++k)
         if (cand[k] && best_ms[k] < best_ms[best]) best = k;
-    // leave the handle as su2_init(SU2_HOT) with the tuning seed would
+    // leave the handle as su2_init(SU2_HOT) with the tuning seed would; trial
+    // caps hit by the tuning sweeps (small couplings under Kennedy-Pendleton
+    // alone) belong to no run of the caller and are not reported
+    SU2_CUDA(cudaMemsetAsync(lat->status_dev(), 0, sizeof(uint32_t), s));
     for (int l = 0; l < lat->n; ++l)
         SU2_CUDA(launch_init(lat->ctx, lat->dtype, l, (uint32_t)lat->V[l], SU2_HOT, tune_seed + l, s));
     if (int r2 = sync_status(lat)) return r2;

@@ -26,6 +26,8 @@
 // 1/2 Tr(U_new P) with P = sum over nu < mu of S_nu (the trace is linear),
 // so the six planes are covered exactly once at no extra memory traffic.
 #pragma once
+#include <type_traits>
+
 #include "su2_internal.h"
 #include "su2_links.cuh"
 #include "su2_math.cuh"
@@ -75,31 +77,74 @@ __device__ __forceinline__ T warp_sum_t(T v)
 // U_mu(x), and (PLAQ) its part P over nu < mu, which closes the plaquettes
 // of the planes (nu, mu).  P is A after its first mu terms, so it costs no
 // extra additions.
+//
+// The order of the additions is fixed per precision, and every kernel of a
+// precision keeps it, so all launch shapes give the same bits.  FP32 folds
+// the sums into the products' last multiply-adds (A = A + up + lo, ν by ν).
+// FP64 sums a tree: s_k = up_k + lo_k for the k-th ν != mu, then
+// A = (s_0 + s_1) + s_2 (P = the prefix over ν < mu), the order in which
+// the cooperative kernel's lanes, which compute the six terms in parallel,
+// can reproduce it.
+template <int MU>
+__device__ __forceinline__ constexpr int nu_of(int k) { return k + (k >= MU ? 1 : 0); }
+
+// the upper (a b^dagger c^dagger) or lower ((e d)^dagger f) staple term of
+// U_mu(x) in the plane (nu, mu)
+template <typename T>
+__device__ __forceinline__ Quat<T> staple_term(const Links<T>& U, int mu, int nu, int p, uint32_t i,
+                                               const int* hp, const int* hm, bool lower)
+{
+    const int q = p ^ 1;
+    if (!lower) {
+        const Quat<T> a = U.load(nu, q, i + hp[mu]);          // U_nu(x+mu)
+        const Quat<T> b = U.load(mu, q, i + hp[nu]);          // U_mu(x+nu)
+        const Quat<T> c = U.load(nu, p, i);                   // U_nu(x)
+        return qmul_nd(qmul_nd(a, b), c);
+    }
+    const Quat<T> d = U.load(nu, p, i + hp[mu] + hm[nu]);     // U_nu(x+mu-nu)
+    const Quat<T> e = U.load(mu, q, i + hm[nu]);              // U_mu(x-nu)
+    const Quat<T> f = U.load(nu, q, i + hm[nu]);              // U_nu(x-nu)
+    return qmul_dn(qmul(e, d), f);
+}
+
 template <typename T, int MU, bool PLAQ>
 __device__ __forceinline__ void staple_sum(const Links<T>& U, const EoSite& s, uint32_t i, int p,
                                            Quat<T>& A, Quat<T>& P)
 {
-    const int q = p ^ 1;
     int hp[4], hm[4];
     s.hops(hp, hm);
-    const uint32_t e_pmu = i + hp[MU];
-    A = {T(0), T(0), T(0), T(0)};
+    if constexpr (std::is_same<T, double>::value) {
+        Quat<T> sk[3];
 #pragma unroll
-    for (int nu = 0; nu < 4; ++nu) {
-        if (nu == MU) continue;
-        const uint32_t e_pnu = i + hp[nu];
-        const uint32_t e_mnu = i + hm[nu];
-        const uint32_t e_pmu_mnu = i + hp[MU] + hm[nu];
-        const Quat<T> a = U.load(nu, q, e_pmu);      // U_nu(x+mu)
-        const Quat<T> b = U.load(MU, q, e_pnu);      // U_mu(x+nu)
-        const Quat<T> c = U.load(nu, p, i);          // U_nu(x)
-        const Quat<T> d = U.load(nu, p, e_pmu_mnu);  // U_nu(x+mu-nu)
-        const Quat<T> e = U.load(MU, q, e_mnu);      // U_mu(x-nu)
-        const Quat<T> f = U.load(nu, q, e_mnu);      // U_nu(x-nu)
-        const Quat<T> up = qmul_nd(qmul_nd(a, b), c);
-        const Quat<T> lo = qmul_dn(qmul(e, d), f);  // (e d)^dagger f
-        A = qadd(A, qadd(up, lo));
-        if (PLAQ && nu == MU - 1) P = A;
+        for (int k = 0; k < 3; ++k) {
+            const int nu = nu_of<MU>(k);
+            sk[k] = qadd(staple_term(U, MU, nu, p, i, hp, hm, false),
+                         staple_term(U, MU, nu, p, i, hp, hm, true));
+        }
+        const Quat<T> s01 = qadd(sk[0], sk[1]);
+        A = qadd(s01, sk[2]);
+        if (PLAQ) P = MU == 1 ? sk[0] : (MU == 2 ? s01 : A);
+    } else {
+        const int q = p ^ 1;
+        const uint32_t e_pmu = i + hp[MU];
+        A = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int nu = 0; nu < 4; ++nu) {
+            if (nu == MU) continue;
+            const uint32_t e_pnu = i + hp[nu];
+            const uint32_t e_mnu = i + hm[nu];
+            const uint32_t e_pmu_mnu = i + hp[MU] + hm[nu];
+            const Quat<T> a = U.load(nu, q, e_pmu);      // U_nu(x+mu)
+            const Quat<T> b = U.load(MU, q, e_pnu);      // U_mu(x+nu)
+            const Quat<T> c = U.load(nu, p, i);          // U_nu(x)
+            const Quat<T> d = U.load(nu, p, e_pmu_mnu);  // U_nu(x+mu-nu)
+            const Quat<T> e = U.load(MU, q, e_mnu);      // U_mu(x-nu)
+            const Quat<T> f = U.load(nu, q, e_mnu);      // U_nu(x-nu)
+            // A += a b^dagger c^dagger + (e d)^dagger f, the sums fused into
+            // the products' last steps
+            A = qmul_dn_acc(qmul(e, d), f, qmul_nd_acc(qmul_nd(a, b), c, A));
+            if (PLAQ && nu == MU - 1) P = A;
+        }
     }
 }
 
@@ -504,9 +549,7 @@ __device__ __forceinline__ void staple_sum_pair(const PairLinks& U, const EoSite
                 f = lanes_swapped(f);
             }
         }
-        const Quat<float2> up = qmul_nd(qmul_nd(a, b), c);
-        const Quat<float2> lo = qmul_dn(qmul(e, d), f);  // (e d)^dagger f
-        A = qadd(A, qadd(up, lo));
+        A = qmul_dn_acc(qmul(e, d), f, qmul_nd_acc(qmul_nd(a, b), c, A));
         if (PLAQ && nu == MU - 1) P = A;
     }
 }
@@ -690,13 +733,125 @@ hb_pair_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     warp_totals<float, MU, PLAQ, NT>(ctx, l, blk0, Vh, plaq, ntrial, ncap);
 }
 
+// ---------------------------------------------------------------------------
+// FP64, G lanes per link: the cooperative kernel for small lattices
+// ---------------------------------------------------------------------------
+// On GB300 an FP64 warp instruction costs the FP64 units the same time with
+// one active lane as with 32, and a small lattice (8^4: 2048 links per
+// phase = 64 warps of one link per thread) leaves most SM sub-partitions
+// without work.  Here G = 8 lanes share one link: lanes 0..5 compute the six
+// staple terms at once (two products each instead of twelve in a row), the
+// sums follow the FP64 tree order above through shuffles, and the G lanes
+// try Kennedy-Pendleton trials t0 .. t0 + G - 1 at once; the link takes the
+// first accepted trial of its own sequence, as every other kernel does, so
+// links and trial counts are bit-identical to theirs.  Eight times as many
+// warps cover the phase, each with about half the FP64 instructions on its
+// critical path.
+template <typename T>
+__device__ __forceinline__ Quat<T> shfl_quat(const Quat<T>& q, int src)
+{
+    return {__shfl_sync(0xffffffffu, q.a0, src), __shfl_sync(0xffffffffu, q.a1, src),
+            __shfl_sync(0xffffffffu, q.a2, src), __shfl_sync(0xffffffffu, q.a3, src)};
+}
+
+template <typename T, int MU, bool PLAQ, bool DBG, int NT, int MINB, bool HYB, int G>
+__global__ void __launch_bounds__(NT, MINB)
+hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
+{
+    static_assert(G == 8 && KP_CAP % G == 0, "eight lanes per link, whole trial groups");
+    const int l = lattice_of_block(ctx.phase_start, ctx.n, blockIdx.x);
+    const LatDesc& D = ctx.desc[l];
+    const uint32_t Vh = D.Vh;
+    const uint32_t blk0 = __ldg(ctx.phase_start + l);
+    const int lane = threadIdx.x & 31, g = lane & (G - 1), g0 = lane & ~(G - 1);
+    const uint32_t j = (blockIdx.x - blk0) * (NT / G) + threadIdx.x / G;  // link position
+    const bool act = j < Vh;  // uniform within the group
+    const Links<T> U(ctx.links, D, ctx.status);
+
+    Quat<T> term = {T(0), T(0), T(0), T(0)};
+    uint32_t key = 0, i = j;
+    int hp[4] = {0, 0, 0, 0}, hm[4] = {0, 0, 0, 0};
+    if (act) {
+        const EoSite s(D, j, p);
+        s.hops(hp, hm);
+        key = s.lex() * 4u + MU;
+        // lanes 0..5: the upper (even lane) or lower (odd lane) staple term of
+        // the (g/2)-th nu != mu
+        if (g < 6) term = staple_term(U, MU, nu_of<MU>(g >> 1), p, i, hp, hm, (g & 1) != 0);
+    }
+    // s_k = up_k + lo_k on lanes 2k and 2k+1, then A = (s_0 + s_1) + s_2
+    const Quat<T> other = shfl_quat(term, lane ^ 1);
+    const Quat<T> sk = (g & 1) ? qadd(other, term) : qadd(term, other);
+    const Quat<T> s0 = shfl_quat(sk, g0), s1 = shfl_quat(sk, g0 + 2), s2 = shfl_quat(sk, g0 + 4);
+    const Quat<T> s01 = qadd(s0, s1);
+    const Quat<T> A = qadd(s01, s2);
+    const Quat<T> P = MU == 1 ? s0 : (MU == 2 ? s01 : A);
+
+    const T k2 = qnorm2(A);
+    const T rk = Math<T>::rsqrt(k2);
+    const T beta = beta_of<T>(D);
+    const T alpha = mul_(mul_(beta, k2), rk);
+    const uint64_t sw = D.sweep;
+    const Stream st{(uint32_t)D.seed, (uint32_t)(D.seed >> 32), key, (uint32_t)sw,
+                    (uint32_t)(sw >> 32)};
+    const bool haar = !(alpha >= alpha_haar<T>());
+    const T inv2a = inv_two_alpha<T>(D, rk, beta);
+    const bool creutz = HYB && alpha < creutz_of<T>(D);
+    const T qc = creutz ? creutz_qc(alpha) : T(0);
+
+    // lane g tries trial t0 + g; the warp loops while any of its links waits
+    bool done = !act || haar;
+    int32_t tr = -1;
+    T delta = T(0);
+    uint32_t kd1 = 0, kd2 = 0;
+    for (int t0 = 0; t0 < KP_CAP; t0 += G) {
+        if (!__any_sync(0xffffffffu, !done)) break;
+        const U4 w = st.draw(TAG_TRIAL, (uint32_t)(t0 + g));
+        if (t0 == 0) {  // the direction: spare bits of trial 0 (lane g0)
+            kd1 = __shfl_sync(0xffffffffu, spare_bits_1(w), g0);
+            kd2 = __shfl_sync(0xffffffffu, spare_bits_2(w), g0);
+        }
+        T d;
+        const bool ok = (creutz ? creutz_try(w, qc, inv2a, &d) : kp_try(w, inv2a, &d)) && !done;
+        const uint32_t m = (__ballot_sync(0xffffffffu, ok) >> g0) & ((1u << G) - 1u);
+        const int first = m ? __ffs(m) - 1 : 0;
+        const T dfirst = __shfl_sync(0xffffffffu, d, g0 + first);
+        if (!done && m) {
+            done = true;
+            tr = t0 + first + 1;
+            delta = dfirst;
+        }
+    }
+    T plaq = T(0);
+    uint32_t ntrial = 0, ncap = 0;
+    if (act && g == 0) {
+        Quat<T> un;
+        if (haar) {
+            un = haar_from<T>(st.draw(TAG_DIRECTION, 0));
+            tr = 0;
+        } else if (tr > 0) {
+            un = new_link(delta, kd1, kd2, A);
+        }
+        if (tr >= 0) {
+            U.store(MU, p, i, un);
+        } else {
+            ncap = 1;
+            if (PLAQ) un = U.load_rw(MU, p, i);
+        }
+        ntrial = tr > 0 ? (uint32_t)tr : (tr < 0 ? (uint32_t)KP_CAP : 0u);
+        if (DBG) dbg[key >> 2] = tr;
+        if (PLAQ) plaq = qretr(un, P);
+    }
+    warp_totals<T, MU, PLAQ, NT>(ctx, l, blk0, Vh, plaq, ntrial, ncap);
+}
+
 // One launch shape (NT threads per block, at least MINB blocks per SM, R
 // links -- or with PAIRS, R site pairs -- per thread, persistent or not) of
 // the phase kernel; the grid covers ctx.phase_blocks blocks of NT R links
 // or pairs (fewer, each walking several tiles, for a persistent shape on a
 // single lattice).
 template <typename T, int NT, int MINB, bool SLAB, int R = 1, bool PERSIST = false,
-          bool PAIRS = false>
+          bool PAIRS = false, int GROUP = 1>
 cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int32_t* dbg,
                                bool hyb, cudaStream_t s)
 {
@@ -704,7 +859,10 @@ cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int3
     const bool pl = plaq && parity == 1 && mu >= 1;
     const dim3 grid(c.phase_blocks), block(NT);
 #define SU2_K(MUV, PL, DB, H)                                                                   \
-    if constexpr (PAIRS)                                                                        \
+    if constexpr (GROUP > 1 && std::is_same<T, double>::value)                                  \
+        hb_phase_coop_kernel<T, MUV, PL, DB, NT, MINB, H, GROUP><<<grid, block, 0, s>>>(        \
+            c, parity, dbg);                                                                    \
+    else if constexpr (PAIRS)                                                                   \
         hb_pair_kernel<MUV, PL, DB, NT, MINB, SLAB, H, R, PERSIST><<<grid, block, 0, s>>>(      \
             c, parity, dbg);                                                                    \
     else if constexpr (R == 1 && !PERSIST)                                                      \

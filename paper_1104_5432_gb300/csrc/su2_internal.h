@@ -36,11 +36,16 @@ constexpr int TPB = 256;            // threads per block of the non-phase kernel
 // persistent (single-lattice handles): only the blocks that fit on the GPU
 // at once are launched, and each walks tiles of R rounds in grid-stride
 // order, so its retry queue carries over from tile to tile and drains once.
+// group (FP64): lanes per link; above 1 the cooperative kernel runs, whose
+// G lanes share one link's staple terms and try G Kennedy-Pendleton trials
+// at once (small lattices, where the FP64 work of few links per warp sets
+// the time).
 struct LaunchCfg {
     int threads, min_blocks;
     bool slab;
     int rounds;
     bool persistent;
+    int group = 1;
 };
 constexpr int NUM_LAUNCH_CFG = 14;
 // rows of the table: link layouts with their own phase kernels
@@ -57,7 +62,7 @@ constexpr LaunchCfg LAUNCH_CFG[NUM_ROWS][NUM_LAUNCH_CFG] = {
     {{256, 1, false, 1, false}, {128, 4, false, 1, false}, {64, 8, false, 1, false},
      {64, 4, false, 1, false}, {32, 16, false, 1, false}, {32, 8, false, 1, false},
      {32, 16, false, 2, false}, {32, 16, false, 4, false}, {32, 16, false, 8, false},
-     {32, 16, false, 16, false}, {32, 16, false, 32, false}, {64, 8, false, 16, false},
+     {32, 16, false, 16, false}, {64, 8, false, 1, false, 8}, {32, 16, false, 1, false, 8},
      {32, 16, false, 2, true}, {32, 16, false, 8, true}},
     // FP32 site pairs: one thread updates two links (t and t + Nt/2) per
     // round with packed two-lane arithmetic; `rounds` counts pairs

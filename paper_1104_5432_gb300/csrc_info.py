@@ -2,7 +2,8 @@
 csrc/su2_internal.h), for reporting which one the autotuner chose.
 Entries: (threads per block, minimum blocks per SM, y-slab walk, links per
 thread, persistent: on a single lattice only the blocks that fit on the GPU
-at once are launched and each walks several tiles)."""
+at once are launched and each walks several tiles[, lanes per link of the
+cooperative FP64 kernel])."""
 
 _F32 = [(256, 4, False, 1, False), (128, 8, False, 1, False), (64, 16, False, 1, False),
         (32, 32, False, 1, False), (256, 4, True, 1, False), (128, 8, True, 1, False),
@@ -12,7 +13,7 @@ _F32 = [(256, 4, False, 1, False), (128, 8, False, 1, False), (64, 16, False, 1,
 _F64 = [(256, 1, False, 1, False), (128, 4, False, 1, False), (64, 8, False, 1, False),
         (64, 4, False, 1, False), (32, 16, False, 1, False), (32, 8, False, 1, False),
         (32, 16, False, 2, False), (32, 16, False, 4, False), (32, 16, False, 8, False),
-        (32, 16, False, 16, False), (32, 16, False, 32, False), (64, 8, False, 16, False),
+        (32, 16, False, 16, False), (64, 8, False, 1, False, 8), (32, 16, False, 1, False, 8),
         (32, 16, False, 2, True), (32, 16, False, 8, True)]
 
 
@@ -37,10 +38,15 @@ def launch_shapes(row):
         row = "f64" if row else "f32"
     pairs = row == "f32pairs"
     unit = "site pair" if pairs else "link"
-    return [f"{t} threads, >= {m} blocks/SM" + (", y-slab traversal" if s else "")
-            + (f", {r} {unit}{'s' if r > 1 else ''} per thread"
-               if r > 1 or ps or pairs else "")
-            + (", packed FP32x2" if pairs else "")
-            + (", retry queue" if r > 1 or ps or pairs else "")
-            + (", persistent" if ps else "")
-            for t, m, s, r, ps in ROWS[row]]
+    out = []
+    for t, m, s, r, ps, *g in ROWS[row]:
+        g = g[0] if g else 1
+        out.append(f"{t} threads, >= {m} blocks/SM" + (", y-slab traversal" if s else "")
+                   + (f", {r} {unit}{'s' if r > 1 else ''} per thread"
+                      if r > 1 or ps or pairs else "")
+                   + (", packed FP32x2" if pairs else "")
+                   + (", retry queue" if r > 1 or ps or pairs else "")
+                   + (", persistent" if ps else "")
+                   + (f", {g} lanes per link (staple terms and trials in parallel)" if g > 1
+                      else ""))
+    return out

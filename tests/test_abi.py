@@ -142,10 +142,13 @@ def test_tune_key_and_launch_config_host_side():
 def test_launch_shape_mirror_matches_library():
     from paper_1104_5432_gb300.csrc_info import _F32, _F32P, _F64
     lib = su2.load()
-    # FP32 4^3x6 is stored plain, FP32 4^4 as site pairs, FP64 always plain
-    for dtype, Nt, table in ((su2.F32, 6, _F32), (su2.F64, 4, _F64), (su2.F32, 4, _F32P)):
+    # plain FP32, FP64, and FP32 4^4 set to site pairs
+    for dtype, pairs, table in ((su2.F32, False, _F32), (su2.F64, False, _F64),
+                                (su2.F32, True, _F32P)):
         h = C.c_void_p()
-        assert lib.su2_lattice_create(4, Nt, dtype, C.byref(h)) == 0
+        assert lib.su2_lattice_create(4, 4, dtype, C.byref(h)) == 0
+        if pairs:
+            assert lib.su2_set_link_layout(h, su2.LAYOUT_PAIRS) == 0
         assert len(table) == 14
         for k, (t, m, *_) in enumerate(table):
             assert lib.su2_set_launch_config(h, k) == 0
@@ -194,10 +197,10 @@ def test_static_plaquette_rejects_huge_extents_without_wrapping():
 
 
 def test_link_layout_choice_and_override():
-    """FP32 handles whose every Nt is a multiple of 4 default to site pairs;
-    the layout can be set before binding only, pairs only for FP32 lattices
-    with Nt a multiple of 4; the choice shows in the tuning key's row and
-    resets the launch shape; the sizes never change."""
+    """Handles default to the plain layout; site pairs can be set before
+    binding only, and only for FP32 lattices with Nt a multiple of 4; the
+    choice shows in the tuning key's row and resets the launch shape; the
+    sizes never change."""
     lib = su2.load()
 
     def layout_of(h):
@@ -212,6 +215,8 @@ def test_link_layout_choice_and_override():
 
     h = C.c_void_p()
     assert lib.su2_lattice_create(8, 8, su2.F32, C.byref(h)) == 0
+    assert layout_of(h) == su2.LAYOUT_PLAIN and key_row(h) == "f32"
+    assert lib.su2_set_link_layout(h, su2.LAYOUT_PAIRS) == 0
     assert layout_of(h) == su2.LAYOUT_PAIRS and key_row(h) == "f32pairs"
     lb0 = C.c_size_t()
     assert lib.su2_memory_requirements(h, C.byref(lb0), None) == 0

@@ -799,20 +799,40 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const bool creutz = HYB && alpha < creutz_of<T>(D);
     const T qc = creutz ? creutz_qc(alpha) : T(0);
 
-    // lane g tries trial t0 + g; the warp loops while any of its links waits
+    // Kennedy-Pendleton: lanes g and g + 4 share trial t0 + (g & 3), lane g
+    // taking ln r1 and lane g + 4 ln r3, so each lane evaluates one logarithm
+    // per pass and a pass tries four trials; Creutz's draw needs one
+    // logarithm per trial, so there each of the eight lanes tries its own.
+    // Each group advances its own t0; the warp loops while any link waits.
+    const int stride = creutz ? G : G / 2;
+    const int tg = creutz ? g : (g & 3);
     bool done = !act || haar;
     int32_t tr = -1;
     T delta = T(0);
     uint32_t kd1 = 0, kd2 = 0;
-    for (int t0 = 0; t0 < KP_CAP; t0 += G) {
+    int t0 = 0;
+    for (int pass = 0;; ++pass) {
+        if (!done && t0 >= KP_CAP) done = true;  // cap hit: tr stays -1
         if (!__any_sync(0xffffffffu, !done)) break;
-        const U4 w = st.draw(TAG_TRIAL, (uint32_t)(t0 + g));
-        if (t0 == 0) {  // the direction: spare bits of trial 0 (lane g0)
+        const U4 w = st.draw(TAG_TRIAL, (uint32_t)(t0 + tg));
+        if (pass == 0) {  // the direction: spare bits of trial 0 (lane g0)
             kd1 = __shfl_sync(0xffffffffu, spare_bits_1(w), g0);
             kd2 = __shfl_sync(0xffffffffu, spare_bits_2(w), g0);
         }
+        const T r1 = u01<T>(w.x), r2 = u01<T>(w.y), r3 = u01<T>(w.z), r4 = u01<T>(w.w);
+        const T lnv = Math<T>::ln_u01(g < 4 ? r1 : r3);
+        const T ln3 = __shfl_sync(0xffffffffu, lnv, lane ^ 4);
         T d;
-        const bool ok = (creutz ? creutz_try(w, qc, inv2a, &d) : kp_try(w, inv2a, &d)) && !done;
+        bool ok;
+        if (creutz) {
+            ok = creutz_try(w, qc, inv2a, &d);
+        } else {
+            // kp_eval's arithmetic, with ln r3 from the partner lane
+            const T lam2 = mul_(neg_(fma_(Math<T>::cos2pi_sq(r2), ln3, lnv)), inv2a);
+            d = add_(lam2, lam2);
+            ok = g < 4 && mul_(r4, r4) <= add_(T(1), neg_(lam2));
+        }
+        ok = ok && !done;
         const uint32_t m = (__ballot_sync(0xffffffffu, ok) >> g0) & ((1u << G) - 1u);
         const int first = m ? __ffs(m) - 1 : 0;
         const T dfirst = __shfl_sync(0xffffffffu, d, g0 + first);
@@ -821,7 +841,26 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             tr = t0 + first + 1;
             delta = dfirst;
         }
+        t0 += stride;
     }
+    // the new link, new_link's arithmetic spread over the group: lanes
+    // g0 .. g0+3 take sin and cos of phi, lane g0+4 sin(theta) and lane
+    // g0+5 |vector part| (the two square roots at once)
+    const T one = T(1);
+    const T cth = fma_(T(2), u18<T>(kd1), T(-1));
+    T sph = T(0), cph = T(0), root = T(0);
+    if (g < 4) {
+        Math<T>::sincos2pi(u18<T>(kd2), &sph, &cph);
+    } else {
+        root = Math<T>::sqrt_pos(g == 4 ? mul_(add_(one, neg_(cth)), add_(one, cth))
+                                        : mul_(delta, add_(T(2), neg_(delta))));
+    }
+    const T sth = __shfl_sync(0xffffffffu, root, g0 + 4);
+    const T vl = __shfl_sync(0xffffffffu, root, g0 + 5);
+    sph = __shfl_sync(0xffffffffu, sph, g0);
+    cph = __shfl_sync(0xffffffffu, cph, g0);
+    const T vs = mul_(vl, sth);
+    const Quat<T> X = {add_(one, neg_(delta)), mul_(vs, cph), mul_(vs, sph), mul_(vl, cth)};
     T plaq = T(0);
     uint32_t ntrial = 0, ncap = 0;
     if (act && g == 0) {
@@ -830,7 +869,7 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             un = haar_from<T>(st.draw(TAG_DIRECTION, 0));
             tr = 0;
         } else if (tr > 0) {
-            un = new_link(delta, kd1, kd2, A);
+            un = qnormalise(qmul_nd(X, A));
         }
         if (tr >= 0) {
             U.store(MU, p, i, un);

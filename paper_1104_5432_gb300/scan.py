@@ -10,9 +10,9 @@ modulus and the correlator C(r).  Everything after that (bin means,
 jackknife errors, the fits) is host post-processing of those FP64 sums.
 
 Scale setting is a reading, since the paper does not give its own: the
-critical coupling beta_c is where <|L|> rises fastest in this scan, and
-T / T_c = a(beta_c) / a(beta) with the two-loop asymptotic scaling of the
-SU(2) lattice spacing.
+critical coupling beta_c is where <|L|> first climbs through half of its
+largest value in this scan, and T / T_c = a(beta_c) / a(beta) with the
+two-loop asymptotic scaling of the SU(2) lattice spacing.
 
     python -m paper_1104_5432_gb300.scan --out scan.json
 """
@@ -57,25 +57,18 @@ def jackknife(bins: np.ndarray, f=lambda m: m):
 
 
 def beta_critical(betas: Sequence[float], abs_L: Sequence[float]) -> float:
-    """The coupling where <|L|> rises fastest: the midpoint of the largest
-    finite-difference slope, refined by a parabola through that slope and
-    its neighbours."""
+    """The coupling where <|L|> first climbs through half of its largest
+    value in the scan, by linear interpolation between the two couplings
+    around the crossing.  Half the maximum, not the steepest slope, because
+    on the deconfined side of a large lattice a hot start can leave Z2
+    domain walls that pull single couplings back towards zero."""
     b = np.asarray(betas, dtype=np.float64)
     y = np.asarray(abs_L, dtype=np.float64)
-    mid = 0.5 * (b[1:] + b[:-1])
-    slope = np.diff(y) / np.diff(b)
-    k = int(np.argmax(slope))
-    if 0 < k < len(slope) - 1:
-        x0, x1, x2 = mid[k - 1:k + 2]
-        s0, s1, s2 = slope[k - 1:k + 2]
-        den = (x0 - x1) * (x0 - x2) * (x1 - x2)
-        a = (x2 * (s1 - s0) + x1 * (s0 - s2) + x0 * (s2 - s1)) / den
-        bb = (x2 ** 2 * (s0 - s1) + x1 ** 2 * (s2 - s0) + x0 ** 2 * (s1 - s2)) / den
-        if a < 0:
-            xv = -bb / (2 * a)
-            if x0 <= xv <= x2:
-                return float(xv)
-    return float(mid[k])
+    half = 0.5 * float(y.max())
+    k = int(np.argmax(y >= half))
+    if k == 0:
+        return float(b[0])
+    return float(b[k - 1] + (half - y[k - 1]) * (b[k] - b[k - 1]) / (y[k] - y[k - 1]))
 
 
 def fit_sigma(C_bins: np.ndarray, Nt: int, rmin: int = 2, rel_err_max: float = 0.3,
@@ -118,10 +111,11 @@ def fit_sigma(C_bins: np.ndarray, Nt: int, rmin: int = 2, rel_err_max: float = 0
 
 def run_scan(betas: Sequence[float], Ns: int = 48, Nt: int = 4, therm: int = 500,
              meas: int = 2000, bin_sweeps: int = 50, rmax: int = 24,
-             seeds: Optional[Sequence[int]] = None, autotune: bool = True) -> Dict:
-    """Thermalise one lattice per coupling, then measure in bins of
-    bin_sweeps sweeps (the Polyakov loop and C(r), r = 0..rmax, after every
-    sweep); returns the per-bin means."""
+             seeds: Optional[Sequence[int]] = None, autotune: bool = True,
+             start: str = "hot") -> Dict:
+    """Thermalise one lattice per coupling from a hot (Haar) or cold (unit)
+    start, then measure in bins of bin_sweeps sweeps (the Polyakov loop and
+    C(r), r = 0..rmax, after every sweep); returns the per-bin means."""
     import torch
 
     from . import su2
@@ -130,8 +124,8 @@ def run_scan(betas: Sequence[float], Ns: int = 48, Nt: int = 4, therm: int = 500
     seeds = list(seeds) if seeds is not None else [1000 + i for i in range(n)]
     lat = su2.Lattice([Ns] * n, [Nt] * n, su2.F32)
     if autotune:
-        lat.autotune()
-    lat.batch_init(su2.HOT, seeds)
+        lat.autotune(beta=list(betas))
+    lat.batch_init(su2.HOT if start == "hot" else su2.COLD, seeds)
     lat.batch_heatbath(betas, therm, seeds, plaq=None)
     nb = meas // bin_sweeps
     L = np.zeros((nb, n))
@@ -149,7 +143,7 @@ def run_scan(betas: Sequence[float], Ns: int = 48, Nt: int = 4, therm: int = 500
     torch.cuda.synchronize()
     seconds = ev[0].elapsed_time(ev[1]) / 1e3
     lat.close()
-    return {"betas": list(map(float, betas)), "Ns": Ns, "Nt": Nt, "therm": therm,
+    return {"betas": list(map(float, betas)), "Ns": Ns, "Nt": Nt, "therm": therm, "start": start,
             "meas": nb * bin_sweeps, "bin_sweeps": bin_sweeps, "rmax": rmax, "seeds": seeds,
             "L": L, "L_abs": L_abs, "C": C, "plaquette": P,
             "measure_seconds": seconds,
@@ -204,11 +198,26 @@ def main(argv=None):
     ap.add_argument("--meas", type=int, default=2000)
     ap.add_argument("--bin", type=int, default=50)
     ap.add_argument("--rmax", type=int, default=24)
+    ap.add_argument("--start", choices=["hot", "cold"], default="hot",
+                    help="hot (Haar) or cold (unit links) start; a cold start avoids Z2 "
+                         "domain walls on the deconfined side")
     ap.add_argument("--out", default=None, help="write the raw bins and the analysis as JSON")
+    ap.add_argument("--analyse", default=None, metavar="JSON",
+                    help="analyse the raw bins of an earlier --out file (no GPU)")
     args = ap.parse_args(argv)
+    if args.analyse:
+        with open(args.analyse) as f:
+            raw = json.load(f)["raw"]
+        res = {k: (np.asarray(v) if k in ("L", "L_abs", "C", "plaquette") else v)
+               for k, v in raw.items()}
+        an = analyse(res)
+        print(f"beta_c = {an['beta_c']:.4f}; {res['Ns']}^3x{res['Nt']}, {res['start']} start, "
+              f"{res['therm']} + {res['meas']} sweeps, bins of {res['bin_sweeps']}")
+        print(table(an))
+        return 0
     scan = inputs.temperature_scan(args.points, args.Ns, args.Nt)
     res = run_scan([e["beta"] for e in scan], args.Ns, args.Nt, args.therm, args.meas, args.bin,
-                   args.rmax, [e["seed"] for e in scan])
+                   args.rmax, [e["seed"] for e in scan], start=args.start)
     an = analyse(res)
     print(f"beta_c = {an['beta_c']:.4f}; {res['link_updates_per_s'] / 1e9:.1f} G link "
           f"updates/s over the measured sweeps")

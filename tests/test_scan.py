@@ -35,11 +35,17 @@ def test_two_loop_scale_setting():
     assert scan.t_over_tc(2.4, 2.3) > 1.0 > scan.t_over_tc(2.2, 2.3)
 
 
-def test_beta_critical_finds_the_steepest_rise():
+def test_beta_critical_at_half_the_largest_value():
+    """A symmetric rise (tanh) crosses half its height at its centre, also
+    when single couplings past it fall back (domain walls)."""
     betas = np.round(np.arange(2.20, 2.405, 0.01), 2)
     for bc in (2.2873, 2.30, 2.3456):
-        y = 0.02 + 0.1 * (1 + np.tanh((betas - bc) / 0.015))
+        y = 0.1 * (1 + np.tanh((betas - bc) / 0.015))
         assert scan.beta_critical(betas, y) == pytest.approx(bc, abs=0.003)
+        dips = y.copy()
+        dips[-1] = dips[-4] = 0.03
+        assert scan.beta_critical(betas, dips) == pytest.approx(bc, abs=0.003)
+    assert scan.beta_critical([2.2, 2.3], [0.5, 0.1]) == 2.2
 
 
 def test_string_tension_fit_recovers_known_parameters():

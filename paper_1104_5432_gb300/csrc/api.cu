@@ -466,6 +466,8 @@ int sync_status(su2_lattice* L)
         SU2_CUDA(cudaMemset(L->status_dev(), 0, sizeof st));
         if (st & STATUS_BOUNDS)
             return fail(SU2_E_BOUNDS, "link index out of bounds (bounds-checked build)");
+        if (st & STATUS_STAGE)
+            return fail(SU2_E_CUDA, "bulk copy of neighbour rows did not complete; phase abandoned");
         if (st & STATUS_CAP_HIT)
             return fail(SU2_E_TRIALS, "Kennedy-Pendleton trial cap (%d) hit; links kept", KP_CAP);
     }
@@ -598,7 +600,8 @@ std::string tune_key(const su2_lattice* L, int dev, int band)
     // shape only in the table it was tuned with
     uint32_t th = 2166136261u;
     for (const LaunchCfg& c : LAUNCH_CFG[L->row])
-        for (int v : {c.threads, c.min_blocks, (int)c.slab, c.rounds, (int)c.persistent, c.group}) {
+        for (int v : {c.threads, c.min_blocks, (int)c.slab, c.rounds, (int)c.persistent, c.group,
+                      (int)c.stage}) {
             th ^= (uint32_t)v;
             th *= 16777619u;
         }

@@ -324,6 +324,114 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 }
 
 // ---------------------------------------------------------------------------
+// neighbour rows staged in shared memory by bulk copies (FP32, Nh = 32)
+// ---------------------------------------------------------------------------
+// With Nh = 32 a warp's 32 consecutive storage indices are one row (fixed y,
+// z, t, all x of one parity), and every one of the 18 neighbour sets of the
+// row is again one row of some (direction, parity) plane: a y, z or t hop
+// moves the whole row, an x hop rotates it within itself.  One lane copies
+// the 18 rows (512 B each) into the warp's shared buffer with cp.async.bulk,
+// completing on an mbarrier; each lane then reads its neighbour at the
+// index (e mod 32) of its own neighbour e.
+constexpr int STAGE_ROWS = 18;
+constexpr uint32_t STAGE_ROW_BYTES = 32 * sizeof(float4);
+constexpr uint32_t STAGE_WAIT_POLLS = 1u << 20;  // bounded wait (each poll waits a while)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 ::"r"(smem_addr(m)), "r"(bytes) : "memory");
+}
+// one contiguous global -> shared copy of `bytes` (16-byte aligned, a
+// multiple of 16) completing on mbarrier m
+__device__ __forceinline__ void bulk_to_shared(void* dst, const void* src, uint32_t bytes,
+                                               uint64_t* m)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(m)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_addr(m)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// bounded wait for phase `parity` of m; false if it did not complete
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity)
+{
+    for (uint32_t k = 0; k < STAGE_WAIT_POLLS; ++k)
+        if (mbar_try_wait(m, parity)) return true;
+    return false;
+}
+
+// storage index of load slot k (ν by ν: a, b, c, d, e, f as in staple_sum)
+// and its (direction, parity) plane
+template <int MU>
+__device__ __forceinline__ uint32_t stage_site(int k, int p, uint32_t i, const int* hp,
+                                               const int* hm, int* plane)
+{
+    const int nu = nu_of<MU>(k / 6), q = p ^ 1;
+    switch (k % 6) {
+    case 0: *plane = nu * 2 + q; return i + hp[MU];           // U_nu(x+mu)
+    case 1: *plane = MU * 2 + q; return i + hp[nu];           // U_mu(x+nu)
+    case 2: *plane = nu * 2 + p; return i;                    // U_nu(x)
+    case 3: *plane = nu * 2 + p; return i + hp[MU] + hm[nu];  // U_nu(x+mu-nu)
+    case 4: *plane = MU * 2 + q; return i + hm[nu];           // U_mu(x-nu)
+    default: *plane = nu * 2 + q; return i + hm[nu];          // U_nu(x-nu)
+    }
+}
+
+// lane 0 starts the 18 row copies of the warp's row (its own neighbours
+// name the rows); the caller waits on m
+template <int MU>
+__device__ __forceinline__ void stage_issue(const Links<float>& U, int p, uint32_t i,
+                                            const int* hp, const int* hm,
+                                            float4 (*rows)[32], uint64_t* m)
+{
+    mbar_expect_tx(m, STAGE_ROWS * STAGE_ROW_BYTES);
+#pragma unroll
+    for (int k = 0; k < STAGE_ROWS; ++k) {
+        int plane;
+        const uint32_t e = stage_site<MU>(k, p, i, hp, hm, &plane);
+        bulk_to_shared(rows[k], U.base + (size_t)plane * U.Vh + (e & ~31u), STAGE_ROW_BYTES, m);
+    }
+}
+
+// staple_sum's FP32 arithmetic on the staged rows
+template <int MU, bool PLAQ>
+__device__ __forceinline__ void staple_sum_staged(const float4 (*rows)[32], int p, uint32_t i,
+                                                  const int* hp, const int* hm, Quat<float>& A,
+                                                  Quat<float>& P)
+{
+    auto ld = [&](int k) {
+        int plane;
+        const float4 v = rows[k][stage_site<MU>(k, p, i, hp, hm, &plane) & 31u];
+        return Quat<float>{v.x, v.y, v.z, v.w};
+    };
+    A = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+        const Quat<float> a = ld(6 * kk), b = ld(6 * kk + 1), c = ld(6 * kk + 2);
+        const Quat<float> d = ld(6 * kk + 3), e = ld(6 * kk + 4), f = ld(6 * kk + 5);
+        A = qmul_dn_acc(qmul(e, d), f, qmul_nd_acc(qmul_nd(a, b), c, A));
+        if (PLAQ && nu_of<MU>(kk) == MU - 1) P = A;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // R links per thread with a per-warp retry queue
 // ---------------------------------------------------------------------------
 // With one link per thread a warp repeats the trial loop until its last
@@ -349,13 +457,17 @@ struct RetryQueue {
 };
 
 template <typename T, int MU, bool PLAQ, bool DBG, int NT, int MINB, bool SLAB, bool HYB, int R,
-          bool PERSIST>
+          bool PERSIST, bool STAGE = false>
 __global__ void __launch_bounds__(NT, MINB)
 hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 {
     static_assert(KP_CAP <= (1 << 13), "trial index must fit 13 bits");
+    static_assert(!STAGE || (std::is_same<T, float>::value && !SLAB),
+                  "staged rows: FP32, plain traversal");
     using Queue = RetryQueue<T, PLAQ, HYB>;
     __shared__ Queue sq[NT / 32];
+    __shared__ __align__(128) float4 srows[STAGE ? NT / 32 : 1][STAGE ? STAGE_ROWS : 1][32];
+    __shared__ __align__(8) uint64_t smbar[NT / 32];
 
     const int l = lattice_of_block(ctx.phase_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
@@ -379,6 +491,14 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     T plaq = T(0);
     uint32_t ntrial = 0, ncap = 0;
     int cnt = 0;  // queued links (warp-uniform)
+    // staged rows: lattices with one row per warp (Nh = 32); block-uniform
+    const bool staged = STAGE && D.Nh == 32;
+    uint64_t* mb = &smbar[threadIdx.x >> 5];
+    uint32_t mphase = 0;
+    if (staged) {
+        if (lane == 0) mbar_init(mb, 1);
+        __syncwarp();
+    }
 
     // a final link: store, plaquette, trial count
     auto put = [&](uint32_t i, uint32_t key, const Quat<T>& un, const Quat<T>& P, int32_t tr) {
@@ -455,9 +575,32 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             Quat<T> A = {T(0), T(0), T(0), T(0)}, P = A;
             T inv2a = T(0), qc = T(0);
             uint32_t key = 0, tk = 0, kd2 = 0, i = j;
-            if (j < Vh) {
+            if (j < Vh) {  // warp-uniform when staged (Vh is a multiple of 32 there)
                 const EoSite s = SLAB ? EoSite::from_slab(D, j, p, &i) : EoSite(D, j, p);
-                staple_sum<T, MU, PLAQ>(U, s, i, p, A, P);
+                if constexpr (STAGE) {
+                    if (staged) {
+                        int hp[4], hm[4];
+                        s.hops(hp, hm);
+                        float4 (*rows)[32] = srows[threadIdx.x >> 5];
+                        // the previous round's reads are done before new copies land
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) stage_issue<MU>(U, p, i, hp, hm, rows, mb);
+                        const bool ok = mbar_wait(mb, mphase);
+                        mphase ^= 1u;
+                        if (!__all_sync(0xffffffffu, ok)) {
+                            // give up the phase; let the copies in flight land first
+                            if (lane == 0) atomicOr(ctx.status, STATUS_STAGE);
+                            mbar_wait(mb, mphase ^ 1u);
+                            return;
+                        }
+                        staple_sum_staged<MU, PLAQ>(rows, p, i, hp, hm, A, P);
+                    } else {
+                        staple_sum<T, MU, PLAQ>(U, s, i, p, A, P);
+                    }
+                } else {
+                    staple_sum<T, MU, PLAQ>(U, s, i, p, A, P);
+                }
                 const T k2 = qnorm2(A);
                 const T rk = Math<T>::rsqrt(k2);
                 const T alpha = mul_(mul_(beta, k2), rk);
@@ -890,7 +1033,7 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 // or pairs (fewer, each walking several tiles, for a persistent shape on a
 // single lattice).
 template <typename T, int NT, int MINB, bool SLAB, int R = 1, bool PERSIST = false,
-          bool PAIRS = false, int GROUP = 1>
+          bool PAIRS = false, int GROUP = 1, bool STAGE = false>
 cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int32_t* dbg,
                                bool hyb, cudaStream_t s)
 {
@@ -904,10 +1047,11 @@ cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int3
     else if constexpr (PAIRS)                                                                   \
         hb_pair_kernel<MUV, PL, DB, NT, MINB, SLAB, H, R, PERSIST><<<grid, block, 0, s>>>(      \
             c, parity, dbg);                                                                    \
-    else if constexpr (R == 1 && !PERSIST)                                                      \
+    else if constexpr (R == 1 && !PERSIST && !STAGE)                                            \
         hb_phase_kernel<T, MUV, PL, DB, NT, MINB, SLAB, H><<<grid, block, 0, s>>>(c, parity, dbg); \
     else                                                                                        \
-        hb_phase_queue_kernel<T, MUV, PL, DB, NT, MINB, SLAB, H, R, PERSIST><<<grid, block, 0, s>>>( \
+        hb_phase_queue_kernel<T, MUV, PL, DB, NT, MINB, SLAB, H, R, PERSIST,                     \
+                              STAGE && std::is_same<T, float>::value><<<grid, block, 0, s>>>(     \
             c, parity, dbg)
 #define SU2_LAUNCH_H(MUV, H)                                    \
     do {                                                        \

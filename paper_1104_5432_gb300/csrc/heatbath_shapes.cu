@@ -23,10 +23,10 @@ cudaError_t launch_phase_pair(const Ctx& c, int cfg, int mu, int parity, bool pl
     constexpr LaunchCfg B = LAUNCH_CFG[ROW][FIRST + 1];
     if (cfg == FIRST)
         return launch_phase_shape<T, A.threads, A.min_blocks, A.slab, A.rounds, A.persistent,
-                                  PAIRS, A.group>(c, mu, parity, plaq, dbg, hyb, s);
+                                  PAIRS, A.group, A.stage>(c, mu, parity, plaq, dbg, hyb, s);
     if (cfg == FIRST + 1)
         return launch_phase_shape<T, B.threads, B.min_blocks, B.slab, B.rounds, B.persistent,
-                                  PAIRS, B.group>(c, mu, parity, plaq, dbg, hyb, s);
+                                  PAIRS, B.group, B.stage>(c, mu, parity, plaq, dbg, hyb, s);
     return cudaErrorInvalidValue;
 }
 

@@ -40,12 +40,17 @@ constexpr int TPB = 256;            // threads per block of the non-phase kernel
 // G lanes share one link's staple terms and try G Kennedy-Pendleton trials
 // at once (small lattices, where the FP64 work of few links per warp sets
 // the time).
+// stage (FP32 queued kernel, lattices with Nh = 32): each round one lane
+// brings the 18 neighbour rows of the warp's 32 sites into shared memory
+// with bulk copies (cp.async.bulk behind an mbarrier), and the lanes read
+// their neighbours there.
 struct LaunchCfg {
     int threads, min_blocks;
     bool slab;
     int rounds;
     bool persistent;
     int group = 1;
+    bool stage = false;
 };
 constexpr int NUM_LAUNCH_CFG = 14;
 // rows of the table: link layouts with their own phase kernels
@@ -57,7 +62,7 @@ constexpr LaunchCfg LAUNCH_CFG[NUM_ROWS][NUM_LAUNCH_CFG] = {
     {{256, 4, false, 1, false}, {128, 8, false, 1, false}, {64, 16, false, 1, false},
      {32, 32, false, 1, false}, {256, 4, true, 1, false}, {128, 8, true, 1, false},
      {32, 32, false, 2, false}, {32, 32, false, 4, false}, {32, 32, false, 8, false},
-     {32, 32, false, 16, false}, {32, 32, false, 2, true}, {32, 32, false, 1, true},
+     {32, 16, false, 4, false, 1, true}, {32, 32, false, 2, true}, {32, 32, false, 1, true},
      {32, 32, true, 8, false}, {32, 32, true, 16, false}},
     {{256, 1, false, 1, false}, {128, 4, false, 1, false}, {64, 8, false, 1, false},
      {64, 4, false, 1, false}, {32, 16, false, 1, false}, {32, 8, false, 1, false},
@@ -82,6 +87,7 @@ constexpr int PLAQ_RING = 4096;     // per-lattice plaquette slots for host outp
 constexpr size_t STAGE_BYTES = size_t(32) << 20;
 constexpr uint32_t STATUS_CAP_HIT = 1u;
 constexpr uint32_t STATUS_BOUNDS = 2u;  // bounds-checked builds only
+constexpr uint32_t STATUS_STAGE = 4u;   // a bulk copy of neighbour rows did not arrive in time
 constexpr int SWEEP_CHUNK = TPB * 8;   // plaquette partials summed per sweep_end block
 constexpr int MAX_RMAX = 128;          // largest correlator separation
 constexpr int TRIAL_SLOTS = 64;        // per-lattice trial counters (spread atomics)

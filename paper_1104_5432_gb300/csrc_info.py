@@ -3,12 +3,13 @@ csrc/su2_internal.h), for reporting which one the autotuner chose.
 Entries: (threads per block, minimum blocks per SM, y-slab walk, links per
 thread, persistent: on a single lattice only the blocks that fit on the GPU
 at once are launched and each walks several tiles[, lanes per link of the
-cooperative FP64 kernel])."""
+cooperative FP64 kernel[, neighbour rows staged in shared memory by bulk
+copies]])."""
 
 _F32 = [(256, 4, False, 1, False), (128, 8, False, 1, False), (64, 16, False, 1, False),
         (32, 32, False, 1, False), (256, 4, True, 1, False), (128, 8, True, 1, False),
         (32, 32, False, 2, False), (32, 32, False, 4, False), (32, 32, False, 8, False),
-        (32, 32, False, 16, False), (32, 32, False, 2, True), (32, 32, False, 1, True),
+        (32, 16, False, 4, False, 1, True), (32, 32, False, 2, True), (32, 32, False, 1, True),
         (32, 32, True, 8, False), (32, 32, True, 16, False)]
 _F64 = [(256, 1, False, 1, False), (128, 4, False, 1, False), (64, 8, False, 1, False),
         (64, 4, False, 1, False), (32, 16, False, 1, False), (32, 8, False, 1, False),
@@ -39,8 +40,9 @@ def launch_shapes(row):
     pairs = row == "f32pairs"
     unit = "site pair" if pairs else "link"
     out = []
-    for t, m, s, r, ps, *g in ROWS[row]:
-        g = g[0] if g else 1
+    for t, m, s, r, ps, *extra in ROWS[row]:
+        g = extra[0] if extra else 1
+        stage = len(extra) > 1 and extra[1]
         out.append(f"{t} threads, >= {m} blocks/SM" + (", y-slab traversal" if s else "")
                    + (f", {r} {unit}{'s' if r > 1 else ''} per thread"
                       if r > 1 or ps or pairs else "")
@@ -48,5 +50,6 @@ def launch_shapes(row):
                    + (", retry queue" if r > 1 or ps or pairs else "")
                    + (", persistent" if ps else "")
                    + (f", {g} lanes per link (staple terms and trials in parallel)" if g > 1
-                      else ""))
+                      else "")
+                   + (", neighbour rows staged by bulk copies" if stage else ""))
     return out

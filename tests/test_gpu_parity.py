@@ -913,3 +913,49 @@ def test_site_pairs_link_io_and_gauge():
     a.gauge_transform(5)
     b.gauge_transform(5)
     np.testing.assert_array_equal(b.get_links(), a.get_links())
+
+
+def test_staged_rows_bit_identical():
+    """FP32 shape 9 stages the warp's 18 neighbour rows in shared memory with
+    bulk copies on lattices whose rows hold 32 sites of a parity (Ns = 64):
+    links, trial statistics and per-link trial counts equal the one-link
+    kernel's bit for bit, alone and in a batch beside a lattice that takes
+    the ordinary loads (Ns = 8), with Kennedy-Pendleton alone and with the
+    Creutz hybrid."""
+    shapes = [(64, 4), (8, 6)]
+    seeds, betas = [91, 92], [1.1, 2.4]
+    from paper_1104_5432_gb300.csrc_info import _F32
+    assert len(_F32[9]) == 7 and _F32[9][6]
+    for creutz in (0.0, 1.7):
+        out = []
+        for cfg in (0, 9):
+            B = su2.Lattice([s[0] for s in shapes], [s[1] for s in shapes], su2.F32)
+            B.set_launch_config(cfg)
+            if creutz:
+                B.set_sampler(creutz)
+            B.batch_init(su2.HOT, seeds)
+            plaq = B.batch_heatbath(betas, 2, seeds)
+            B.sync()
+            out.append(([B.get_links(l) for l in range(2)], [B.stats(l) for l in range(2)], plaq))
+            B.close()
+        (la, sa, pa), (lb, sb, pb) = out
+        for l in range(2):
+            np.testing.assert_array_equal(lb[l], la[l])
+        assert sb == sa
+        np.testing.assert_allclose(pb, pa, rtol=0, atol=1e-7)
+    # per-link trial counts of single phases at a coupling with many retries
+    Ns, Nt = 64, 4
+    V = Ns ** 3 * Nt
+    tr = {}
+    for cfg in (0, 9):
+        lat = lattice(Ns, Nt, su2.F32)
+        lat.set_launch_config(cfg)
+        lat.init(su2.HOT, 93)
+        t = torch.full((V,), -2, dtype=torch.int32, device="cuda")
+        for mu, p in PHASES[:4]:
+            lat.heatbath_phase(0.8, mu, p, 94, t)
+        lat.sync()
+        tr[cfg] = (t.cpu().numpy(), lat.get_links())
+        lat.close()
+    np.testing.assert_array_equal(tr[9][0], tr[0][0])
+    np.testing.assert_array_equal(tr[9][1], tr[0][1])

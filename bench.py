@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-arms", action="store_true", help="skip the FP64 and batched arms")
     ap.add_argument("--profile-case",
-                    choices=["f32_64", "f32_80", "f32_128", "f64_64", "f64_8", "scan"],
+                    choices=["f32_64", "f32_80", "f32_128", "f32_128x16", "f64_64", "f64_8",
+                             "scan"],
                     help="run only a few sweeps of one lattice (for ncu captures) and exit")
     ap.add_argument("--launch-shape", type=int, default=None,
                     help="phase-kernel launch shape index instead of autotuning")
@@ -721,9 +722,10 @@ def profile_case(args):
         print(json.dumps({"profile_case": "scan", "launch_shape": S.launch_config(),
                           "abs_polyakov_0": float(ps[1, 0] / 3)}))
         return
-    Ns, dt = {"f32_64": (64, su2.F32), "f32_80": (80, su2.F32), "f32_128": (128, su2.F32),
-              "f64_64": (64, su2.F64), "f64_8": (8, su2.F64)}[args.profile_case]
-    lat = su2.Lattice(Ns, Ns, dt, layout=None if dt == su2.F64 else layout_arg(args, su2))
+    Ns, Nt, dt = {"f32_64": (64, 64, su2.F32), "f32_80": (80, 80, su2.F32),
+                  "f32_128": (128, 128, su2.F32), "f32_128x16": (128, 16, su2.F32),
+                  "f64_64": (64, 64, su2.F64), "f64_8": (8, 8, su2.F64)}[args.profile_case]
+    lat = su2.Lattice(Ns, Nt, dt, layout=None if dt == su2.F64 else layout_arg(args, su2))
     lat.set_launch_config(args.launch_shape or 0)
     lat.init(su2.HOT, WORKLOAD["init_seed"])
     pl = torch.zeros(3, dtype=torch.float64, device="cuda")

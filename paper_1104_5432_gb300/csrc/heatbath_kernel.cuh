@@ -877,7 +877,7 @@ hb_pair_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 }
 
 // ---------------------------------------------------------------------------
-// G lanes per link: the cooperative kernel for small lattices
+// FP64, G lanes per link: the cooperative kernel for small lattices
 // ---------------------------------------------------------------------------
 // On GB300 an FP64 warp instruction costs the FP64 units the same time with
 // one active lane as with 32, and a small lattice (8^4: 2048 links per
@@ -911,62 +911,25 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const bool act = j < Vh;  // uniform within the group
     const Links<T> U(ctx.links, D, ctx.status);
 
+    static_assert(std::is_same<T, double>::value, "the FP64 tree order of the staple");
+    Quat<T> term = {T(0), T(0), T(0), T(0)};
     uint32_t key = 0, i = j;
     int hp[4] = {0, 0, 0, 0}, hm[4] = {0, 0, 0, 0};
-    Quat<T> A, P;
-    if constexpr (std::is_same<T, double>::value) {
-        Quat<T> term = {T(0), T(0), T(0), T(0)};
-        if (act) {
-            const EoSite s(D, j, p);
-            s.hops(hp, hm);
-            key = s.lex() * 4u + MU;
-            // lanes 0..5: the upper (even lane) or lower (odd lane) staple
-            // term of the (g/2)-th nu != mu
-            if (g < 6) term = staple_term(U, MU, nu_of<MU>(g >> 1), p, i, hp, hm, (g & 1) != 0);
-        }
-        // s_k = up_k + lo_k on lanes 2k and 2k+1, then A = (s_0 + s_1) + s_2
-        const Quat<T> other = shfl_quat(term, lane ^ 1);
-        const Quat<T> sk = (g & 1) ? qadd(other, term) : qadd(term, other);
-        const Quat<T> s0 = shfl_quat(sk, g0), s1 = shfl_quat(sk, g0 + 2), s2 = shfl_quat(sk, g0 + 4);
-        const Quat<T> s01 = qadd(s0, s1);
-        A = qadd(s01, s2);
-        P = MU == 1 ? s0 : (MU == 2 ? s01 : A);
-    } else {
-        // FP32 keeps its fused order (A += a b^dagger c^dagger + (e d)^dagger f,
-        // nu by nu): lanes 0..5 load one term's three links and form its
-        // inner product (a b^dagger or e d) at once, then every lane runs the
-        // six accumulating products of the chain with the inner products and
-        // the third links gathered by shuffles
-        Quat<T> inner = {T(0), T(0), T(0), T(0)}, last = inner;
-        if (act) {
-            const EoSite s(D, j, p);
-            s.hops(hp, hm);
-            key = s.lex() * 4u + MU;
-            if (g < 6) {
-                const int nu = nu_of<MU>(g >> 1), q = p ^ 1;
-                if (g & 1) {
-                    const Quat<T> d = U.load(nu, p, i + hp[MU] + hm[nu]);  // U_nu(x+mu-nu)
-                    const Quat<T> e = U.load(MU, q, i + hm[nu]);           // U_mu(x-nu)
-                    last = U.load(nu, q, i + hm[nu]);                      // U_nu(x-nu)
-                    inner = qmul(e, d);
-                } else {
-                    const Quat<T> a = U.load(nu, q, i + hp[MU]);           // U_nu(x+mu)
-                    const Quat<T> b = U.load(MU, q, i + hp[nu]);           // U_mu(x+nu)
-                    last = U.load(nu, p, i);                               // U_nu(x)
-                    inner = qmul_nd(a, b);
-                }
-            }
-        }
-        A = {T(0), T(0), T(0), T(0)};
-        P = A;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const Quat<T> ab = shfl_quat(inner, g0 + 2 * k), c = shfl_quat(last, g0 + 2 * k);
-            const Quat<T> ed = shfl_quat(inner, g0 + 2 * k + 1), f = shfl_quat(last, g0 + 2 * k + 1);
-            A = qmul_dn_acc(ed, f, qmul_nd_acc(ab, c, A));
-            if (PLAQ && nu_of<MU>(k) == MU - 1) P = A;
-        }
+    if (act) {
+        const EoSite s(D, j, p);
+        s.hops(hp, hm);
+        key = s.lex() * 4u + MU;
+        // lanes 0..5: the upper (even lane) or lower (odd lane) staple term of
+        // the (g/2)-th nu != mu
+        if (g < 6) term = staple_term(U, MU, nu_of<MU>(g >> 1), p, i, hp, hm, (g & 1) != 0);
     }
+    // s_k = up_k + lo_k on lanes 2k and 2k+1, then A = (s_0 + s_1) + s_2
+    const Quat<T> other = shfl_quat(term, lane ^ 1);
+    const Quat<T> sk = (g & 1) ? qadd(other, term) : qadd(term, other);
+    const Quat<T> s0 = shfl_quat(sk, g0), s1 = shfl_quat(sk, g0 + 2), s2 = shfl_quat(sk, g0 + 4);
+    const Quat<T> s01 = qadd(s0, s1);
+    const Quat<T> A = qadd(s01, s2);
+    const Quat<T> P = MU == 1 ? s0 : (MU == 2 ? s01 : A);
 
     const T k2 = qnorm2(A);
     const T rk = Math<T>::rsqrt(k2);
@@ -985,9 +948,8 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     // per pass and a pass tries four trials; Creutz's draw needs one
     // logarithm per trial, so there each of the eight lanes tries its own.
     // Each group advances its own t0; the warp loops while any link waits.
-    constexpr bool SPLIT = std::is_same<T, double>::value;  // FP32 logarithms are cheap
-    const int stride = (creutz || !SPLIT) ? G : G / 2;
-    const int tg = (creutz || !SPLIT) ? g : (g & 3);
+    const int stride = creutz ? G : G / 2;
+    const int tg = creutz ? g : (g & 3);
     bool done = !act || haar;
     int32_t tr = -1;
     T delta = T(0);
@@ -1002,14 +964,12 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             kd2 = __shfl_sync(0xffffffffu, spare_bits_2(w), g0);
         }
         const T r1 = u01<T>(w.x), r2 = u01<T>(w.y), r3 = u01<T>(w.z), r4 = u01<T>(w.w);
-        const T lnv = SPLIT ? Math<T>::ln_u01(g < 4 ? r1 : r3) : T(0);
-        const T ln3 = SPLIT ? __shfl_sync(0xffffffffu, lnv, lane ^ 4) : T(0);
+        const T lnv = Math<T>::ln_u01(g < 4 ? r1 : r3);
+        const T ln3 = __shfl_sync(0xffffffffu, lnv, lane ^ 4);
         T d;
         bool ok;
         if (creutz) {
             ok = creutz_try(w, qc, inv2a, &d);
-        } else if (!SPLIT) {
-            ok = kp_try(w, inv2a, &d);
         } else {
             // kp_eval's arithmetic, with ln r3 from the partner lane
             const T lam2 = mul_(neg_(fma_(Math<T>::cos2pi_sq(r2), ln3, lnv)), inv2a);
@@ -1082,7 +1042,7 @@ cudaError_t launch_phase_shape(const Ctx& c, int mu, int parity, bool plaq, int3
     const bool pl = plaq && parity == 1 && mu >= 1;
     const dim3 grid(c.phase_blocks), block(NT);
 #define SU2_K(MUV, PL, DB, H)                                                                   \
-    if constexpr (GROUP > 1 && !PAIRS)                                                          \
+    if constexpr (GROUP > 1 && std::is_same<T, double>::value)                                  \
         hb_phase_coop_kernel<T, MUV, PL, DB, NT, MINB, H, GROUP><<<grid, block, 0, s>>>(        \
             c, parity, dbg);                                                                    \
     else if constexpr (PAIRS)                                                                   \

@@ -36,9 +36,10 @@ constexpr int TPB = 256;            // threads per block of the non-phase kernel
 // persistent (single-lattice handles): only the blocks that fit on the GPU
 // at once are launched, and each walks tiles of R rounds in grid-stride
 // order, so its retry queue carries over from tile to tile and drains once.
-// group: lanes per link; above 1 the cooperative kernel runs, whose G lanes
-// share one link's staple terms and try several Kennedy-Pendleton trials at
-// once (small lattices, where one update's chain of work sets the time).
+// group (FP64): lanes per link; above 1 the cooperative kernel runs, whose
+// G lanes share one link's staple terms and try several Kennedy-Pendleton
+// trials at once (small lattices, where the FP64 work of few links per warp
+// sets the time).
 // stage (FP32 queued kernel, lattices with Nh = 32): each round one lane
 // brings the 18 neighbour rows of the warp's 32 sites into shared memory
 // with bulk copies (cp.async.bulk behind an mbarrier), and the lanes read
@@ -59,7 +60,7 @@ constexpr int ROW_F32 = 0, ROW_F64 = 1, ROW_F32_PAIRS = 2, NUM_ROWS = 3;
 // rejected trials at once) but leave small ones with too few blocks.
 constexpr LaunchCfg LAUNCH_CFG[NUM_ROWS][NUM_LAUNCH_CFG] = {
     {{256, 4, false, 1, false}, {128, 8, false, 1, false}, {64, 16, false, 1, false},
-     {32, 32, false, 1, false}, {256, 4, true, 1, false}, {64, 16, false, 1, false, 8},
+     {32, 32, false, 1, false}, {256, 4, true, 1, false}, {128, 8, true, 1, false},
      {32, 32, false, 2, false}, {32, 32, false, 4, false}, {32, 32, false, 8, false},
      {32, 16, false, 4, false, 1, true}, {32, 32, false, 2, true}, {32, 32, false, 1, true},
      {32, 32, true, 8, false}, {32, 32, true, 16, false}},

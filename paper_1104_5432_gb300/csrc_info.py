@@ -7,7 +7,7 @@ cooperative FP64 kernel[, neighbour rows staged in shared memory by bulk
 copies]])."""
 
 _F32 = [(256, 4, False, 1, False), (128, 8, False, 1, False), (64, 16, False, 1, False),
-        (32, 32, False, 1, False), (256, 4, True, 1, False), (64, 16, False, 1, False, 8),
+        (32, 32, False, 1, False), (256, 4, True, 1, False), (128, 8, True, 1, False),
         (32, 32, False, 2, False), (32, 32, False, 4, False), (32, 32, False, 8, False),
         (32, 16, False, 4, False, 1, True), (32, 32, False, 2, True), (32, 32, False, 1, True),
         (32, 32, True, 8, False), (32, 32, True, 16, False)]

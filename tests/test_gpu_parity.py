@@ -510,7 +510,7 @@ def test_every_launch_shape_gives_identical_results(dtype):
     shapes = [(8, 4), (8, 6), (4, 2)]
     seeds, betas = [7, 8, 9], [2.3, 2.5, 1.9]
     ref_links = ref_plaq = None
-    for cfg, slabs in [(k, 1) for k in range(14)] + [(4, 2), (12, 4), (4, 4), (12, 2), (13, 4)]:
+    for cfg, slabs in [(k, 1) for k in range(14)] + [(4, 2), (5, 4), (4, 4), (12, 2), (13, 4)]:
         B = su2.Lattice([s[0] for s in shapes], [s[1] for s in shapes], dtype)
         B.set_launch_config(cfg)
         B.set_slabs(slabs)  # slab shapes walk y in `slabs` slabs (FP32)

@@ -89,7 +89,11 @@ template <int MU>
 __device__ __forceinline__ constexpr int nu_of(int k) { return k + (k >= MU ? 1 : 0); }
 
 // the upper (a b^dagger c^dagger) or lower ((e d)^dagger f) staple term of
-// U_mu(x) in the plane (nu, mu)
+// U_mu(x) in the plane (nu, mu).  Both are formed as x y^dagger z^dagger:
+// the lower one is d^dagger e^dagger f, i.e. x = d^dagger, y = e,
+// z = f^dagger (conjugation is an exact sign flip), so that lanes computing
+// upper and lower terms side by side run one instruction stream (the
+// cooperative kernel).
 template <typename T>
 __device__ __forceinline__ Quat<T> staple_term(const Links<T>& U, int mu, int nu, int p, uint32_t i,
                                                const int* hp, const int* hm, bool lower)
@@ -104,7 +108,7 @@ __device__ __forceinline__ Quat<T> staple_term(const Links<T>& U, int mu, int nu
     const Quat<T> d = U.load(nu, p, i + hp[mu] + hm[nu]);     // U_nu(x+mu-nu)
     const Quat<T> e = U.load(mu, q, i + hm[nu]);              // U_mu(x-nu)
     const Quat<T> f = U.load(nu, q, i + hm[nu]);              // U_nu(x-nu)
-    return qmul_dn(qmul(e, d), f);
+    return qmul_nd(qmul_nd(qdag(d), e), qdag(f));
 }
 
 template <typename T, int MU, bool PLAQ>
@@ -882,14 +886,18 @@ hb_pair_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 // On GB300 an FP64 warp instruction costs the FP64 units the same time with
 // one active lane as with 32, and a small lattice (8^4: 2048 links per
 // phase = 64 warps of one link per thread) leaves most SM sub-partitions
-// without work.  Here G = 8 lanes share one link: lanes 0..5 compute the six
-// staple terms at once (two products each instead of twelve in a row), the
-// sums follow the FP64 tree order above through shuffles, and the G lanes
-// try Kennedy-Pendleton trials t0 .. t0 + G - 1 at once; the link takes the
-// first accepted trial of its own sequence, as every other kernel does, so
-// links and trial counts are bit-identical to theirs.  Eight times as many
-// warps cover the phase, each with about half the FP64 instructions on its
-// critical path.
+// without work.  Here G = 8 lanes share one link, and the phase takes as
+// long as one warp's stream of FP64 instructions, so the link's work is
+// laid out for few instructions, not few lanes: lanes 0..5 compute the six
+// staple terms at once (upper and lower in one stream), the sums follow the
+// FP64 tree order above through shuffles, the lanes try Kennedy-Pendleton
+// trials t0 .. t0 + 3 at once (one logarithm per lane) while two of them
+// take the direction's cosine and sine in the trials' cospi stream, the
+// two square roots of the new link share one stream, and lanes 0..3 form
+// one component each of the final product.  The link takes the first
+// accepted trial of its own sequence, as every other kernel does, and each
+// value comes from the same operations as in the scalar kernels, so links
+// and trial counts are bit-identical to theirs.
 template <typename T>
 __device__ __forceinline__ Quat<T> shfl_quat(const Quat<T>& q, int src)
 {
@@ -897,11 +905,47 @@ __device__ __forceinline__ Quat<T> shfl_quat(const Quat<T>& q, int src)
             __shfl_sync(0xffffffffu, q.a2, src), __shfl_sync(0xffffffffu, q.a3, src)};
 }
 
+// x with its sign flipped where m has bit 63 set (an integer operation)
+__device__ __forceinline__ double flip_sign(double x, uint64_t m)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)m);
+}
+__device__ __forceinline__ Quat<double> qdag_if(const Quat<double>& q, uint64_t m)
+{
+    return {q.a0, flip_sign(q.a1, m), flip_sign(q.a2, m), flip_sign(q.a3, m)};
+}
+
+// the k-th of four values, by selects (no indexed local array)
+template <typename V>
+__device__ __forceinline__ V pick4(int k, V v0, V v1, V v2, V v3)
+{
+    return k == 0 ? v0 : (k == 1 ? v1 : (k == 2 ? v2 : v3));
+}
+
+// Component c of p q^dagger: qmul_nd's multiply and three fused
+// multiply-adds for that component, in its order, on operands picked per
+// lane, so four lanes form the four components in one stream with
+// qmul_nd's bits.
+__device__ __forceinline__ double qmul_nd_part(int c, const Quat<double>& p, const Quat<double>& q)
+{
+    constexpr uint64_t S = 0x8000000000000000ull;
+    const double x0 = pick4(c, p.a0, p.a1, p.a2, p.a3);
+    const double x1 = c == 0 ? p.a1 : p.a0;
+    const double x2 = (c == 1 || c == 2) ? p.a3 : p.a2;
+    const double x3 = pick4(c, p.a3, p.a2, p.a1, p.a1);
+    const double y1 = flip_sign(pick4(c, q.a1, q.a1, q.a2, q.a3), c != 0 ? S : 0ull);
+    const double y2 = flip_sign(pick4(c, q.a2, q.a2, q.a1, q.a1), (c & 1) ? S : 0ull);
+    const double y3 = flip_sign(pick4(c, q.a3, q.a3, q.a3, q.a2), c == 2 ? S : 0ull);
+    return fma_(x3, y3, fma_(x2, y2, fma_(x1, y1, mul_(x0, q.a0))));
+}
+
 template <typename T, int MU, bool PLAQ, bool DBG, int NT, int MINB, bool HYB, int G>
 __global__ void __launch_bounds__(NT, MINB)
 hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 {
     static_assert(G == 8 && KP_CAP % G == 0, "eight lanes per link, whole trial groups");
+    static_assert(std::is_same<T, double>::value, "the FP64 tree order of the staple");
+    constexpr uint64_t SIGN = 0x8000000000000000ull;
     const int l = lattice_of_block(ctx.phase_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
     const uint32_t Vh = D.Vh;
@@ -911,17 +955,30 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const bool act = j < Vh;  // uniform within the group
     const Links<T> U(ctx.links, D, ctx.status);
 
-    static_assert(std::is_same<T, double>::value, "the FP64 tree order of the staple");
     Quat<T> term = {T(0), T(0), T(0), T(0)};
-    uint32_t key = 0, i = j;
-    int hp[4] = {0, 0, 0, 0}, hm[4] = {0, 0, 0, 0};
+    uint32_t key = 0;
+    const uint32_t i = j;
     if (act) {
         const EoSite s(D, j, p);
+        int hp[4], hm[4];
         s.hops(hp, hm);
         key = s.lex() * 4u + MU;
-        // lanes 0..5: the upper (even lane) or lower (odd lane) staple term of
-        // the (g/2)-th nu != mu
-        if (g < 6) term = staple_term(U, MU, nu_of<MU>(g >> 1), p, i, hp, hm, (g & 1) != 0);
+        if (g < 6) {
+            // lane 2k: the upper term of the k-th nu != mu, (a, b, c) =
+            // (U_nu(x+mu), U_mu(x+nu), U_nu(x)); lane 2k+1: the lower one,
+            // (d^dagger, e, f^dagger) = (U_nu(x+mu-nu)^dagger, U_mu(x-nu),
+            // U_nu(x-nu)^dagger); each lane forms x y^dagger z^dagger
+            const int nu = nu_of<MU>(g >> 1);
+            const bool lower = (g & 1) != 0;
+            const int q = p ^ 1;
+            const int hpn = pick4(nu, hp[0], hp[1], hp[2], hp[3]);
+            const int hmn = pick4(nu, hm[0], hm[1], hm[2], hm[3]);
+            const uint64_t m = lower ? SIGN : 0ull;
+            const Quat<T> x = qdag_if(U.load(nu, lower ? p : q, i + hp[MU] + (lower ? hmn : 0)), m);
+            const Quat<T> y = U.load(MU, q, i + (lower ? hmn : hpn));
+            const Quat<T> z = qdag_if(U.load(nu, lower ? q : p, lower ? i + hmn : i), m);
+            term = qmul_nd(qmul_nd(x, y), z);
+        }
     }
     // s_k = up_k + lo_k on lanes 2k and 2k+1, then A = (s_0 + s_1) + s_2
     const Quat<T> other = shfl_quat(term, lane ^ 1);
@@ -945,14 +1002,18 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 
     // Kennedy-Pendleton: lanes g and g + 4 share trial t0 + (g & 3), lane g
     // taking ln r1 and lane g + 4 ln r3, so each lane evaluates one logarithm
-    // per pass and a pass tries four trials; Creutz's draw needs one
-    // logarithm per trial, so there each of the eight lanes tries its own.
-    // Each group advances its own t0; the warp loops while any link waits.
+    // per pass and a pass tries four trials; in the first pass lanes 4 and 5
+    // put the direction's cos(phi) and sin(phi) = cos(phi - pi/2), phi =
+    // 2 pi u2, in place of the cos(2 pi r2) that only lanes 0..3 use.
+    // Creutz's draw needs one logarithm per trial, so there each of the eight
+    // lanes tries its own (the direction still comes from lanes 4 and 5 of
+    // the first pass).  Each group advances its own t0; the warp loops while
+    // any link waits.
     const int stride = creutz ? G : G / 2;
     const int tg = creutz ? g : (g & 3);
     bool done = !act || haar;
     int32_t tr = -1;
-    T delta = T(0);
+    T delta = T(0), cph = T(0), sph = T(0);
     uint32_t kd1 = 0, kd2 = 0;
     int t0 = 0;
     for (int pass = 0;; ++pass) {
@@ -963,17 +1024,31 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             kd1 = __shfl_sync(0xffffffffu, spare_bits_1(w), g0);
             kd2 = __shfl_sync(0xffffffffu, spare_bits_2(w), g0);
         }
-        const T r1 = u01<T>(w.x), r2 = u01<T>(w.y), r3 = u01<T>(w.z), r4 = u01<T>(w.w);
-        const T lnv = Math<T>::ln_u01(g < 4 ? r1 : r3);
+        // kp_eval's pieces, with ln r3 from the partner lane (all lanes,
+        // outside the branch: the shuffles need the whole warp)
+        const T lnv = Math<T>::ln_u01(u01<T>(g < 4 ? w.x : w.z));
         const T ln3 = __shfl_sync(0xffffffffu, lnv, lane ^ 4);
+        // u01(r2) or, for the direction, u18(kd2): the same bit construction
+        // and subtraction as u01d / u18d, operands picked per lane
+        const bool dir = pass == 0 && (g == 4 || g == 5);
+        const uint32_t k23 = w.y >> 9;
+        const T u = add_(__hiloint2double((int)(0x3FF00000u | (dir ? kd2 << 2 : k23 >> 3)),
+                                          dir ? 0 : (int)(k23 << 29)),
+                         dir ? -0.9999980926513671875 : -0.999999940395355224609375);
+        // 2 u exactly; minus 1/2 (exact) on lane 5 for the sine
+        const T cv = cospi(add_(mul_(T(2), u), dir && g == 5 ? T(-0.5) : T(-0.0)));
+        if (pass == 0) {
+            cph = __shfl_sync(0xffffffffu, cv, g0 + 4);
+            sph = __shfl_sync(0xffffffffu, cv, g0 + 5);
+        }
         T d;
         bool ok;
         if (creutz) {
             ok = creutz_try(w, qc, inv2a, &d);
         } else {
-            // kp_eval's arithmetic, with ln r3 from the partner lane
-            const T lam2 = mul_(neg_(fma_(Math<T>::cos2pi_sq(r2), ln3, lnv)), inv2a);
+            const T lam2 = mul_(neg_(fma_(mul_(cv, cv), ln3, lnv)), inv2a);
             d = add_(lam2, lam2);
+            const T r4 = u01<T>(w.w);
             ok = g < 4 && mul_(r4, r4) <= add_(T(1), neg_(lam2));
         }
         ok = ok && !done;
@@ -987,33 +1062,34 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
         }
         t0 += stride;
     }
-    // the new link, new_link's arithmetic spread over the group: lanes
-    // g0 .. g0+3 take sin and cos of phi, lane g0+4 sin(theta) and lane
-    // g0+5 |vector part| (the two square roots at once)
+    // the new link, new_link's arithmetic: lane 4 takes sin(theta) =
+    // sqrt((1 - cth)(1 + cth)) and lane 5 |vector part| =
+    // sqrt((delta + (-0)) (2 - delta)) in one stream
     const T one = T(1);
     const T cth = fma_(T(2), u18<T>(kd1), T(-1));
-    T sph = T(0), cph = T(0), root = T(0);
-    if (g < 4) {
-        Math<T>::sincos2pi(u18<T>(kd2), &sph, &cph);
-    } else {
-        root = Math<T>::sqrt_pos(g == 4 ? mul_(add_(one, neg_(cth)), add_(one, cth))
-                                        : mul_(delta, add_(T(2), neg_(delta))));
-    }
+    const bool l5 = g == 5;
+    const T root = Math<T>::sqrt_pos(
+        mul_(add_(l5 ? delta : one, l5 ? T(-0.0) : flip_sign(cth, SIGN)),
+             add_(l5 ? T(2) : one, l5 ? flip_sign(delta, SIGN) : cth)));
     const T sth = __shfl_sync(0xffffffffu, root, g0 + 4);
     const T vl = __shfl_sync(0xffffffffu, root, g0 + 5);
-    sph = __shfl_sync(0xffffffffu, sph, g0);
-    cph = __shfl_sync(0xffffffffu, cph, g0);
     const T vs = mul_(vl, sth);
     const Quat<T> X = {add_(one, neg_(delta)), mul_(vs, cph), mul_(vs, sph), mul_(vl, cth)};
+    // U = X A^dagger / |X A^dagger|: one component per lane, the norm on
+    // every lane, the scaled components gathered on lane 0
+    const T rc = qmul_nd_part(g & 3, X, A);
+    const Quat<T> r = {__shfl_sync(0xffffffffu, rc, g0), __shfl_sync(0xffffffffu, rc, g0 + 1),
+                       __shfl_sync(0xffffffffu, rc, g0 + 2), __shfl_sync(0xffffffffu, rc, g0 + 3)};
+    const T uc = mul_(rc, rsqrt_t(qnorm2(r)));
+    const Quat<T> unew = {__shfl_sync(0xffffffffu, uc, g0), __shfl_sync(0xffffffffu, uc, g0 + 1),
+                          __shfl_sync(0xffffffffu, uc, g0 + 2), __shfl_sync(0xffffffffu, uc, g0 + 3)};
     T plaq = T(0);
     uint32_t ntrial = 0, ncap = 0;
     if (act && g == 0) {
-        Quat<T> un;
+        Quat<T> un = unew;
         if (haar) {
             un = haar_from<T>(st.draw(TAG_DIRECTION, 0));
             tr = 0;
-        } else if (tr > 0) {
-            un = qnormalise(qmul_nd(X, A));
         }
         if (tr >= 0) {
             U.store(MU, p, i, un);

@@ -1,7 +1,8 @@
 // su2_math.cuh -- the transcendental pieces of the heat-bath draw.
 //
 // FP64 uses CUDA's accurate double functions (the reciprocal square root
-// through rsqrt, within 1 ulp, instead of a division by sqrt).  FP32 uses
+// through rsqrt, within 1 ulp, instead of a division by sqrt; the sine of
+// the direction's angle as a shifted cospi).  FP32 uses
 // short forms whose
 // error is bounded well inside the FP32 parity budget (2e-5 per link):
 //   ln u       for u on the uniform grid ((k + 1/2) 2^-23):
@@ -109,9 +110,14 @@ template <> struct Math<double> {
         const double c = cospi(mul_(2.0, r));
         return mul_(c, c);
     }
+    // sin x = cos(x - pi/2): both from cospi, on exact arguments (2 r and
+    // 2 r - 1/2 for r on the uniform grid), so that the cooperative kernel
+    // can take them in the same instruction stream as a trial's cos(2 pi r2)
     static __device__ __forceinline__ void sincos2pi(double r, double* s, double* c)
     {
-        sincospi(mul_(2.0, r), s, c);
+        const double x = mul_(2.0, r);
+        *c = cospi(x);
+        *s = cospi(add_(x, -0.5));
     }
     static __device__ __forceinline__ double sqrt_pos(double x) { return sqrt(x); }
     static __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }

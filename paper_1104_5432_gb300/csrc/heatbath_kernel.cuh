@@ -883,28 +883,22 @@ hb_pair_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 // ---------------------------------------------------------------------------
 // FP64, G lanes per link: the cooperative kernel for small lattices
 // ---------------------------------------------------------------------------
-// On GB300 an FP64 warp instruction costs the FP64 units the same time with
-// one active lane as with 32, and a small lattice (8^4: 2048 links per
-// phase = 64 warps of one link per thread) leaves most SM sub-partitions
-// without work.  Here G = 8 lanes share one link, and the phase takes as
-// long as one warp's stream of FP64 instructions, so the link's work is
-// laid out for few instructions, not few lanes: lanes 0..5 compute the six
+// On GB300 an FP64 warp instruction holds its SM sub-partition's FP64 unit
+// for ~76 cycles, with one active lane as with 32, and a dependent one
+// waits no longer than that; a small lattice (8^4: 2048 links per phase =
+// 64 warps of one link per thread) leaves most sub-partitions without
+// work.  Here G = 8 lanes share one link, and the phase takes about as long
+// as one warp's stream of FP64 instructions, so the link's work is laid
+// out for few instructions, not few lanes: lanes 0..5 compute the six
 // staple terms at once (upper and lower in one stream), the sums follow the
-// FP64 tree order above through shuffles, the lanes try Kennedy-Pendleton
-// trials t0 .. t0 + 3 at once (one logarithm per lane) while two of them
-// take the direction's cosine and sine in the trials' cospi stream, the
-// two square roots of the new link share one stream, and lanes 0..3 form
-// one component each of the final product.  The link takes the first
+// FP64 tree order above one component per lane, the lanes try
+// Kennedy-Pendleton trials t0 .. t0 + 3 at once (one logarithm per lane)
+// while two of them take the direction's cosine and sine in the trials'
+// cospi stream, the two square roots of the new link share one stream, and
+// lanes 0..3 form one component each of the final product.  The link takes the first
 // accepted trial of its own sequence, as every other kernel does, and each
 // value comes from the same operations as in the scalar kernels, so links
 // and trial counts are bit-identical to theirs.
-template <typename T>
-__device__ __forceinline__ Quat<T> shfl_quat(const Quat<T>& q, int src)
-{
-    return {__shfl_sync(0xffffffffu, q.a0, src), __shfl_sync(0xffffffffu, q.a1, src),
-            __shfl_sync(0xffffffffu, q.a2, src), __shfl_sync(0xffffffffu, q.a3, src)};
-}
-
 // x with its sign flipped where m has bit 63 set (an integer operation)
 __device__ __forceinline__ double flip_sign(double x, uint64_t m)
 {
@@ -980,13 +974,32 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             term = qmul_nd(qmul_nd(x, y), z);
         }
     }
-    // s_k = up_k + lo_k on lanes 2k and 2k+1, then A = (s_0 + s_1) + s_2
-    const Quat<T> other = shfl_quat(term, lane ^ 1);
-    const Quat<T> sk = (g & 1) ? qadd(other, term) : qadd(term, other);
-    const Quat<T> s0 = shfl_quat(sk, g0), s1 = shfl_quat(sk, g0 + 2), s2 = shfl_quat(sk, g0 + 4);
-    const Quat<T> s01 = qadd(s0, s1);
-    const Quat<T> A = qadd(s01, s2);
-    const Quat<T> P = MU == 1 ? s0 : (MU == 2 ? s01 : A);
+    // The tree s_k = up_k + lo_k, A = (s_0 + s_1) + s_2 one component per
+    // lane: the terms go through shared memory, lane (kk, c) = (g >> 2, g & 3)
+    // adds component c of s_kk and of s_2, lanes c and c + 4 swap theirs,
+    // and every lane then holds component c of s_0, s_1, s_01 and A (four
+    // additions in the stream instead of twelve).
+    __shared__ double terms[NT / G][6][4];
+    double* const tg6 = &terms[threadIdx.x / G][0][0];
+    if (g < 6) {
+        reinterpret_cast<double2*>(tg6 + 4 * g)[0] = make_double2(term.a0, term.a1);
+        reinterpret_cast<double2*>(tg6 + 4 * g)[1] = make_double2(term.a2, term.a3);
+    }
+    __syncwarp();
+    const int c = g & 3, kk = g >> 2;
+    const T skc = add_(tg6[4 * (2 * kk) + c], tg6[4 * (2 * kk + 1) + c]);
+    const T s2c = add_(tg6[16 + c], tg6[20 + c]);
+    const T swp = __shfl_sync(0xffffffffu, skc, lane ^ 4);
+    const T s0c = kk ? swp : skc, s1c = kk ? skc : swp;
+    const T s01c = add_(s0c, s1c);
+    const T Ac = add_(s01c, s2c);
+    auto gather = [&](T v) -> Quat<T> {
+        return {__shfl_sync(0xffffffffu, v, g0), __shfl_sync(0xffffffffu, v, g0 + 1),
+                __shfl_sync(0xffffffffu, v, g0 + 2), __shfl_sync(0xffffffffu, v, g0 + 3)};
+    };
+    const Quat<T> A = gather(Ac);
+    Quat<T> P = A;
+    if (PLAQ && MU < 3) P = gather(MU == 1 ? s0c : s01c);
 
     const T k2 = qnorm2(A);
     const T rk = Math<T>::rsqrt(k2);

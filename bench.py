@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-arms", action="store_true", help="skip the FP64 and batched arms")
     ap.add_argument("--profile-case",
                     choices=["f32_64", "f32_80", "f32_128", "f32_128x16", "f64_64", "f64_8",
-                             "scan"],
+                             "f32_8", "scan"],
                     help="run only a few sweeps of one lattice (for ncu captures) and exit")
     ap.add_argument("--launch-shape", type=int, default=None,
                     help="phase-kernel launch shape index instead of autotuning")
@@ -226,9 +226,10 @@ def layout_arg(args, su2):
 def shape_name(lat, idx=None):
     """The launch shape a handle runs (its table row by precision and link
     layout), by name."""
-    from paper_1104_5432_gb300.csrc_info import launch_shapes, row_name
+    from paper_1104_5432_gb300.csrc_info import row_name
+    from paper_1104_5432_gb300.csrc_info import shape_name as name_of
     row = row_name(lat.dtype, lat.link_layout())
-    return row, launch_shapes(row)[lat.launch_config()[0] if idx is None else idx]
+    return row, name_of(row, lat.launch_config()[0] if idx is None else idx)
 
 
 def gpu_arm(args, rank, world, local):
@@ -724,7 +725,8 @@ def profile_case(args):
         return
     Ns, Nt, dt = {"f32_64": (64, 64, su2.F32), "f32_80": (80, 80, su2.F32),
                   "f32_128": (128, 128, su2.F32), "f32_128x16": (128, 16, su2.F32),
-                  "f64_64": (64, 64, su2.F64), "f64_8": (8, 8, su2.F64)}[args.profile_case]
+                  "f64_64": (64, 64, su2.F64), "f64_8": (8, 8, su2.F64),
+                  "f32_8": (8, 8, su2.F32)}[args.profile_case]
     lat = su2.Lattice(Ns, Nt, dt, layout=None if dt == su2.F64 else layout_arg(args, su2))
     lat.set_launch_config(args.launch_shape or 0)
     lat.init(su2.HOT, WORKLOAD["init_seed"])

@@ -257,21 +257,39 @@ int su2_set_sweep(su2_lattice* lat, int l, uint64_t sweep);
  * SM, plain or y-slab traversal of the lattice, links per thread) compiled
  * for the phase kernel; shape 0 is the default.
  *   FP32:  0 256x4   1 128x8   2 64x16   3 32x32   4 256x4 slab  5 128x8 slab
- *          6 32x32 /2  7 32x32 /4  8 32x32 /8  9 32x32 /16  10 32x32 /2 P
- *          11 32x32 /1 P  12 32x32 slab /8  13 32x32 slab /16
+ *          6 32x32 /2  7 32x32 /4  8 32x32 /8  9 32x16 /4 staged
+ *          10 32x32 /2 P  11 32x32 /1 P  12 32x32 slab /8  13 32x32 slab /16
  *   FP64:  0 256x1   1 128x4   2 64x8   3 64x4   4 32x16   5 32x8
- *          6 32x16 /2  7 32x16 /4  8 32x16 /8  9 32x16 /16  10 32x16 /32
- *          11 64x8 /16  12 32x16 /2 P  13 32x16 /8 P
+ *          6 32x16 /2  7 32x16 /4  8 32x16 /8  9 32x16 /16  10 64x8 G8
+ *          11 32x16 G8  12 32x16 /2 P  13 32x16 /8 P
+ *   FP32 site pairs (SU2_LAYOUT_PAIRS; R counts pairs): 0 256x2  1 32x16
+ *          2 32x20  3 32x24  4 32x28  5 32x16 /2  6 32x20 /2  7 32x24 /2
+ *          8 32x24 /4  9 32x20 /4  10 32x24 /1 P  11 32x16 /1 P
+ *          12 32x24 slab /4  13 32x16 slab /4
  * (/R: R links per thread with a per-warp queue of rejected Kennedy-
  * Pendleton trials, retried 32 at a time; slab: large lattices walked in y
  * slabs so the +-t neighbours stay in L2; P, persistent: on a single
  * lattice only the blocks that fit on the GPU at once are launched, each
  * walking tiles of R rounds in grid-stride order with one queue drain at
- * the end; on a batch one block per tile, as the other shapes.)  Small blocks spread tiny
- * lattices over more SMs; several links per thread pay off on large ones.
- * Results never depend on the shape (the random streams are keyed by link
- * and sweep). */
+ * the end; on a batch one block per tile, as the other shapes; staged: the
+ * neighbour rows of a warp copied into shared memory by bulk copies; G8:
+ * eight lanes per link, the staple terms and trials in parallel, for small
+ * FP64 lattices.)  Small blocks spread tiny lattices over more SMs; several
+ * links per thread pay off on large ones.  Results never depend on the
+ * shape (the random streams are keyed by link and sweep). */
 #define SU2_NUM_LAUNCH_CONFIGS 14
+
+/* Launch index SU2_LAUNCH_CLUSTER (one past the shapes): a whole sweep in
+ * ONE launch of one thread-block cluster (up to 16 CTAs on 16 SMs) that
+ * holds all links of the lattice in its distributed shared memory, the
+ * eight phases separated by the hardware cluster barrier.  For one FP32
+ * lattice in the plain layout whose links fit the cluster's shared memory
+ * (8^4, 10^4, 12^4, ...: Vh = V/2 divisible by the cluster size and
+ * 8 Vh/S links of 16 B per CTA); elsewhere su2_set_launch_config refuses it
+ * with SU2_E_INVAL, and su2_autotune times it only where it applies.  The
+ * links are bit-identical to the shapes'; the single-phase entry point
+ * (su2_heatbath_phase) keeps using the last shape. */
+#define SU2_LAUNCH_CLUSTER 14
 
 /* Times every launch shape on this handle's lattices (whole sweeps with the
  * fused plaquette, replayed as in su2_heatbath, ~20 ms per shape in each of
@@ -296,8 +314,10 @@ int su2_autotune(su2_lattice* lat, int* chosen);
  * still left in the tuning seed's hot start). */
 int su2_autotune_beta(su2_lattice* lat, const double* betas, int* chosen);
 
-/* Select a launch shape by index (0 .. SU2_NUM_LAUNCH_CONFIGS-1) / read
- * the current one with its threads per block and minimum blocks per SM. */
+/* Select a launch shape by index (0 .. SU2_NUM_LAUNCH_CONFIGS-1, or
+ * SU2_LAUNCH_CLUSTER once memory is bound) / read the current one with its
+ * threads per block and minimum blocks per SM (for the cluster sweep: the
+ * threads per CTA and the CTAs in the cluster). */
 int su2_set_launch_config(su2_lattice* lat, int cfg);
 int su2_get_launch_config(const su2_lattice* lat, int* cfg, int* threads, int* min_blocks);
 

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsu2gb300.so")
 SOURCES = ["heatbath.cu", "observables.cu", "links.cu", "api.cu", "plaquette_static.cu",
-           "selftest.cu"]
+           "selftest.cu", "cluster.cu"]
 # heatbath_shapes.cu once per pair of launch shapes and row of the 14-entry
 # table in csrc/su2_internal.h (FP32, FP64, FP32 site pairs): (object name,
 # defines, flags).

@@ -18,6 +18,9 @@
 
 using namespace su2;
 
+static_assert(SU2_NUM_LAUNCH_CONFIGS == NUM_LAUNCH_CFG, "shape count of the header");
+static_assert(SU2_LAUNCH_CLUSTER == CFG_CLUSTER, "cluster launch index of the header");
+
 namespace {
 
 thread_local std::string g_err;
@@ -90,6 +93,11 @@ struct su2_lattice {
     size_t off_pstart_cfg[NUM_LAUNCH_CFG] = {};
     uint32_t max_phase_blocks = 0;
     int cfg = 0;                    // active launch shape
+    // whole sweeps in one thread-block cluster (launch index CFG_CLUSTER):
+    // on, and the cluster geometry (cluster_ok: -1 not yet known, 0 / 1)
+    bool cluster = false;
+    int cluster_ok = -1;
+    ClusterGeom cgeom{};
     std::string tune_key;
     std::vector<int> ysplit;        // y slabs per lattice (slab launch shapes)
     bool hybrid = false;            // Creutz/Kennedy-Pendleton sampler variant in use
@@ -119,6 +127,8 @@ struct su2_lattice {
     // parallel branch, and the measurement alone (after the last sweep)
     cudaGraphExec_t measure_graph[NUM_LAUNCH_CFG][2] = {};
     cudaGraphExec_t measure_tail = nullptr;
+    // the same two for the cluster sweep
+    cudaGraphExec_t cluster_graph[2] = {}, cluster_measure_graph[2] = {};
     Ctx ctx{};                      // non-phase kernels
     Ctx cfg_ctx[NUM_LAUNCH_CFG]{};  // phase kernels and sweep end, per launch shape
 
@@ -144,9 +154,19 @@ struct su2_lattice {
                 }
     }
 
+    static void drop2(cudaGraphExec_t (&gs)[2])
+    {
+        for (auto& g : gs)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
+
     void drop_measure_graphs()
     {
         drop(measure_graph);
+        drop2(cluster_measure_graph);
         if (measure_tail) {
             cudaGraphExecDestroy(measure_tail);
             measure_tail = nullptr;
@@ -156,6 +176,7 @@ struct su2_lattice {
     void drop_graphs()
     {
         drop(sweep_graph);
+        drop2(cluster_graph);
         drop_measure_graphs();
         measure_rmax = -1;
     }
@@ -375,6 +396,14 @@ int record_measure(su2_lattice* L, int rmax, cudaStream_t s)
 // leave alone, so it overlaps them and joins before phase (3, 0).
 int record_sweep(su2_lattice* L, bool plaq, int rmax, cudaStream_t s)
 {
+    if (L->cluster) {
+        // the cluster kernel holds all links for the whole sweep: the
+        // previous sweep's result is measured before it, not beside it
+        if (rmax >= 0)
+            if (int rc = record_measure(L, rmax, s)) return rc;
+        SU2_CUDA(launch_cluster_sweep(L->cfg_ctx[L->cfg], L->cgeom, plaq, L->hybrid, s));
+        return SU2_OK;
+    }
     const bool branch = rmax >= 0;
     if (branch) {
         SU2_CUDA(cudaEventRecord(L->fork_ev, s));
@@ -432,8 +461,10 @@ void set_measure_rmax(su2_lattice* L, int rmax)
 int sweep_graph(su2_lattice* L, bool plaq, int rmax, cudaGraphExec_t* exec)
 {
     if (rmax >= 0) set_measure_rmax(L, rmax);
-    cudaGraphExec_t& g = rmax >= 0 ? L->measure_graph[L->cfg][plaq ? 1 : 0]
-                                   : L->sweep_graph[L->cfg][plaq ? 1 : 0];
+    cudaGraphExec_t& g = L->cluster ? (rmax >= 0 ? L->cluster_measure_graph[plaq ? 1 : 0]
+                                                 : L->cluster_graph[plaq ? 1 : 0])
+                         : rmax >= 0 ? L->measure_graph[L->cfg][plaq ? 1 : 0]
+                                     : L->sweep_graph[L->cfg][plaq ? 1 : 0];
     if (!g) {
         if (int rc = capture_graph(
                 L, [&](cudaStream_t s) { return record_sweep(L, plaq, rmax, s); }, &g))
@@ -472,6 +503,40 @@ int sync_status(su2_lattice* L)
             return fail(SU2_E_TRIALS, "Kennedy-Pendleton trial cap (%d) hit; links kept", KP_CAP);
     }
     return SU2_OK;
+}
+
+// Whether the whole-sweep cluster kernel applies to this handle: one FP32
+// lattice in the plain layout whose links fit the shared memory of one
+// cluster that the GPU can hold (decided once per binding and layout).
+bool cluster_available(su2_lattice* L)
+{
+    if (L->cluster_ok < 0) {
+        L->cluster_ok = 0;
+        if (L->row == ROW_F32 && L->n == 1 && L->device >= 0) {
+            DeviceGuard dg(L->device);
+            ClusterGeom g;
+            if (cluster_geometry((uint32_t)(L->V[0] / 2), L->dtype == SU2_F32, L->n, &g) &&
+                cluster_launchable(g)) {
+                L->cgeom = g;
+                L->cluster_ok = 1;
+            }
+        }
+    }
+    return L->cluster_ok == 1;
+}
+
+// select launch index cfg (0 .. NUM_LAUNCH_CFG - 1, or CFG_CLUSTER)
+bool select_cfg(su2_lattice* L, int cfg)
+{
+    if (cfg == CFG_CLUSTER) {
+        if (!cluster_available(L)) return false;
+        L->cluster = true;  // L->cfg stays: the single-phase entry point uses it
+        return true;
+    }
+    if (cfg < 0 || cfg >= NUM_LAUNCH_CFG) return false;
+    L->cluster = false;
+    L->cfg = cfg;
+    return true;
 }
 
 int heatbath_impl(su2_lattice* L, const double* betas, double beta, int nsweeps,
@@ -877,10 +942,11 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
     // (at the default tuning coupling)
     lat->tune_key = tune_key(lat, dev, beta_band(lat, nullptr, TUNE_BETA));
     lat->cfg = 0;
+    lat->cluster = false;
+    lat->cluster_ok = -1;
     if (const char* path = getenv("SU2_AUTOTUNE_CACHE")) {
         int cached = -1;
-        if (cache_lookup(path, lat->tune_key, &cached) && cached >= 0 && cached < NUM_LAUNCH_CFG)
-            lat->cfg = cached;
+        if (cache_lookup(path, lat->tune_key, &cached)) select_cfg(lat, cached);
     }
     return SU2_OK;
 }
@@ -902,6 +968,8 @@ int su2_set_link_layout(su2_lattice* lat, int layout_code)
         return fail(SU2_E_INVAL, "bad link layout %d", layout_code);
     }
     lat->cfg = 0;
+    lat->cluster = false;
+    lat->cluster_ok = -1;
     return layout(lat);
 }
 
@@ -1111,9 +1179,8 @@ int su2_autotune_beta(su2_lattice* lat, const double* betas, int* chosen)
     // a choice cached for this GPU, shapes and coupling band: no timing
     if (const char* path = getenv("SU2_AUTOTUNE_CACHE")) {
         int cached = -1;
-        if (cache_lookup(path, lat->tune_key, &cached) && cached >= 0 && cached < NUM_LAUNCH_CFG) {
+        if (cache_lookup(path, lat->tune_key, &cached) && select_cfg(lat, cached)) {
             if (int r2 = sync_status(lat)) return r2;
-            lat->cfg = cached;
             if (chosen) *chosen = cached;
             return SU2_OK;
         }
@@ -1123,13 +1190,16 @@ int su2_autotune_beta(su2_lattice* lat, const double* betas, int* chosen)
     SU2_CUDA(cudaEventCreate(&e0));
     SU2_CUDA(cudaEventCreate(&e1));
     const int saved = lat->cfg;
-    double best_ms[NUM_LAUNCH_CFG];
-    int reps[NUM_LAUNCH_CFG];
+    const bool saved_cluster = lat->cluster;
+    constexpr int NC = NUM_LAUNCH_CFG + 1;  // the shapes and the cluster sweep
+    double best_ms[NC];
+    int reps[NC];
     int rc = SU2_OK;
     // Time what production runs: whole sweeps (graph replay, fused
     // plaquette), shapes interleaved over three rounds, best round kept.
     auto time_sweeps = [&](int k, int n, float* ms) -> int {
-        lat->cfg = k;
+        lat->cluster = k == CFG_CLUSTER;
+        if (k != CFG_CLUSTER) lat->cfg = k;
         cudaGraphExec_t g = nullptr;
         if (int r = sweep_graph(lat, true, -1, &g)) return r;
         cudaError_t e = cudaEventRecord(e0, s);
@@ -1142,9 +1212,10 @@ int su2_autotune_beta(su2_lattice* lat, const double* betas, int* chosen)
     // slab shapes only matter when some lattice is walked in slabs
     bool any_slab = false;
     for (int l = 0; l < lat->n; ++l) any_slab = any_slab || lat->ysplit[l] > 1;
-    bool cand[NUM_LAUNCH_CFG];
+    bool cand[NC];
     for (int k = 0; k < NUM_LAUNCH_CFG; ++k) cand[k] = any_slab || !LAUNCH_CFG[lat->row][k].slab;
-    const int ncand = NUM_LAUNCH_CFG;
+    cand[CFG_CLUSTER] = cluster_available(lat);
+    const int ncand = NC;
     for (int k = 0; k < ncand && rc == SU2_OK; ++k) {
         if (!cand[k]) continue;
         float ms = 0.f;
@@ -1164,6 +1235,7 @@ int su2_autotune_beta(su2_lattice* lat, const double* betas, int* chosen)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     lat->cfg = saved;
+    lat->cluster = saved_cluster;
     if (rc != SU2_OK) return rc;
     int best = 0;
     for (int k = 1; k < ncand; ++k)
@@ -1175,7 +1247,7 @@ int su2_autotune_beta(su2_lattice* lat, const double* betas, int* chosen)
     for (int l = 0; l < lat->n; ++l)
         SU2_CUDA(launch_init(lat->ctx, lat->dtype, l, (uint32_t)lat->V[l], SU2_HOT, tune_seed + l, s));
     if (int r2 = sync_status(lat)) return r2;
-    lat->cfg = best;
+    select_cfg(lat, best);
     if (const char* path = getenv("SU2_AUTOTUNE_CACHE"))
         if (!cache_store(path, lat->tune_key, best, best_ms[best]))
             return fail(SU2_E_INVAL, "cannot append to autotune cache %s", path);
@@ -1186,15 +1258,26 @@ int su2_autotune_beta(su2_lattice* lat, const double* betas, int* chosen)
 int su2_set_launch_config(su2_lattice* lat, int cfg)
 {
     if (int rc = check_handle(lat, false)) return rc;
-    if (cfg < 0 || cfg >= NUM_LAUNCH_CFG)
-        return fail(SU2_E_INVAL, "launch config %d outside 0..%d", cfg, NUM_LAUNCH_CFG - 1);
-    lat->cfg = cfg;  // graphs are kept per launch shape
+    if (cfg == CFG_CLUSTER && !lat->bound())
+        return fail(SU2_E_INVAL, "the cluster sweep is chosen once memory is bound");
+    if (!select_cfg(lat, cfg)) {  // graphs are kept per launch shape
+        if (cfg == CFG_CLUSTER)
+            return fail(SU2_E_INVAL, "the cluster sweep needs one FP32 lattice in the plain "
+                                     "layout whose links fit one thread-block cluster");
+        return fail(SU2_E_INVAL, "launch config %d outside 0..%d", cfg, CFG_CLUSTER);
+    }
     return SU2_OK;
 }
 
 int su2_get_launch_config(const su2_lattice* lat, int* cfg, int* threads, int* min_blocks)
 {
     if (int rc = check_handle(lat, false)) return rc;
+    if (lat->cluster) {
+        if (cfg) *cfg = CFG_CLUSTER;
+        if (threads) *threads = lat->cgeom.threads;
+        if (min_blocks) *min_blocks = lat->cgeom.S;
+        return SU2_OK;
+    }
     if (cfg) *cfg = lat->cfg;
     if (threads) *threads = LAUNCH_CFG[lat->row][lat->cfg].threads;
     if (min_blocks) *min_blocks = LAUNCH_CFG[lat->row][lat->cfg].min_blocks;
@@ -1272,7 +1355,7 @@ int su2_tune_cache_lookup(const char* path, const char* key, int* cfg)
 int su2_tune_cache_store(const char* path, const char* key, int cfg, double ms)
 {
     if (!path || !key) return fail(SU2_E_INVAL, "null argument");
-    if (cfg < 0 || cfg >= NUM_LAUNCH_CFG) return fail(SU2_E_INVAL, "bad config");
+    if (cfg < 0 || cfg > CFG_CLUSTER) return fail(SU2_E_INVAL, "bad config");
     return cache_store(path, key, cfg, ms) ? SU2_OK : fail(SU2_E_INVAL, "cannot write %s", path);
 }
 

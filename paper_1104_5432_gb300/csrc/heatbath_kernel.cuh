@@ -94,8 +94,8 @@ __device__ __forceinline__ constexpr int nu_of(int k) { return k + (k >= MU ? 1 
 // z = f^dagger (conjugation is an exact sign flip), so that lanes computing
 // upper and lower terms side by side run one instruction stream (the
 // cooperative kernel).
-template <typename T>
-__device__ __forceinline__ Quat<T> staple_term(const Links<T>& U, int mu, int nu, int p, uint32_t i,
+template <typename T, typename LT>
+__device__ __forceinline__ Quat<T> staple_term(const LT& U, int mu, int nu, int p, uint32_t i,
                                                const int* hp, const int* hm, bool lower)
 {
     const int q = p ^ 1;
@@ -111,8 +111,10 @@ __device__ __forceinline__ Quat<T> staple_term(const Links<T>& U, int mu, int nu
     return qmul_nd(qmul_nd(qdag(d), e), qdag(f));
 }
 
-template <typename T, int MU, bool PLAQ>
-__device__ __forceinline__ void staple_sum(const Links<T>& U, const EoSite& s, uint32_t i, int p,
+// (U: any link source with load(mu, parity, eo) -- global memory, or the
+// distributed shared memory of a cluster)
+template <typename T, int MU, bool PLAQ, typename LT>
+__device__ __forceinline__ void staple_sum(const LT& U, const EoSite& s, uint32_t i, int p,
                                            Quat<T>& A, Quat<T>& P)
 {
     int hp[4], hm[4];
@@ -122,8 +124,8 @@ __device__ __forceinline__ void staple_sum(const Links<T>& U, const EoSite& s, u
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int nu = nu_of<MU>(k);
-            sk[k] = qadd(staple_term(U, MU, nu, p, i, hp, hm, false),
-                         staple_term(U, MU, nu, p, i, hp, hm, true));
+            sk[k] = qadd(staple_term<T>(U, MU, nu, p, i, hp, hm, false),
+                         staple_term<T>(U, MU, nu, p, i, hp, hm, true));
         }
         const Quat<T> s01 = qadd(sk[0], sk[1]);
         A = qadd(s01, sk[2]);
@@ -249,6 +251,60 @@ __device__ __forceinline__ void warp_totals(const Ctx& ctx, int l, uint32_t blk0
     }
 }
 
+// One link update, U_mu(x) at storage index i of parity p in sweep sw: the
+// staple sum, the Kennedy-Pendleton (or Creutz) draw and the new link *un.
+// Returns the trials used (> 0), 0 for the Haar branch (alpha -> 0) or -1
+// when the cap was hit (*un then undefined); *P is the staple part closing
+// the plaquettes (PLAQ).
+template <typename T, int MU, bool PLAQ, bool HYB, typename LT>
+__device__ __forceinline__ int32_t update_link(const LT& U, const LatDesc& D, const EoSite& s,
+                                               uint32_t i, int p, uint64_t sw, Quat<T>* un,
+                                               Quat<T>* P)
+{
+    Quat<T> A;
+    staple_sum<T, MU, PLAQ>(U, s, i, p, A, *P);
+
+    // alpha = beta k and 1/(2 alpha) from one reciprocal square root of k^2
+    const T k2 = qnorm2(A);
+    const T rk = Math<T>::rsqrt(k2);
+    const T beta = beta_of<T>(D);
+    const T alpha = mul_(mul_(beta, k2), rk);
+    const Stream st{(uint32_t)D.seed, (uint32_t)(D.seed >> 32), s.lex() * 4u + MU,
+                    (uint32_t)sw, (uint32_t)(sw >> 32)};
+
+    if (!(alpha >= alpha_haar<T>())) {
+        // alpha -> 0 limit of the conditional law (zero staple or beta = 0)
+        *un = haar_from<T>(st.draw(TAG_DIRECTION, 0));
+        return 0;
+    }
+    const T inv2a = inv_two_alpha<T>(D, rk, beta);
+    T delta = T(0);
+    int32_t tr = -1;
+    // trial 0 also carries the direction in the low 9 bits of its words
+    const U4 w = st.draw(TAG_TRIAL, 0u);
+    const uint32_t kd1 = spare_bits_1(w), kd2 = spare_bits_2(w);
+    if (HYB && alpha < creutz_of<T>(D)) {
+        const T qc = creutz_qc(alpha);
+        for (int t = 0; t < KP_CAP; ++t) {
+            if (creutz_try(t == 0 ? w : st.draw(TAG_TRIAL, (uint32_t)t), qc, inv2a, &delta)) {
+                tr = t + 1;
+                break;
+            }
+        }
+    } else if (kp_try(w, inv2a, &delta)) {
+        tr = 1;
+    } else {
+        for (int t = 1; t < KP_CAP; ++t) {
+            if (kp_try(st.draw(TAG_TRIAL, (uint32_t)t), inv2a, &delta)) {
+                tr = t + 1;
+                break;
+            }
+        }
+    }
+    if (tr > 0) *un = new_link(delta, kd1, kd2, A);
+    return tr;
+}
+
 // ---------------------------------------------------------------------------
 // one link per thread
 // ---------------------------------------------------------------------------
@@ -259,7 +315,7 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const int l = lattice_of_block(ctx.phase_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
     const uint32_t Vh = D.Vh;
-    const uint32_t blk0 = __ldg(ctx.phase_start + l);
+    const uint32_t blk0 = first_block(ctx.phase_start, l);
     const uint32_t j = (blockIdx.x - blk0) * NT + threadIdx.x;  // traversal position
     const Links<T> U(ctx.links, D, ctx.status);
 
@@ -269,51 +325,8 @@ hb_phase_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     if (j < Vh) {
         uint32_t i = j;  // storage index of the site
         const EoSite s = SLAB ? EoSite::from_slab(D, j, p, &i) : EoSite(D, j, p);
-        Quat<T> A, P;
-        staple_sum<T, MU, PLAQ>(U, s, i, p, A, P);
-
-        // alpha = beta k and 1/(2 alpha) from one reciprocal square root of k^2
-        const T k2 = qnorm2(A);
-        const T rk = Math<T>::rsqrt(k2);
-        const T beta = beta_of<T>(D);
-        const T alpha = mul_(mul_(beta, k2), rk);
-        const uint64_t sw = D.sweep;
-        const Stream st{(uint32_t)D.seed, (uint32_t)(D.seed >> 32), s.lex() * 4u + MU,
-                        (uint32_t)sw, (uint32_t)(sw >> 32)};
-
-        Quat<T> un;
-        int32_t tr;
-        if (!(alpha >= alpha_haar<T>())) {
-            // alpha -> 0 limit of the conditional law (zero staple or beta = 0)
-            un = haar_from<T>(st.draw(TAG_DIRECTION, 0));
-            tr = 0;
-        } else {
-            const T inv2a = inv_two_alpha<T>(D, rk, beta);
-            T delta = T(0);
-            tr = -1;
-            // trial 0 also carries the direction in the low 9 bits of its words
-            const U4 w = st.draw(TAG_TRIAL, 0u);
-            const uint32_t kd1 = spare_bits_1(w), kd2 = spare_bits_2(w);
-            if (HYB && alpha < creutz_of<T>(D)) {
-                const T qc = creutz_qc(alpha);
-                for (int t = 0; t < KP_CAP; ++t) {
-                    if (creutz_try(t == 0 ? w : st.draw(TAG_TRIAL, (uint32_t)t), qc, inv2a, &delta)) {
-                        tr = t + 1;
-                        break;
-                    }
-                }
-            } else if (kp_try(w, inv2a, &delta)) {
-                tr = 1;
-            } else {
-                for (int t = 1; t < KP_CAP; ++t) {
-                    if (kp_try(st.draw(TAG_TRIAL, (uint32_t)t), inv2a, &delta)) {
-                        tr = t + 1;
-                        break;
-                    }
-                }
-            }
-            if (tr > 0) un = new_link(delta, kd1, kd2, A);
-        }
+        Quat<T> un, P;
+        const int32_t tr = update_link<T, MU, PLAQ, HYB>(U, D, s, i, p, D.sweep, &un, &P);
         if (tr >= 0) {
             U.store(MU, p, i, un);
         } else {
@@ -476,7 +489,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const int l = lattice_of_block(ctx.phase_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
     const uint32_t Vh = D.Vh;
-    const uint32_t blk0 = __ldg(ctx.phase_start + l);
+    const uint32_t blk0 = first_block(ctx.phase_start, l);
     // tiles of NT R positions, one per block; a persistent shape's nb blocks
     // take them in grid-stride order (nb <= the tile count), and a block's
     // queue carries over from tile to tile
@@ -711,7 +724,7 @@ hb_pair_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const int l = lattice_of_block(ctx.phase_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
     const uint32_t Vh = D.Vh, Vq = D.Vq;
-    const uint32_t blk0 = __ldg(ctx.phase_start + l);
+    const uint32_t blk0 = first_block(ctx.phase_start, l);
     // tiles of NT R pairs, as the queued kernel's tiles of links
     const uint32_t nb = PERSIST ? __ldg(ctx.phase_start + l + 1) - blk0 : 0u;
     const uint32_t ntiles = PERSIST ? (Vq + NT * R - 1) / (NT * R) : 0u;
@@ -943,11 +956,15 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const int l = lattice_of_block(ctx.phase_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
     const uint32_t Vh = D.Vh;
-    const uint32_t blk0 = __ldg(ctx.phase_start + l);
+    const uint32_t blk0 = first_block(ctx.phase_start, l);
     const int lane = threadIdx.x & 31, g = lane & (G - 1), g0 = lane & ~(G - 1);
     const uint32_t j = (blockIdx.x - blk0) * (NT / G) + threadIdx.x / G;  // link position
     const bool act = j < Vh;  // uniform within the group
     const Links<T> U(ctx.links, D, ctx.status);
+    // the per-call values, loaded up front (they are needed only after the
+    // staple, and their loads then wait on nothing)
+    const uint64_t sw = D.sweep, seed = D.seed;
+    const T beta = beta_of<T>(D), hib = D.half_inv_beta;
 
     Quat<T> term = {T(0), T(0), T(0), T(0)};
     uint32_t key = 0;
@@ -1003,13 +1020,11 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
 
     const T k2 = qnorm2(A);
     const T rk = Math<T>::rsqrt(k2);
-    const T beta = beta_of<T>(D);
     const T alpha = mul_(mul_(beta, k2), rk);
-    const uint64_t sw = D.sweep;
-    const Stream st{(uint32_t)D.seed, (uint32_t)(D.seed >> 32), key, (uint32_t)sw,
+    const Stream st{(uint32_t)seed, (uint32_t)(seed >> 32), key, (uint32_t)sw,
                     (uint32_t)(sw >> 32)};
     const bool haar = !(alpha >= alpha_haar<T>());
-    const T inv2a = inv_two_alpha<T>(D, rk, beta);
+    const T inv2a = mul_(rk, hib);  // inv_two_alpha's product
     const bool creutz = HYB && alpha < creutz_of<T>(D);
     const T qc = creutz ? creutz_qc(alpha) : T(0);
 

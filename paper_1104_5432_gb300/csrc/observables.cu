@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(TPB) plaquette_kernel(Ctx ctx)
     __shared__ T s_warp[TPB / 32];
     const int l = lattice_of_block(ctx.site_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
-    const uint32_t lex = (blockIdx.x - __ldg(ctx.site_start + l)) * TPB + threadIdx.x;
+    const uint32_t lex = (blockIdx.x - first_block(ctx.site_start, l)) * TPB + threadIdx.x;
     T acc = T(0);
     if (lex < D.V) {
         const AnyLinks<T> U(ctx.links, D, ctx.status);
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(TPB) polyakov_kernel(Ctx ctx)
     __shared__ T s_warp[TPB / 32];
     const int l = lattice_of_block(ctx.spat_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
-    const uint32_t sidx = (blockIdx.x - __ldg(ctx.spat_start + l)) * TPB + threadIdx.x;
+    const uint32_t sidx = (blockIdx.x - first_block(ctx.spat_start, l)) * TPB + threadIdx.x;
     T L = T(0);
     if (sidx < (uint32_t)D.Vs) {
         const AnyLinks<T> U(ctx.links, D, ctx.status);
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(TPB) correlator_kernel(Ctx ctx, int rmax)
     __shared__ T s_rows[MAX_RMAX + 1][TPB / 32];
     const int l = lattice_of_block(ctx.spat_start, ctx.n, blockIdx.x);
     const LatDesc& D = ctx.desc[l];
-    const uint32_t sidx = (blockIdx.x - __ldg(ctx.spat_start + l)) * TPB + threadIdx.x;
+    const uint32_t sidx = (blockIdx.x - first_block(ctx.spat_start, l)) * TPB + threadIdx.x;
     const bool act = sidx < (uint32_t)D.Vs;
     const T* F = reinterpret_cast<const T*>(ctx.field) + D.field_off;
     uint32_t x = 0, y = 0, z = 0;

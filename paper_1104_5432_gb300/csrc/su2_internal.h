@@ -142,6 +142,14 @@ struct Ctx {
     uint32_t phase_wpb;            // warps per phase block of this launch shape
 };
 
+// first grid block of lattice l; lattice 0 starts at block 0, so a single
+// lattice's kernels need no load (one global-memory round trip fewer before
+// the first link load)
+__device__ __forceinline__ uint32_t first_block(const uint32_t* start, int l)
+{
+    return l == 0 ? 0u : __ldg(start + l);
+}
+
 // lattice owning grid block b: largest l with start[l] <= b
 __device__ __forceinline__ int lattice_of_block(const uint32_t* start, int n, uint32_t b)
 {
@@ -168,6 +176,22 @@ cudaError_t launch_set_params(const Ctx& c, const ParamChunk& pc, cudaStream_t s
 cudaError_t launch_phase(const Ctx& c, int row, int cfg, int mu, int parity, bool plaq,
                          int32_t* dbg_trials, bool hybrid, cudaStream_t s);
 cudaError_t launch_sweep_end(const Ctx& c, bool plaq, cudaStream_t s);
+
+// The whole sweep of a small single FP32 lattice in one thread-block
+// cluster (cluster.cu): launch index NUM_LAUNCH_CFG.
+constexpr int CFG_CLUSTER = NUM_LAUNCH_CFG;
+constexpr int CLUSTER_MAX = 16;  // CTAs per cluster (16 needs the non-portable opt-in)
+struct ClusterGeom {
+    int S = 0;          // CTAs in the cluster
+    uint32_t C = 0;     // links per (mu, parity) per CTA: Vh / S
+    FastDiv div_c{};
+    int threads = 0;    // per CTA
+    size_t smem = 0;    // dynamic shared memory per CTA
+};
+bool cluster_geometry(uint32_t Vh, int dtype_f32, int n, ClusterGeom* g);
+bool cluster_launchable(const ClusterGeom& g);
+cudaError_t launch_cluster_sweep(const Ctx& c, const ClusterGeom& g, bool plaq, bool hyb,
+                                 cudaStream_t s);
 cudaError_t launch_init(const Ctx& c, int dtype, int l, uint32_t V, int hot, uint64_t seed,
                         cudaStream_t s);
 // canonical values in double (cdtype 1) or float (cdtype 0); pairs_whole:

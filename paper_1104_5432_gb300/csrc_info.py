@@ -25,11 +25,20 @@ _F32P = [(256, 2, False, 1, False), (32, 16, False, 1, False), (32, 20, False, 1
          (32, 20, False, 4, False), (32, 24, False, 1, True), (32, 16, False, 1, True),
          (32, 24, True, 4, False), (32, 16, True, 4, False)]
 ROWS = {"f32": _F32, "f64": _F64, "f32pairs": _F32P}
+# launch index 14: the whole sweep in one thread-block cluster (FP32 only)
+CLUSTER = 14
+CLUSTER_NAME = ("one thread-block cluster (up to 16 CTAs), whole lattice in distributed "
+                "shared memory, one launch per sweep")
 
 
 def row_name(dtype: int, layout: int) -> str:
     """The shape-table row a handle uses (dtype 0/1, layout 0 plain / 1 pairs)."""
     return "f64" if dtype == 1 else ("f32pairs" if layout == 1 else "f32")
+
+
+def shape_name(row, idx):
+    """Name of launch index idx of a row: a shape, or the cluster sweep."""
+    return CLUSTER_NAME if idx == CLUSTER else launch_shapes(row)[idx]
 
 
 def launch_shapes(row):

@@ -30,6 +30,10 @@ F32_PAIRS = 2  # su2_plaquette_static: FP32 links in the site-pair layout
 LAYOUT_PLAIN, LAYOUT_PAIRS = 0, 1
 COLD, HOT = 0, 1
 KP_CAP = 4096
+NUM_LAUNCH_CONFIGS = 14
+# launch index of the whole-sweep thread-block-cluster kernel (one small FP32
+# lattice in the plain layout; include/su2.h SU2_LAUNCH_CLUSTER)
+LAUNCH_CLUSTER = 14
 
 _lock = threading.Lock()
 _lib = None

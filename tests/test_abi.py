@@ -105,7 +105,8 @@ def test_tune_cache_round_trip(tmp_path):
     assert lib.su2_tune_cache_store(path, b"gpu|f32|n1|V256|00ff", 3, 0.2) == 0
     assert lib.su2_tune_cache_lookup(path, b"gpu|f32|n1|V256|00ff", C.byref(cfg)) == 1
     assert cfg.value == 3
-    assert lib.su2_tune_cache_store(path, b"k", 14, 0.1) == su2.SU2_E_INVAL
+    # 14 is the cluster sweep's launch index; past it nothing
+    assert lib.su2_tune_cache_store(path, b"k", 15, 0.1) == su2.SU2_E_INVAL
 
 
 def test_tune_key_and_launch_config_host_side():
@@ -134,9 +135,24 @@ def test_tune_key_and_launch_config_host_side():
     assert lib.su2_set_launch_config(h, 1) == 0
     assert lib.su2_get_launch_config(h, C.byref(cfg), C.byref(thr), C.byref(mb)) == 0
     assert (cfg.value, thr.value, mb.value) == (1, 128, 8)
-    assert lib.su2_set_launch_config(h, 14) == su2.SU2_E_INVAL
+    # the cluster sweep: never on a batch, and chosen only once memory is bound
+    assert lib.su2_set_launch_config(h, su2.LAUNCH_CLUSTER) == su2.SU2_E_INVAL
+    assert lib.su2_set_launch_config(h, 15) == su2.SU2_E_INVAL
     assert lib.su2_set_launch_config(h, -1) == su2.SU2_E_INVAL
     lib.su2_lattice_destroy(h)
+
+
+def test_cluster_launch_index_mirrors_the_header():
+    """SU2_LAUNCH_CLUSTER of include/su2.h is the Python and shape-table
+    mirrors' index, one past the shapes."""
+    import re
+    from paper_1104_5432_gb300 import csrc_info
+    text = open(os.path.join(ROOT, "include", "su2.h")).read()
+    defs = dict(re.findall(r"#define (SU2_\w+) (\d+)", text))
+    assert int(defs["SU2_NUM_LAUNCH_CONFIGS"]) == su2.NUM_LAUNCH_CONFIGS == 14
+    assert int(defs["SU2_LAUNCH_CLUSTER"]) == su2.LAUNCH_CLUSTER == csrc_info.CLUSTER == 14
+    assert "cluster" in csrc_info.shape_name("f32", 14)
+    assert csrc_info.shape_name("f32", 3) == csrc_info.launch_shapes("f32")[3]
 
 
 def test_launch_shape_mirror_matches_library():

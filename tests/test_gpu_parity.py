@@ -531,6 +531,75 @@ def test_every_launch_shape_gives_identical_results(dtype):
             np.testing.assert_allclose(plaq, ref_plaq, rtol=0, atol=1e-7)
 
 
+@pytest.mark.parametrize("Ns,Nt", [(8, 8), (12, 12), (10, 10), (8, 4), (6, 8)])
+def test_cluster_sweep_matches_the_shapes(Ns, Nt):
+    """The whole-sweep cluster kernel (the lattice in the distributed shared
+    memory of one thread-block cluster, the phases separated by the cluster
+    barrier) gives the shapes' links bit for bit, the same trial counts and
+    sweep counter, the fused plaquette to the FP32 grouping, and, in measured
+    runs, the same Polyakov sums (the measurements read the same links).
+    10^4 takes a cluster of 8 CTAs (Vh = 5000), the others 16."""
+    beta, seed = 2.3, 11
+    ref = lattice(Ns, Nt, su2.F32)
+    ref.init(su2.HOT, 5)
+    p_ref = ref.heatbath(beta, 3, seed)
+    lat = lattice(Ns, Nt, su2.F32)
+    lat.set_launch_config(su2.LAUNCH_CLUSTER)
+    cfg, threads, ctas = lat.launch_config()
+    assert cfg == su2.LAUNCH_CLUSTER and ctas == (8 if Ns == 10 else 16)
+    assert (Ns ** 3 * Nt // 2) % ctas == 0 and threads in (128, 1024)
+    lat.init(su2.HOT, 5)
+    p = lat.heatbath(beta, 3, seed)
+    np.testing.assert_array_equal(lat.get_links(), ref.get_links())
+    assert lat.stats() == ref.stats()
+    assert lat.get_sweep() == ref.get_sweep() == 3
+    np.testing.assert_allclose(p, p_ref, rtol=0, atol=1e-7)
+    rmax = Ns // 2
+    pm_ref, ps_ref, cs_ref = ref.batch_heatbath_measure([beta], 4, [seed], rmax)
+    pm, ps, cs = lat.batch_heatbath_measure([beta], 4, [seed], rmax)
+    np.testing.assert_array_equal(lat.get_links(), ref.get_links())
+    np.testing.assert_array_equal(ps, ps_ref)
+    np.testing.assert_array_equal(cs, cs_ref)
+    np.testing.assert_allclose(pm, pm_ref, rtol=0, atol=1e-7)
+    # the Creutz / Kennedy-Pendleton hybrid and plaquette-free sweeps too
+    for h in (ref, lat):
+        h.set_sampler(1.7)
+        h.heatbath(0.9, 2, seed + 1, plaq=None)
+    np.testing.assert_array_equal(lat.get_links(), ref.get_links())
+    assert lat.stats() == ref.stats() and lat.get_sweep() == 9
+
+
+def test_cluster_sweep_refused_where_it_does_not_apply():
+    """FP64, site pairs, batches and lattices whose links exceed one
+    cluster's shared memory (16^4 FP32: 4 MiB of links, 256 KiB per CTA of a
+    16-CTA cluster, above the 227 KB a CTA can hold) keep their shapes: the
+    index is refused with SU2_E_INVAL and the shape stays."""
+    cases = [lambda: lattice(8, 8, su2.F64), lambda: lattice(8, 8, su2.F32, su2.LAYOUT_PAIRS),
+             lambda: su2.Lattice([8, 8], [8, 8], su2.F32), lambda: lattice(16, 16, su2.F32)]
+    for make in cases:
+        lat = make()
+        lat.set_launch_config(2)
+        with pytest.raises(su2.SU2Error) as e:
+            lat.set_launch_config(su2.LAUNCH_CLUSTER)
+        assert e.value.code == su2.SU2_E_INVAL
+        assert lat.launch_config()[0] == 2
+        lat.close()
+
+
+def test_autotune_times_the_cluster_sweep():
+    """On 8^4 FP32 the autotuner also times the cluster sweep; whichever it
+    keeps, a sweep afterwards gives shape 0's links."""
+    lat = lattice(8, 8, su2.F32)
+    chosen = lat.autotune(beta=6.0)
+    assert 0 <= chosen <= su2.LAUNCH_CLUSTER and lat.launch_config()[0] == chosen
+    lat.init(su2.HOT, 3)
+    lat.heatbath(6.0, 2, 4, plaq=None)
+    ref = lattice(8, 8, su2.F32)
+    ref.init(su2.HOT, 3)
+    ref.heatbath(6.0, 2, 4, plaq=None)
+    np.testing.assert_array_equal(lat.get_links(), ref.get_links())
+
+
 def test_autotune_and_cache(tmp_path, monkeypatch):
     cache = tmp_path / "tune.txt"
     monkeypatch.setenv("SU2_AUTOTUNE_CACHE", str(cache))

@@ -111,7 +111,9 @@ hb_cluster_kernel(Ctx ctx, uint32_t C, FastDiv div_c, int pl)
     __shared__ double wsum[NT / 32];
     __shared__ double cta_part[CLUSTER_MAX];
     LatDesc* const Dw = ctx.desc;
-    const LatDesc& D = *Dw;
+    // a register copy: the barriers' memory clobbers would otherwise reload
+    // the geometry and the coupling from global memory in every phase
+    const LatDesc D = *Dw;
     const uint32_t rank = cluster_rank();
     const uint32_t S = gridDim.x;
     const uint32_t Vh = D.Vh;

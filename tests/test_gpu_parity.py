@@ -531,7 +531,7 @@ def test_every_launch_shape_gives_identical_results(dtype):
             np.testing.assert_allclose(plaq, ref_plaq, rtol=0, atol=1e-7)
 
 
-@pytest.mark.parametrize("Ns,Nt", [(8, 8), (12, 12), (10, 10), (8, 4), (6, 8)])
+@pytest.mark.parametrize("Ns,Nt", [(8, 8), (12, 12), (10, 10), (8, 4), (6, 8), (8, 2), (4, 4)])
 def test_cluster_sweep_matches_the_shapes(Ns, Nt):
     """The whole-sweep cluster kernel (the lattice in the distributed shared
     memory of one thread-block cluster, the phases separated by the cluster
@@ -547,6 +547,7 @@ def test_cluster_sweep_matches_the_shapes(Ns, Nt):
     lat.set_launch_config(su2.LAUNCH_CLUSTER)
     cfg, threads, ctas = lat.launch_config()
     assert cfg == su2.LAUNCH_CLUSTER and ctas == (8 if Ns == 10 else 16)
+    # (8^3 x 2: both t neighbours of a site are the same time slice)
     assert (Ns ** 3 * Nt // 2) % ctas == 0 and threads in (128, 1024)
     lat.init(su2.HOT, 5)
     p = lat.heatbath(beta, 3, seed)
@@ -567,6 +568,28 @@ def test_cluster_sweep_matches_the_shapes(Ns, Nt):
         h.heatbath(0.9, 2, seed + 1, plaq=None)
     np.testing.assert_array_equal(lat.get_links(), ref.get_links())
     assert lat.stats() == ref.stats() and lat.get_sweep() == 9
+
+
+def test_cluster_sweep_cap_hit():
+    """beta = 1e-9 under plain Kennedy-Pendleton in the cluster sweep: every
+    link runs to the 4096-trial cap, keeps its value and is counted once;
+    the call reports SU2_E_TRIALS, as the shapes do."""
+    Ns, Nt = 4, 4
+    V = Ns ** 3 * Nt
+    lat = lattice(Ns, Nt, su2.F32)
+    lat.set_launch_config(su2.LAUNCH_CLUSTER)
+    lat.init(su2.HOT, 3)
+    before = lat.get_links()
+    lat.heatbath(1e-9, 1, 3, plaq=None)
+    with pytest.raises(su2.SU2Error) as e:
+        lat.sync()
+    assert e.value.code == su2.SU2_E_TRIALS
+    np.testing.assert_array_equal(lat.get_links(), before)
+    st = lat.stats()
+    assert st["cap_hits"] == 4 * V and st["trials"] == su2.KP_CAP * 4 * V
+    assert lat.get_sweep() == 1
+    with pytest.raises(su2.SU2Error):
+        lat.heatbath(1e-9, 1, 3)  # host plaquette output: reported by the call
 
 
 def test_cluster_sweep_refused_where_it_does_not_apply():

@@ -16,6 +16,8 @@ FP32 lattices run in the plain layout by default; the site-pair layout (two
 links per thread, packed FP32x2 arithmetic; Nt a multiple of 4) is tested
 explicitly, and the two give identical bits.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -568,6 +570,33 @@ def test_cluster_sweep_matches_the_shapes(Ns, Nt):
         h.heatbath(0.9, 2, seed + 1, plaq=None)
     np.testing.assert_array_equal(lat.get_links(), ref.get_links())
     assert lat.stats() == ref.stats() and lat.get_sweep() == 9
+
+
+def test_cluster_sweep_from_the_tuning_cache_and_single_phases(tmp_path, monkeypatch):
+    """A cached cluster choice (launch index 14) is taken by the next 8^4
+    FP32 handle at binding; the single-phase entry point of a handle in
+    cluster mode keeps using a phase-kernel shape and matches shape 0."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("SU2_AUTOTUNE_CACHE", str(cache))
+    lat = lattice(8, 8, su2.F32)
+    buf = C.create_string_buffer(256)
+    assert su2.load().su2_tune_key(lat._h, buf, 256) == 0
+    assert su2.load().su2_tune_cache_store(str(cache).encode(), buf.value,
+                                           su2.LAUNCH_CLUSTER, 0.1) == 0
+    again = lattice(8, 8, su2.F32)
+    assert again.launch_config()[0] == su2.LAUNCH_CLUSTER
+    ref = lattice(8, 8, su2.F32)
+    for h in (again, ref):
+        h.init(su2.HOT, 21)
+    V = 8 ** 4
+    for mu, p in PHASES[:3]:
+        ta = torch.full((V,), -2, dtype=torch.int32, device="cuda")
+        tb = torch.full((V,), -2, dtype=torch.int32, device="cuda")
+        again.heatbath_phase(2.4, mu, p, 5, ta)
+        ref.heatbath_phase(2.4, mu, p, 5, tb)
+        assert torch.equal(ta, tb)
+    np.testing.assert_array_equal(again.get_links(), ref.get_links())
+    assert again.launch_config()[0] == su2.LAUNCH_CLUSTER
 
 
 def test_cluster_sweep_cap_hit():

@@ -176,6 +176,18 @@ __device__ __forceinline__ bool kp_try(const U4& w, T inv2a, T* d)
     kp_eval(u01<T>(w.x), u01<T>(w.y), u01<T>(w.z), u01<T>(w.w), inv2a, d, &lhs, &rhs);
     return lhs <= rhs;
 }
+// FP64: kp_eval's operations, with cospi's argument 2 r2 assembled exactly
+// from the bits instead of doubled by an FP64 multiply
+template <>
+__device__ __forceinline__ bool kp_try<double>(const U4& w, double inv2a, double* d)
+{
+    const double c = cospi(two_u01d(w.y));
+    const double lam2 = mul_(neg_(fma_(mul_(c, c), Math<double>::ln_u01(u01d(w.z)),
+                                       Math<double>::ln_u01(u01d(w.x)))), inv2a);
+    *d = add_(lam2, lam2);
+    const double r4 = u01d(w.w);
+    return mul_(r4, r4) <= add_(1.0, neg_(lam2));
+}
 
 // One trial of Creutz's draw (small alpha): a0 from exp(alpha a0) by
 // inversion, delta = -ln(1 - r1 qc) / alpha with qc = 1 - exp(-2 alpha),
@@ -198,18 +210,24 @@ __device__ __forceinline__ T creutz_qc(T alpha)
 // The accepted draw X = (1 - delta, sqrt(delta (2 - delta)) n) with the
 // direction n from the uniforms u1 (cos theta = 2 u1 - 1) and u2
 // (phi = 2 pi u2), and the new link U = X A^dagger / |A|, renormalised.
+// (cth = cos theta, sph / cph = sin / cos phi)
 template <typename V>
-__device__ __forceinline__ Quat<V> new_link_u(V delta, V u1, V u2, const Quat<V>& A)
+__device__ __forceinline__ Quat<V> new_link_dir(V delta, V cth, V sph, V cph, const Quat<V>& A)
 {
     const V one = splat<V>(1.0f);
-    const V cth = fma_(splat<V>(2.0f), u1, splat<V>(-1.0f));
     const V sth = Math<V>::sqrt_pos(mul_(add_(one, neg_(cth)), add_(one, cth)));
-    V sph, cph;
-    Math<V>::sincos2pi(u2, &sph, &cph);
     const V vl = Math<V>::sqrt_pos(mul_(delta, add_(splat<V>(2.0f), neg_(delta))));
     const V vs = mul_(vl, sth);
     const Quat<V> X = {add_(one, neg_(delta)), mul_(vs, cph), mul_(vs, sph), mul_(vl, cth)};
     return qnormalise(qmul_nd(X, A));
+}
+template <typename V>
+__device__ __forceinline__ Quat<V> new_link_u(V delta, V u1, V u2, const Quat<V>& A)
+{
+    const V cth = fma_(splat<V>(2.0f), u1, splat<V>(-1.0f));
+    V sph, cph;
+    Math<V>::sincos2pi(u2, &sph, &cph);
+    return new_link_dir(delta, cth, sph, cph, A);
 }
 
 // the direction from the spare bits kd1, kd2 of the first trial block
@@ -217,6 +235,24 @@ template <typename T>
 __device__ __forceinline__ Quat<T> new_link(T delta, uint32_t kd1, uint32_t kd2, const Quat<T>& A)
 {
     return new_link_u(delta, u18<T>(kd1), u18<T>(kd2), A);
+}
+// FP64: cos theta = 2 u1 - 1 = (2 kd1 + 1 - 2^18) 2^-18, and the cospi
+// arguments 2 u2 and 2 u2 - 1/2 (Math<double>::sincos2pi), assembled exactly
+// from the bits: the values new_link_u computes, without FP64 instructions
+__device__ __forceinline__ double dir_cth(uint32_t kd1)
+{
+    return exact_double((int32_t)(2u * kd1 + 1u) - (1 << 18), -18);
+}
+__device__ __forceinline__ double dir_arg(uint32_t kd2, bool sine)
+{
+    return exact_double((int32_t)(2u * kd2 + 1u) - (sine ? (1 << 17) : 0), -18);
+}
+template <>
+__device__ __forceinline__ Quat<double> new_link<double>(double delta, uint32_t kd1, uint32_t kd2,
+                                                         const Quat<double>& A)
+{
+    return new_link_dir(delta, dir_cth(kd1), cospi(dir_arg(kd2, true)), cospi(dir_arg(kd2, false)),
+                        A);
 }
 
 // the spare low 9 bits of the first trial's four words: two 18-bit uniforms
@@ -1056,15 +1092,10 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
         // outside the branch: the shuffles need the whole warp)
         const T lnv = Math<T>::ln_u01(u01<T>(g < 4 ? w.x : w.z));
         const T ln3 = __shfl_sync(0xffffffffu, lnv, lane ^ 4);
-        // u01(r2) or, for the direction, u18(kd2): the same bit construction
-        // and subtraction as u01d / u18d, operands picked per lane
+        // cospi's argument, assembled exactly (no FP64 instruction): 2 r2,
+        // or for the direction 2 u2 (lane 4) and 2 u2 - 1/2 (lane 5)
         const bool dir = pass == 0 && (g == 4 || g == 5);
-        const uint32_t k23 = w.y >> 9;
-        const T u = add_(__hiloint2double((int)(0x3FF00000u | (dir ? kd2 << 2 : k23 >> 3)),
-                                          dir ? 0 : (int)(k23 << 29)),
-                         dir ? -0.9999980926513671875 : -0.999999940395355224609375);
-        // 2 u exactly; minus 1/2 (exact) on lane 5 for the sine
-        const T cv = cospi(add_(mul_(T(2), u), dir && g == 5 ? T(-0.5) : T(-0.0)));
+        const T cv = cospi(dir ? dir_arg(kd2, g == 5) : two_u01d(w.y));
         if (pass == 0) {
             cph = __shfl_sync(0xffffffffu, cv, g0 + 4);
             sph = __shfl_sync(0xffffffffu, cv, g0 + 5);
@@ -1094,7 +1125,7 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     // sqrt((1 - cth)(1 + cth)) and lane 5 |vector part| =
     // sqrt((delta + (-0)) (2 - delta)) in one stream
     const T one = T(1);
-    const T cth = fma_(T(2), u18<T>(kd1), T(-1));
+    const T cth = dir_cth(kd1);
     const bool l5 = g == 5;
     const T root = Math<T>::sqrt_pos(
         mul_(add_(l5 ? delta : one, l5 ? T(-0.0) : flip_sign(cth, SIGN)),

@@ -213,10 +213,9 @@ struct Stream {
 };
 
 // uniform in (0,1): ((w >> 9) + 0.5) 2^-23, exact in float and double.
-// The top 23 bits as the leading mantissa bits of a number in [1,2) give
-// 1 + k 2^-23; subtracting 1 - 2^-24 leaves (2k + 1) 2^-24 exactly
-// (Sterbenz).  Integer operations and one subtraction: no conversion on
-// the FP64 pipe.
+// FP32: the top 23 bits as the leading mantissa bits of a number in [1,2)
+// give 1 + k 2^-23; subtracting 1 - 2^-24 leaves (2k + 1) 2^-24 exactly
+// (Sterbenz).  FP64: the same value assembled from its bits (exact_double).
 __device__ __forceinline__ float u01_bits(uint32_t w)  // 1 + k 2^-23
 {
     return __int_as_float((int)((w >> 9) | 0x3F800000u));
@@ -230,11 +229,28 @@ __device__ __forceinline__ float2 u01f2(uint32_t wa, uint32_t wb)
 {
     return add_(make_float2(u01_bits(wa), u01_bits(wb)), splat<float2>(-0.99999994039535522f));
 }
+// m 2^e as a double, for an integer 0 < |m| < 2^31, assembled from its bits
+// with integer operations only (the value is exact): on GB300 an FP64
+// instruction holds its SM sub-partition's FP64 unit for ~76 cycles, so the
+// uniforms of the FP64 path cost none
+__device__ __forceinline__ double exact_double(int32_t m, int e)
+{
+    const uint32_t a = (uint32_t)(m < 0 ? -m : m);
+    const int p = 31 - __clz((int)a);  // position of the leading bit
+    const uint64_t f = ((uint64_t)a << (52 - p)) & 0x000FFFFFFFFFFFFFull;
+    const uint32_t hi = (m < 0 ? 0x80000000u : 0u) | ((uint32_t)(1023 + p + e) << 20) |
+                        (uint32_t)(f >> 32);
+    return __hiloint2double((int)hi, (int)(uint32_t)f);
+}
+// ((w >> 9) + 1/2) 2^-23 = (2 (w >> 9) + 1) 2^-24
 __device__ __forceinline__ double u01d(uint32_t w)
 {
-    const uint32_t k = w >> 9;  // 23 bits -> mantissa bits 51..29
-    return add_(__hiloint2double((int)(0x3FF00000u | (k >> 3)), (int)(k << 29)),
-                -0.999999940395355224609375);
+    return exact_double((int32_t)(2u * (w >> 9) + 1u), -24);
+}
+// twice that, the argument of cospi for cos(2 pi u)
+__device__ __forceinline__ double two_u01d(uint32_t w)
+{
+    return exact_double((int32_t)(2u * (w >> 9) + 1u), -23);
 }
 // uniform in (0,1) from an 18-bit integer k: (k + 0.5) 2^-18, exact
 __device__ __forceinline__ float u18_bits(uint32_t k)
@@ -249,10 +265,10 @@ __device__ __forceinline__ float2 u18f2(uint32_t ka, uint32_t kb)
 {
     return add_(make_float2(u18_bits(ka), u18_bits(kb)), splat<float2>(-0.9999980926513671875f));
 }
+// (k + 1/2) 2^-18 = (2 k + 1) 2^-19
 __device__ __forceinline__ double u18d(uint32_t k)
 {
-    // 18 bits -> mantissa bits 51..34, all in the high word
-    return add_(__hiloint2double((int)(0x3FF00000u | (k << 2)), 0), -0.9999980926513671875);
+    return exact_double((int32_t)(2u * k + 1u), -19);
 }
 template <typename T> __device__ __forceinline__ T u18(uint32_t k);
 template <> __device__ __forceinline__ float u18<float>(uint32_t k) { return u18f(k); }

@@ -81,7 +81,18 @@ int su2_probe_fma_rate(int dtype, int iters, double* fma_per_s, void* stream);
 #define SU2_PROBE_SINCOSPI 2
 #define SU2_PROBE_SQRT 3
 #define SU2_PROBE_RSQRT 4
+/* SU2_PROBE_LN_TABLE: the FP64 heat bath's own logarithm of a uniform,
+ * table-driven (the argument's bits give the uniform; chains feed each
+ * result's low bits back in) */
+#define SU2_PROBE_LN_TABLE 5
 int su2_probe_special_rate(int fn, int iters, double* calls_per_s, void* stream);
+
+/* The FP64 heat bath's table-driven logarithm against CUDA's log on all
+ * 2^23 uniforms u = (2k + 1) 2^-24 it is used on.  out: device buffer of 2
+ * doubles, filled on `stream` with the largest absolute difference and the
+ * largest difference in units of the last place of CUDA's result.  Uploads
+ * the table (synchronous); the kernel is asynchronous on `stream`. */
+int su2_selftest_ln(void* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -176,14 +176,23 @@ __device__ __forceinline__ bool kp_try(const U4& w, T inv2a, T* d)
     kp_eval(u01<T>(w.x), u01<T>(w.y), u01<T>(w.z), u01<T>(w.w), inv2a, d, &lhs, &rhs);
     return lhs <= rhs;
 }
-// FP64: kp_eval's operations, with cospi's argument 2 r2 assembled exactly
-// from the bits instead of doubled by an FP64 multiply
+// The same with the FP64 path's logarithm table (unused in FP32).  FP64:
+// kp_eval's operations, with the logarithms table-driven (ln_u01_tab) and
+// cospi's argument 2 r2 assembled exactly from the bits instead of doubled
+// by an FP64 multiply.
+template <typename T>
+__device__ __forceinline__ bool kp_try(const U4& w, T inv2a, T* d, const double2* tab)
+{
+    (void)tab;
+    return kp_try(w, inv2a, d);
+}
 template <>
-__device__ __forceinline__ bool kp_try<double>(const U4& w, double inv2a, double* d)
+__device__ __forceinline__ bool kp_try<double>(const U4& w, double inv2a, double* d,
+                                               const double2* tab)
 {
     const double c = cospi(two_u01d(w.y));
-    const double lam2 = mul_(neg_(fma_(mul_(c, c), Math<double>::ln_u01(u01d(w.z)),
-                                       Math<double>::ln_u01(u01d(w.x)))), inv2a);
+    const double lam2 =
+        mul_(neg_(fma_(mul_(c, c), ln_u01_tab(w.z, tab), ln_u01_tab(w.x, tab))), inv2a);
     *d = add_(lam2, lam2);
     const double r4 = u01d(w.w);
     return mul_(r4, r4) <= add_(1.0, neg_(lam2));
@@ -327,11 +336,11 @@ __device__ __forceinline__ int32_t update_link(const LT& U, const LatDesc& D, co
                 break;
             }
         }
-    } else if (kp_try(w, inv2a, &delta)) {
+    } else if (kp_try(w, inv2a, &delta, D.ln_table)) {
         tr = 1;
     } else {
         for (int t = 1; t < KP_CAP; ++t) {
-            if (kp_try(st.draw(TAG_TRIAL, (uint32_t)t), inv2a, &delta)) {
+            if (kp_try(st.draw(TAG_TRIAL, (uint32_t)t), inv2a, &delta, D.ln_table)) {
                 tr = t + 1;
                 break;
             }
@@ -540,6 +549,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const uint64_t sw = D.sweep;
     const uint32_t k0 = (uint32_t)D.seed, k1 = (uint32_t)(D.seed >> 32);
     const uint32_t slo = (uint32_t)sw, shi = (uint32_t)(sw >> 32);
+    const double2* const lnt = D.ln_table;  // FP64's logarithm table
 
     T plaq = T(0);
     uint32_t ntrial = 0, ncap = 0;
@@ -603,7 +613,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             const U4 w = st.draw(TAG_TRIAL, t);
             T delta;
             const bool ok = (HYB && qc > T(0)) ? creutz_try(w, qc, inv2a, &delta)
-                                               : kp_try(w, inv2a, &delta);
+                                               : kp_try(w, inv2a, &delta, lnt);
             if (ok) {
                 put(i, key, new_link(delta, kd1, kd2, A), P, (int32_t)t + 1);
             } else if (t + 1 >= (uint32_t)KP_CAP) {
@@ -672,7 +682,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
                         qc = creutz_qc(alpha);
                         ok = creutz_try(w, qc, inv2a, &delta);
                     } else {
-                        ok = kp_try(w, inv2a, &delta);
+                        ok = kp_try(w, inv2a, &delta, lnt);
                     }
                     if (ok) {
                         put(i, key, new_link(delta, kd1, kd2, A), P, 1);
@@ -1001,6 +1011,7 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     // staple, and their loads then wait on nothing)
     const uint64_t sw = D.sweep, seed = D.seed;
     const T beta = beta_of<T>(D), hib = D.half_inv_beta;
+    const double2* const lnt = D.ln_table;
 
     Quat<T> term = {T(0), T(0), T(0), T(0)};
     uint32_t key = 0;
@@ -1090,7 +1101,7 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
         }
         // kp_eval's pieces, with ln r3 from the partner lane (all lanes,
         // outside the branch: the shuffles need the whole warp)
-        const T lnv = Math<T>::ln_u01(u01<T>(g < 4 ? w.x : w.z));
+        const T lnv = ln_u01_tab(g < 4 ? w.x : w.z, lnt);
         const T ln3 = __shfl_sync(0xffffffffu, lnv, lane ^ 4);
         // cospi's argument, assembled exactly (no FP64 instruction): 2 r2,
         // or for the direction 2 u2 (lane 4) and 2 u2 - 1/2 (lane 5)

@@ -49,6 +49,39 @@ __global__ void math_selftest_kernel(unsigned long long* out)
 
 __device__ double fma_rate_sink;
 
+// the FP64 path's logarithm table for the self-test and the probe (the
+// heat-bath kernels read the copy in the handle's work memory)
+__device__ double2 g_ln_tab[LN_TABLE_ENTRIES];
+
+int upload_ln_table()
+{
+    double2 tab[LN_TABLE_ENTRIES];
+    fill_ln_table(tab);
+    return cudaMemcpyToSymbol(g_ln_tab, tab, sizeof tab) == cudaSuccess ? SU2_OK : SU2_E_CUDA;
+}
+
+// ln_u01_tab against CUDA's log on every grid point u = (2k + 1) 2^-24:
+// out[0] max absolute error, out[1] max error in units of the last place of
+// the reference
+__global__ void ln_selftest_kernel(unsigned long long* out)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (1u << 23)) return;
+    const uint32_t w = k << 9;
+    const double ref = log(u01d(w));
+    const double err = fabs(ln_u01_tab(w, g_ln_tab) - ref);
+    const int ex = (int)((__double_as_longlong(ref) >> 52) & 0x7FF) - 1023;
+    const double ulps = err / ldexp(1.0, ex - 52);
+    double v[2] = {err, ulps};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        double m = v[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) atomic_max_pos(out + j, m);
+    }
+}
+
 // 8 independent FMA chains per thread: the pipe never waits on a result
 template <typename T>
 __global__ void __launch_bounds__(256) fma_rate_kernel(int iters, T a, T b)
@@ -78,6 +111,8 @@ __global__ void __launch_bounds__(256) special_rate_kernel(int iters)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             if (FN == SU2_PROBE_LOG) x[j] = log(x[j] + 2.0);
+            else if (FN == SU2_PROBE_LN_TABLE)
+                x[j] = ln_u01_tab((uint32_t)__double_as_longlong(x[j]), g_ln_tab);
             else if (FN == SU2_PROBE_COSPI) x[j] = cospi(x[j]);
             else if (FN == SU2_PROBE_SINCOSPI) {
                 double sn, cs;
@@ -130,11 +165,13 @@ int probe_blocks(unsigned* blocks)
 
 extern "C" int su2_probe_special_rate(int fn, int iters, double* calls_per_s, void* stream)
 {
-    if (!calls_per_s || iters <= 0 || fn < SU2_PROBE_LOG || fn > SU2_PROBE_RSQRT)
+    if (!calls_per_s || iters <= 0 || fn < SU2_PROBE_LOG || fn > SU2_PROBE_LN_TABLE)
         return SU2_E_INVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned blocks = 0;
     if (int rc = su2::probe_blocks(&blocks)) return rc;
+    if (fn == SU2_PROBE_LN_TABLE)
+        if (int rc = su2::upload_ln_table()) return rc;
     float ms = 0.0f;
     auto launch = [&] {
         switch (fn) {
@@ -142,6 +179,7 @@ extern "C" int su2_probe_special_rate(int fn, int iters, double* calls_per_s, vo
         case SU2_PROBE_COSPI: su2::special_rate_kernel<SU2_PROBE_COSPI><<<blocks, 256, 0, s>>>(iters); break;
         case SU2_PROBE_SINCOSPI: su2::special_rate_kernel<SU2_PROBE_SINCOSPI><<<blocks, 256, 0, s>>>(iters); break;
         case SU2_PROBE_SQRT: su2::special_rate_kernel<SU2_PROBE_SQRT><<<blocks, 256, 0, s>>>(iters); break;
+        case SU2_PROBE_LN_TABLE: su2::special_rate_kernel<SU2_PROBE_LN_TABLE><<<blocks, 256, 0, s>>>(iters); break;
         default: su2::special_rate_kernel<SU2_PROBE_RSQRT><<<blocks, 256, 0, s>>>(iters); break;
         }
     };
@@ -174,6 +212,17 @@ extern "C" int su2_selftest_math(void* out, void* stream)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(out, 0, 4 * sizeof(double), s) != cudaSuccess) return SU2_E_CUDA;
     su2::math_selftest_kernel<<<(1u << 23) / 256, 256, 0, s>>>(
+        static_cast<unsigned long long*>(out));
+    return cudaGetLastError() == cudaSuccess ? SU2_OK : SU2_E_CUDA;
+}
+
+extern "C" int su2_selftest_ln(void* out, void* stream)
+{
+    if (!out) return SU2_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (int rc = su2::upload_ln_table()) return rc;
+    if (cudaMemsetAsync(out, 0, 2 * sizeof(double), s) != cudaSuccess) return SU2_E_CUDA;
+    su2::ln_selftest_kernel<<<(1u << 23) / 256, 256, 0, s>>>(
         static_cast<unsigned long long*>(out));
     return cudaGetLastError() == cudaSuccess ? SU2_OK : SU2_E_CUDA;
 }

@@ -125,4 +125,38 @@ template <> struct Math<double> {
     static __device__ __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
 };
 
+// ln u for the FP64 path's uniform u = (2 (w >> 9) + 1) 2^-24, table-driven
+// after Tang (ACM TOMS 15 (1989) 144): u = 2^n m with m in [0.75, 1.5) read
+// off the bits, c the centre of m's table interval, g = 1/c rounded and
+// -ln g stored (computed once on the host in extended precision),
+// r = m g - 1 with one fused multiply-add (|r| <= 2^-9 / 0.75; the
+// interval just below 1 takes c = 1, r = m - 1 exactly), and
+//   ln u = n ln 2 - ln g + ln(1 + r),
+//   ln(1 + r) = r + r^2 (-1/2 + r (1/3 + r (-1/4 + r (1/5 - r/6))))
+// (the Taylor series; the first term left out is below r^7/7 < 2e-19).
+// ln 2 = hi + lo with hi's low mantissa bits zero, so that n hi is exact.
+// Ten FP64 instructions against ~30 instruction times for a general log:
+// on GB300 the FP64 unit is the heat bath's bottleneck in FP64.
+// tab: 256 intervals, then (ln 2 hi, ln 2 lo) (fill_ln_table, su2_internal.h)
+__device__ __forceinline__ double ln_u01_tab(uint32_t w, const double2* __restrict__ tab)
+{
+    const uint32_t a = 2u * (w >> 9) + 1u;  // u = a 2^-24, 1 <= a < 2^24
+    const int p = 31 - __clz((int)a);     // 2^p <= a < 2^(p+1)
+    // the first 8 fraction bits of M = a 2^-p in [1, 2): the table interval
+    const uint32_t t = (p >= 8 ? a >> (p - 8) : a << (8 - p)) & 255u;
+    const int h = t >= 128 ? 1 : 0;         // M >= 1.5: m = M / 2
+    const int n = p - 24 + h;
+    const double m = exact_double((int32_t)a, -p - h);
+    const double2 e = __ldg(tab + t);       // (g, -ln g)
+    const double2 l2 = __ldg(tab + 256);    // (ln 2 hi, ln 2 lo)
+    const double r = fma_(m, e.x, -1.0);
+    double q = fma_(r, -1.0 / 6.0, 0.2);
+    q = fma_(r, q, -0.25);
+    q = fma_(r, q, 1.0 / 3.0);
+    q = fma_(r, q, -0.5);
+    const double lp = fma_(mul_(r, r), q, r);
+    const double nd = n ? exact_double(n, 0) : 0.0;
+    return add_(fma_(nd, l2.x, e.y), fma_(nd, l2.y, lp));
+}
+
 }  // namespace su2

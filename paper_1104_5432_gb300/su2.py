@@ -87,6 +87,7 @@ def load(build_if_needed: bool = True):
             "su2_selftest_fastdiv": (u64, [C.c_uint32, C.c_uint32]),
             "su2_plaquette_static": (i, [P, i, i, i, P, P]),
             "su2_selftest_math": (i, [P, P]),
+            "su2_selftest_ln": (i, [P, P]),
             "su2_get_links_f32": (i, [P, i, P]),
             "su2_set_links_f32": (i, [P, i, P]),
             "su2_probe_fma_rate": (i, [i, i, P, P]),
@@ -129,7 +130,7 @@ def probe_fma_rate(dtype: int, iters: Optional[int] = None) -> float:
     return v.value
 
 
-PROBE_LOG, PROBE_COSPI, PROBE_SINCOSPI, PROBE_SQRT, PROBE_RSQRT = range(5)
+PROBE_LOG, PROBE_COSPI, PROBE_SINCOSPI, PROBE_SQRT, PROBE_RSQRT, PROBE_LN_TABLE = range(6)
 
 
 def probe_special_rate(fn: int, iters: int = 1024) -> float:

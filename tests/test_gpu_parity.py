@@ -494,14 +494,33 @@ def test_special_function_rate_probe():
     runs below the FP64 FMA rate (each is several FP64 operations), stably
     to 15% between calls; a bad function index is refused."""
     fma = su2.probe_fma_rate(su2.F64)
+    rates = {}
     for fn in (su2.PROBE_LOG, su2.PROBE_COSPI, su2.PROBE_SINCOSPI, su2.PROBE_SQRT,
-               su2.PROBE_RSQRT):
+               su2.PROBE_RSQRT, su2.PROBE_LN_TABLE):
         r = su2.probe_special_rate(fn)
         again = su2.probe_special_rate(fn)
         assert 0 < r < fma, (fn, r, fma)
         assert abs(again - r) <= 0.15 * r, (fn, r, again)
+        rates[fn] = r
+    # the kernels' table-driven logarithm of a uniform beats the general one
+    assert rates[su2.PROBE_LN_TABLE] > 1.5 * rates[su2.PROBE_LOG]
     with pytest.raises(su2.SU2Error):
-        su2.probe_special_rate(5)
+        su2.probe_special_rate(6)
+
+
+def test_table_logarithm_on_every_uniform():
+    """The FP64 heat bath's table-driven ln u (Tang's method: interval table,
+    degree-6 series of ln(1 + r)) against CUDA's log on all 2^23 uniforms
+    u = (2k + 1) 2^-24: within 2 units in the last place of CUDA's result
+    (each within about 1 ulp of ln u; near u = 1 too, where the last table
+    interval is centred on 1), i.e. at most ~4e-15 absolute (|ln u| < 16.7)."""
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    rc = su2.load().su2_selftest_ln(out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    err_abs, err_ulp = out.cpu().tolist()
+    assert err_ulp <= 2.0, (err_abs, err_ulp)
+    assert err_abs <= 4e-15, (err_abs, err_ulp)
 
 
 @pytest.mark.parametrize("dtype", [su2.F32, su2.F64])

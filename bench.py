@@ -172,8 +172,8 @@ def recorded_traffic(kernel_key, field="dram_bytes_per_launch_full_size"):
 # and the renormalisation (~40) -- and the math-function calls the update
 # makes: per trial 2 log + 1 cospi (lambda^2), and once 2 rsqrt (1/k, the
 # renormalisation), 2 sqrt (sin theta, |vector part|), 1 sincospi (phi).
-# Each at the measured rate of the routine the kernels call (the logarithm
-# is their own table-driven one).
+# Each at the measured rate of the routine the kernels call (the logarithm,
+# the cosine and the sine + cosine are their own table-driven ones).
 FP64_FLOPS_FIXED, FP64_FLOPS_PER_TRIAL = 420.0, 10.0
 FP64_CALLS = {"log": (0, 2), "cospi": (0, 1), "sincospi": (1, 0), "sqrt": (2, 0),
               "rsqrt": (2, 0)}  # (per update, per trial)
@@ -185,9 +185,10 @@ def fp64_roofline(su2, ups, trials_per_update):
     function, calls / its measured call rate.  peak = 1 / that time."""
     t = trials_per_update
     fma = su2.probe_fma_rate(su2.F64)
-    # the logarithm the FP64 kernels call: their table-driven one
-    ids = {"log": su2.PROBE_LN_TABLE, "cospi": su2.PROBE_COSPI, "sincospi": su2.PROBE_SINCOSPI,
-           "sqrt": su2.PROBE_SQRT, "rsqrt": su2.PROBE_RSQRT}
+    # the routines the FP64 kernels call: their table-driven logarithm,
+    # cosine and sine + cosine, CUDA's sqrt and rsqrt
+    ids = {"log": su2.PROBE_LN_TABLE, "cospi": su2.PROBE_COS_TABLE,
+           "sincospi": su2.PROBE_SINCOS_TABLE, "sqrt": su2.PROBE_SQRT, "rsqrt": su2.PROBE_RSQRT}
     rates = {k: su2.probe_special_rate(ids[k]) for k in FP64_CALLS}
     flops = FP64_FLOPS_FIXED + FP64_FLOPS_PER_TRIAL * t
     parts = {"flops": flops / (2 * fma)}

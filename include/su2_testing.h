@@ -85,6 +85,11 @@ int su2_probe_fma_rate(int dtype, int iters, double* fma_per_s, void* stream);
  * table-driven (the argument's bits give the uniform; chains feed each
  * result's low bits back in) */
 #define SU2_PROBE_LN_TABLE 5
+/* SU2_PROBE_COS_TABLE / SU2_PROBE_SINCOS_TABLE: its table-driven cosine
+ * (the trials' cos(2 pi r2)) and sine + cosine (the direction's angle) of
+ * the grid values */
+#define SU2_PROBE_COS_TABLE 6
+#define SU2_PROBE_SINCOS_TABLE 7
 int su2_probe_special_rate(int fn, int iters, double* calls_per_s, void* stream);
 
 /* The FP64 heat bath's table-driven logarithm against CUDA's log on all
@@ -93,6 +98,14 @@ int su2_probe_special_rate(int fn, int iters, double* calls_per_s, void* stream)
  * largest difference in units of the last place of CUDA's result.  Uploads
  * the table (synchronous); the kernel is asynchronous on `stream`. */
 int su2_selftest_ln(void* out, void* stream);
+
+/* The FP64 heat bath's table-driven sine and cosine of pi y against CUDA's
+ * sincospi: out (device, 2 doubles) gets the cosine's largest absolute
+ * difference over the trials' 2^23 arguments y = (2k + 1) 2^-23 and the
+ * sine's and cosine's over the direction's 2^18 arguments
+ * y = (2k + 1) 2^-18.  Uploads the table (synchronous); the kernel is
+ * asynchronous on `stream`. */
+int su2_selftest_trig(void* out, void* stream);
 
 #ifdef __cplusplus
 }

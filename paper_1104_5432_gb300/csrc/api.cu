@@ -15,6 +15,7 @@
 
 #include "su2_testing.h"
 #include "su2_internal.h"
+#include "su2_math.cuh"
 
 using namespace su2;
 
@@ -109,7 +110,7 @@ struct su2_lattice {
     size_t link_bytes = 0, work_bytes = 0;
     size_t off_status = 0, off_desc = 0, off_sstart = 0, off_spstart = 0;
     size_t off_plaq = 0, off_obs = 0, off_field = 0, off_ring = 0, off_res = 0, off_stage = 0;
-    size_t off_chunks = 0, off_tickets = 0, off_acc = 0, off_tslots = 0, off_lntab = 0;
+    size_t off_chunks = 0, off_tickets = 0, off_acc = 0, off_tslots = 0, off_fp64tab = 0;
     uint32_t max_chunks = 1;
     size_t res_doubles = 0;
     // bound state
@@ -297,7 +298,7 @@ int layout(su2_lattice* L)
     L->off_acc = take(8 * L->res_doubles);
     L->off_res = take(8 * L->res_doubles);
     L->off_stage = take(STAGE_BYTES);
-    L->off_lntab = take(sizeof(double2) * LN_TABLE_ENTRIES);
+    L->off_fp64tab = take(sizeof(double2) * FP64_TABLE_ENTRIES);
     L->work_bytes = w;
     return SU2_OK;
 }
@@ -714,19 +715,21 @@ bool cache_store(const char* path, const std::string& key, int cfg, double ms)
 
 void su2::record_error(const char* msg) { g_err = msg; }
 
-// ln_u01_tab's table: for each of the 256 intervals of the mantissa
+// The FP64 path's tables (su2_math.cuh).  ln_u01_tab: for each of the 256
+// intervals of the mantissa
 // M in [1, 2) (m = M / 2 from M = 1.5 on), g = 1 / c rounded, c the
 // interval's centre, and -ln g from the long double logarithm; the last
 // interval (m just below 1) takes c = 1, so that r = m - 1 is exact and
 // ln u near 1 keeps its relative accuracy (no cancellation between -ln g
 // and ln(1 + r)); then ln 2 = hi + lo with hi cut to 32 significant bits
-// (n hi exact for |n| < 2^21)
-void su2::fill_ln_table(double2* tab)
+// (n hi exact for |n| < 2^21).  sincospi_tab: cos and sin of pi j / 128
+// from the long double functions.
+void su2::fill_fp64_table(double2* tab)
 {
     for (int t = 0; t < 256; ++t) {
         const double cM = 1.0 + (t + 0.5) / 256.0;  // exact
         const double g = t == 255 ? 1.0 : 1.0 / (t >= 128 ? 0.5 * cM : cM);
-        tab[t] = make_double2(g, t == 255 ? 0.0 : (double)(-logl((long double)g)));
+        tab[TAB_LN + t] = make_double2(g, t == 255 ? 0.0 : (double)(-logl((long double)g)));
     }
     const long double l2 = logl(2.0L);
     double hi = (double)l2;
@@ -734,7 +737,12 @@ void su2::fill_ln_table(double2* tab)
     memcpy(&b, &hi, sizeof b);
     b &= ~((uint64_t(1) << 21) - 1);
     memcpy(&hi, &b, sizeof hi);
-    tab[256] = make_double2(hi, (double)(l2 - (long double)hi));
+    tab[TAB_LN2] = make_double2(hi, (double)(l2 - (long double)hi));
+    const long double pi = acosl(-1.0L);
+    for (int j = 0; j < 256; ++j) {
+        const long double a = pi * (long double)j / 128.0L;
+        tab[TAB_TRIG + j] = make_double2((double)cosl(a), (double)sinl(a));
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -903,13 +911,13 @@ int su2_bind_memory(su2_lattice* lat, void* links, size_t link_bytes, void* work
         lat->ysplit[l] = D.ysplit;
         D.link_off = lat->link_off[l];
         D.field_off = lat->field_off[l];
-        D.ln_table = reinterpret_cast<const double2*>(lat->work + lat->off_lntab);
+        D.fp64_table = reinterpret_cast<const double2*>(lat->work + lat->off_fp64tab);
     }
     char* w = lat->work;
     {
-        double2 tab[LN_TABLE_ENTRIES];
-        fill_ln_table(tab);
-        SU2_CUDA(cudaMemcpy(w + lat->off_lntab, tab, sizeof tab, cudaMemcpyHostToDevice));
+        double2 tab[FP64_TABLE_ENTRIES];
+        fill_fp64_table(tab);
+        SU2_CUDA(cudaMemcpy(w + lat->off_fp64tab, tab, sizeof tab, cudaMemcpyHostToDevice));
     }
     SU2_CUDA(cudaMemset(w + lat->off_status, 0, 256));
     SU2_CUDA(cudaMemcpy(w + lat->off_desc, d.data(), sizeof(LatDesc) * lat->n,

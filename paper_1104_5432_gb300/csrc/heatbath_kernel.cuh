@@ -176,10 +176,9 @@ __device__ __forceinline__ bool kp_try(const U4& w, T inv2a, T* d)
     kp_eval(u01<T>(w.x), u01<T>(w.y), u01<T>(w.z), u01<T>(w.w), inv2a, d, &lhs, &rhs);
     return lhs <= rhs;
 }
-// The same with the FP64 path's logarithm table (unused in FP32).  FP64:
-// kp_eval's operations, with the logarithms table-driven (ln_u01_tab) and
-// cospi's argument 2 r2 assembled exactly from the bits instead of doubled
-// by an FP64 multiply.
+// The same with the FP64 path's tables (unused in FP32).  FP64: kp_eval's
+// operations, with the logarithms and cos(2 pi r2) table-driven
+// (ln_u01_tab, sincospi_tab), their arguments read off the random bits.
 template <typename T>
 __device__ __forceinline__ bool kp_try(const U4& w, T inv2a, T* d, const double2* tab)
 {
@@ -190,7 +189,8 @@ template <>
 __device__ __forceinline__ bool kp_try<double>(const U4& w, double inv2a, double* d,
                                                const double2* tab)
 {
-    const double c = cospi(two_u01d(w.y));
+    double sn, c;  // cos(2 pi r2) from the table (the sine is not used)
+    sincospi_tab(2u * (w.y >> 9) + 1u, 23, tab, &sn, &c);
     const double lam2 =
         mul_(neg_(fma_(mul_(c, c), ln_u01_tab(w.z, tab), ln_u01_tab(w.x, tab))), inv2a);
     *d = add_(lam2, lam2);
@@ -245,23 +245,28 @@ __device__ __forceinline__ Quat<T> new_link(T delta, uint32_t kd1, uint32_t kd2,
 {
     return new_link_u(delta, u18<T>(kd1), u18<T>(kd2), A);
 }
-// FP64: cos theta = 2 u1 - 1 = (2 kd1 + 1 - 2^18) 2^-18, and the cospi
-// arguments 2 u2 and 2 u2 - 1/2 (Math<double>::sincos2pi), assembled exactly
-// from the bits: the values new_link_u computes, without FP64 instructions
+// FP64: cos theta = 2 u1 - 1 = (2 kd1 + 1 - 2^18) 2^-18 assembled exactly
+// from the bits (new_link_u's value, without FP64 instructions)
 __device__ __forceinline__ double dir_cth(uint32_t kd1)
 {
     return exact_double((int32_t)(2u * kd1 + 1u) - (1 << 18), -18);
 }
-__device__ __forceinline__ double dir_arg(uint32_t kd2, bool sine)
+// with the FP64 path's tables (unused in FP32): FP64 takes phi's sine and
+// cosine from sincospi_tab at 2 u2 = (2 kd2 + 1) 2^-18
+template <typename T>
+__device__ __forceinline__ Quat<T> new_link(T delta, uint32_t kd1, uint32_t kd2, const Quat<T>& A,
+                                            const double2* tab)
 {
-    return exact_double((int32_t)(2u * kd2 + 1u) - (sine ? (1 << 17) : 0), -18);
+    (void)tab;
+    return new_link(delta, kd1, kd2, A);
 }
 template <>
 __device__ __forceinline__ Quat<double> new_link<double>(double delta, uint32_t kd1, uint32_t kd2,
-                                                         const Quat<double>& A)
+                                                         const Quat<double>& A, const double2* tab)
 {
-    return new_link_dir(delta, dir_cth(kd1), cospi(dir_arg(kd2, true)), cospi(dir_arg(kd2, false)),
-                        A);
+    double sph, cph;
+    sincospi_tab(2u * kd2 + 1u, 18, tab, &sph, &cph);
+    return new_link_dir(delta, dir_cth(kd1), sph, cph, A);
 }
 
 // the spare low 9 bits of the first trial's four words: two 18-bit uniforms
@@ -336,17 +341,17 @@ __device__ __forceinline__ int32_t update_link(const LT& U, const LatDesc& D, co
                 break;
             }
         }
-    } else if (kp_try(w, inv2a, &delta, D.ln_table)) {
+    } else if (kp_try(w, inv2a, &delta, D.fp64_table)) {
         tr = 1;
     } else {
         for (int t = 1; t < KP_CAP; ++t) {
-            if (kp_try(st.draw(TAG_TRIAL, (uint32_t)t), inv2a, &delta, D.ln_table)) {
+            if (kp_try(st.draw(TAG_TRIAL, (uint32_t)t), inv2a, &delta, D.fp64_table)) {
                 tr = t + 1;
                 break;
             }
         }
     }
-    if (tr > 0) *un = new_link(delta, kd1, kd2, A);
+    if (tr > 0) *un = new_link(delta, kd1, kd2, A, D.fp64_table);
     return tr;
 }
 
@@ -549,7 +554,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     const uint64_t sw = D.sweep;
     const uint32_t k0 = (uint32_t)D.seed, k1 = (uint32_t)(D.seed >> 32);
     const uint32_t slo = (uint32_t)sw, shi = (uint32_t)(sw >> 32);
-    const double2* const lnt = D.ln_table;  // FP64's logarithm table
+    const double2* const lnt = D.fp64_table;  // FP64's log and sin/cos tables
 
     T plaq = T(0);
     uint32_t ntrial = 0, ncap = 0;
@@ -615,7 +620,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
             const bool ok = (HYB && qc > T(0)) ? creutz_try(w, qc, inv2a, &delta)
                                                : kp_try(w, inv2a, &delta, lnt);
             if (ok) {
-                put(i, key, new_link(delta, kd1, kd2, A), P, (int32_t)t + 1);
+                put(i, key, new_link(delta, kd1, kd2, A, lnt), P, (int32_t)t + 1);
             } else if (t + 1 >= (uint32_t)KP_CAP) {
                 // cap hit: the link keeps its value
                 ncap += 1;
@@ -685,7 +690,7 @@ hb_phase_queue_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
                         ok = kp_try(w, inv2a, &delta, lnt);
                     }
                     if (ok) {
-                        put(i, key, new_link(delta, kd1, kd2, A), P, 1);
+                        put(i, key, new_link(delta, kd1, kd2, A, lnt), P, 1);
                     } else {
                         pend = true;
                         tk = 1u | (kd1 << 13);
@@ -1011,7 +1016,7 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     // staple, and their loads then wait on nothing)
     const uint64_t sw = D.sweep, seed = D.seed;
     const T beta = beta_of<T>(D), hib = D.half_inv_beta;
-    const double2* const lnt = D.ln_table;
+    const double2* const lnt = D.fp64_table;
 
     Quat<T> term = {T(0), T(0), T(0), T(0)};
     uint32_t key = 0;
@@ -1078,8 +1083,9 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
     // Kennedy-Pendleton: lanes g and g + 4 share trial t0 + (g & 3), lane g
     // taking ln r1 and lane g + 4 ln r3, so each lane evaluates one logarithm
     // per pass and a pass tries four trials; in the first pass lanes 4 and 5
-    // put the direction's cos(phi) and sin(phi) = cos(phi - pi/2), phi =
-    // 2 pi u2, in place of the cos(2 pi r2) that only lanes 0..3 use.
+    // take the direction's cos(phi) and sin(phi), phi = 2 pi u2, from the
+    // table's sine/cosine stream in place of the cos(2 pi r2) that only
+    // lanes 0..3 use.
     // Creutz's draw needs one logarithm per trial, so there each of the eight
     // lanes tries its own (the direction still comes from lanes 4 and 5 of
     // the first pass).  Each group advances its own t0; the warp loops while
@@ -1103,13 +1109,15 @@ hb_phase_coop_kernel(Ctx ctx, int p, int32_t* __restrict__ dbg)
         // outside the branch: the shuffles need the whole warp)
         const T lnv = ln_u01_tab(g < 4 ? w.x : w.z, lnt);
         const T ln3 = __shfl_sync(0xffffffffu, lnv, lane ^ 4);
-        // cospi's argument, assembled exactly (no FP64 instruction): 2 r2,
-        // or for the direction 2 u2 (lane 4) and 2 u2 - 1/2 (lane 5)
+        // cos(2 pi r2) from the table; in the first pass lanes 4 and 5 take
+        // the direction's cos phi and sin phi from the same stream
         const bool dir = pass == 0 && (g == 4 || g == 5);
-        const T cv = cospi(dir ? dir_arg(kd2, g == 5) : two_u01d(w.y));
+        T sv, cv;
+        sincospi_tab(dir ? 2u * kd2 + 1u : 2u * (w.y >> 9) + 1u, dir ? 18 : 23, lnt, &sv, &cv);
+        const T dv = dir && g == 5 ? sv : cv;
         if (pass == 0) {
-            cph = __shfl_sync(0xffffffffu, cv, g0 + 4);
-            sph = __shfl_sync(0xffffffffu, cv, g0 + 5);
+            cph = __shfl_sync(0xffffffffu, dv, g0 + 4);
+            sph = __shfl_sync(0xffffffffu, dv, g0 + 5);
         }
         T d;
         bool ok;

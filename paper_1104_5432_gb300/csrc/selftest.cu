@@ -51,13 +51,39 @@ __device__ double fma_rate_sink;
 
 // the FP64 path's logarithm table for the self-test and the probe (the
 // heat-bath kernels read the copy in the handle's work memory)
-__device__ double2 g_ln_tab[LN_TABLE_ENTRIES];
+__device__ double2 g_fp64_tab[FP64_TABLE_ENTRIES];
 
-int upload_ln_table()
+int upload_fp64_table()
 {
-    double2 tab[LN_TABLE_ENTRIES];
-    fill_ln_table(tab);
-    return cudaMemcpyToSymbol(g_ln_tab, tab, sizeof tab) == cudaSuccess ? SU2_OK : SU2_E_CUDA;
+    double2 tab[FP64_TABLE_ENTRIES];
+    fill_fp64_table(tab);
+    return cudaMemcpyToSymbol(g_fp64_tab, tab, sizeof tab) == cudaSuccess ? SU2_OK : SU2_E_CUDA;
+}
+
+// sincospi_tab against CUDA's sincospi: out[0] the cosine's largest
+// absolute error on the trials' grid y = (2k + 1) 2^-23 (k < 2^23), out[1]
+// the sine's and cosine's on the direction's grid y = (2k + 1) 2^-18
+// (k < 2^18)
+__global__ void trig_selftest_kernel(unsigned long long* out)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (1u << 23)) return;
+    double sn, cs, sref, cref;
+    sincospi_tab(2u * k + 1u, 23, g_fp64_tab, &sn, &cs);
+    sincospi(ldexp((double)(2u * k + 1u), -23), &sref, &cref);
+    double v[2] = {fabs(cs - cref), 0.0};
+    if (k < (1u << 18)) {
+        sincospi_tab(2u * k + 1u, 18, g_fp64_tab, &sn, &cs);
+        sincospi(ldexp((double)(2u * k + 1u), -18), &sref, &cref);
+        v[1] = fmax(fabs(sn - sref), fabs(cs - cref));
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        double m = v[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) atomic_max_pos(out + j, m);
+    }
 }
 
 // ln_u01_tab against CUDA's log on every grid point u = (2k + 1) 2^-24:
@@ -69,7 +95,7 @@ __global__ void ln_selftest_kernel(unsigned long long* out)
     if (k >= (1u << 23)) return;
     const uint32_t w = k << 9;
     const double ref = log(u01d(w));
-    const double err = fabs(ln_u01_tab(w, g_ln_tab) - ref);
+    const double err = fabs(ln_u01_tab(w, g_fp64_tab) - ref);
     const int ex = (int)((__double_as_longlong(ref) >> 52) & 0x7FF) - 1023;
     const double ulps = err / ldexp(1.0, ex - 52);
     double v[2] = {err, ulps};
@@ -112,7 +138,14 @@ __global__ void __launch_bounds__(256) special_rate_kernel(int iters)
         for (int j = 0; j < 8; ++j) {
             if (FN == SU2_PROBE_LOG) x[j] = log(x[j] + 2.0);
             else if (FN == SU2_PROBE_LN_TABLE)
-                x[j] = ln_u01_tab((uint32_t)__double_as_longlong(x[j]), g_ln_tab);
+                x[j] = ln_u01_tab((uint32_t)__double_as_longlong(x[j]), g_fp64_tab);
+            else if (FN == SU2_PROBE_COS_TABLE || FN == SU2_PROBE_SINCOS_TABLE) {
+                // an odd numerator below 2^24 from the previous result's bits
+                const uint32_t num = ((uint32_t)__double_as_longlong(x[j]) & 0xFFFFFEu) | 1u;
+                double sn, cs;
+                sincospi_tab(num, 23, g_fp64_tab, &sn, &cs);
+                x[j] = FN == SU2_PROBE_COS_TABLE ? cs : sn + cs;
+            }
             else if (FN == SU2_PROBE_COSPI) x[j] = cospi(x[j]);
             else if (FN == SU2_PROBE_SINCOSPI) {
                 double sn, cs;
@@ -165,13 +198,13 @@ int probe_blocks(unsigned* blocks)
 
 extern "C" int su2_probe_special_rate(int fn, int iters, double* calls_per_s, void* stream)
 {
-    if (!calls_per_s || iters <= 0 || fn < SU2_PROBE_LOG || fn > SU2_PROBE_LN_TABLE)
+    if (!calls_per_s || iters <= 0 || fn < SU2_PROBE_LOG || fn > SU2_PROBE_SINCOS_TABLE)
         return SU2_E_INVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned blocks = 0;
     if (int rc = su2::probe_blocks(&blocks)) return rc;
-    if (fn == SU2_PROBE_LN_TABLE)
-        if (int rc = su2::upload_ln_table()) return rc;
+    if (fn >= SU2_PROBE_LN_TABLE)
+        if (int rc = su2::upload_fp64_table()) return rc;
     float ms = 0.0f;
     auto launch = [&] {
         switch (fn) {
@@ -180,6 +213,8 @@ extern "C" int su2_probe_special_rate(int fn, int iters, double* calls_per_s, vo
         case SU2_PROBE_SINCOSPI: su2::special_rate_kernel<SU2_PROBE_SINCOSPI><<<blocks, 256, 0, s>>>(iters); break;
         case SU2_PROBE_SQRT: su2::special_rate_kernel<SU2_PROBE_SQRT><<<blocks, 256, 0, s>>>(iters); break;
         case SU2_PROBE_LN_TABLE: su2::special_rate_kernel<SU2_PROBE_LN_TABLE><<<blocks, 256, 0, s>>>(iters); break;
+        case SU2_PROBE_COS_TABLE: su2::special_rate_kernel<SU2_PROBE_COS_TABLE><<<blocks, 256, 0, s>>>(iters); break;
+        case SU2_PROBE_SINCOS_TABLE: su2::special_rate_kernel<SU2_PROBE_SINCOS_TABLE><<<blocks, 256, 0, s>>>(iters); break;
         default: su2::special_rate_kernel<SU2_PROBE_RSQRT><<<blocks, 256, 0, s>>>(iters); break;
         }
     };
@@ -220,9 +255,20 @@ extern "C" int su2_selftest_ln(void* out, void* stream)
 {
     if (!out) return SU2_E_INVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (int rc = su2::upload_ln_table()) return rc;
+    if (int rc = su2::upload_fp64_table()) return rc;
     if (cudaMemsetAsync(out, 0, 2 * sizeof(double), s) != cudaSuccess) return SU2_E_CUDA;
     su2::ln_selftest_kernel<<<(1u << 23) / 256, 256, 0, s>>>(
+        static_cast<unsigned long long*>(out));
+    return cudaGetLastError() == cudaSuccess ? SU2_OK : SU2_E_CUDA;
+}
+
+extern "C" int su2_selftest_trig(void* out, void* stream)
+{
+    if (!out) return SU2_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (int rc = su2::upload_fp64_table()) return rc;
+    if (cudaMemsetAsync(out, 0, 2 * sizeof(double), s) != cudaSuccess) return SU2_E_CUDA;
+    su2::trig_selftest_kernel<<<(1u << 23) / 256, 256, 0, s>>>(
         static_cast<unsigned long long*>(out));
     return cudaGetLastError() == cudaSuccess ? SU2_OK : SU2_E_CUDA;
 }

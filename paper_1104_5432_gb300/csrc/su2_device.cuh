@@ -247,11 +247,6 @@ __device__ __forceinline__ double u01d(uint32_t w)
 {
     return exact_double((int32_t)(2u * (w >> 9) + 1u), -24);
 }
-// twice that, the argument of cospi for cos(2 pi u)
-__device__ __forceinline__ double two_u01d(uint32_t w)
-{
-    return exact_double((int32_t)(2u * (w >> 9) + 1u), -23);
-}
 // uniform in (0,1) from an 18-bit integer k: (k + 0.5) 2^-18, exact
 __device__ __forceinline__ float u18_bits(uint32_t k)
 {

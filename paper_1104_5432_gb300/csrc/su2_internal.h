@@ -106,7 +106,7 @@ struct LatDesc {
     uint32_t Vq;            // site pairs per parity (Vh / 2) when paired
     double creutz_below;    // alpha below which Creutz's draw replaces Kennedy-Pendleton's
     float creutz_below_f;
-    const double2* ln_table;  // ln_u01_tab's table (in the handle's work memory)
+    const double2* fp64_table;  // the FP64 path's log and sin/cos tables (work memory)
     uint64_t link_off;      // byte offset of this lattice in the link buffer
     uint64_t field_off;     // double offset of its Polyakov field
     // per call
@@ -178,10 +178,9 @@ cudaError_t launch_phase(const Ctx& c, int row, int cfg, int mu, int parity, boo
                          int32_t* dbg_trials, bool hybrid, cudaStream_t s);
 cudaError_t launch_sweep_end(const Ctx& c, bool plaq, cudaStream_t s);
 
-// the table of the FP64 path's logarithm (ln_u01_tab, su2_math.cuh), filled
-// on the host: 256 intervals, then ln 2 as hi + lo
-constexpr int LN_TABLE_ENTRIES = 257;
-void fill_ln_table(double2* tab);
+// the tables of the FP64 path's logarithm and sine/cosine (ln_u01_tab,
+// sincospi_tab, su2_math.cuh: layout TAB_*), filled on the host
+void fill_fp64_table(double2* tab);
 
 // The whole sweep of a small single FP32 lattice in one thread-block
 // cluster (cluster.cu): launch index NUM_LAUNCH_CFG.

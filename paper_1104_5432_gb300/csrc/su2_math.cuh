@@ -1,8 +1,10 @@
 // su2_math.cuh -- the transcendental pieces of the heat-bath draw.
 //
-// FP64 uses CUDA's accurate double functions (the reciprocal square root
-// through rsqrt, within 1 ulp, instead of a division by sqrt; the sine of
-// the direction's angle as a shifted cospi).  FP32 uses
+// FP64 takes ln u and sin/cos(2 pi u) of its uniforms from tables and short
+// series (ln_u01_tab, sincospi_tab, at the end of this file; each checked
+// on every grid point against CUDA's log and sincospi by su2_selftest_ln /
+// su2_selftest_trig), and CUDA's accurate sqrt and rsqrt (the reciprocal
+// square root within 1 ulp, instead of a division by sqrt).  FP32 uses
 // short forms whose
 // error is bounded well inside the FP32 parity budget (2e-5 per link):
 //   ln u       for u on the uniform grid ((k + 1/2) 2^-23):
@@ -110,9 +112,8 @@ template <> struct Math<double> {
         const double c = cospi(mul_(2.0, r));
         return mul_(c, c);
     }
-    // sin x = cos(x - pi/2): both from cospi, on exact arguments (2 r and
-    // 2 r - 1/2 for r on the uniform grid), so that the cooperative kernel
-    // can take them in the same instruction stream as a trial's cos(2 pi r2)
+    // (the FP64 kernels take these from sincospi_tab; kept for the generic
+    // forms)
     static __device__ __forceinline__ void sincos2pi(double r, double* s, double* c)
     {
         const double x = mul_(2.0, r);
@@ -137,7 +138,10 @@ template <> struct Math<double> {
 // ln 2 = hi + lo with hi's low mantissa bits zero, so that n hi is exact.
 // Ten FP64 instructions against ~30 instruction times for a general log:
 // on GB300 the FP64 unit is the heat bath's bottleneck in FP64.
-// tab: 256 intervals, then (ln 2 hi, ln 2 lo) (fill_ln_table, su2_internal.h)
+// The FP64 tables (fill_fp64_table): the logarithm's 256 intervals, ln 2
+// as (hi, lo), then (cos, sin) of pi j / 128, j = 0 .. 255.
+constexpr int TAB_LN = 0, TAB_LN2 = 256, TAB_TRIG = 257, FP64_TABLE_ENTRIES = 513;
+
 __device__ __forceinline__ double ln_u01_tab(uint32_t w, const double2* __restrict__ tab)
 {
     const uint32_t a = 2u * (w >> 9) + 1u;  // u = a 2^-24, 1 <= a < 2^24
@@ -147,8 +151,8 @@ __device__ __forceinline__ double ln_u01_tab(uint32_t w, const double2* __restri
     const int h = t >= 128 ? 1 : 0;         // M >= 1.5: m = M / 2
     const int n = p - 24 + h;
     const double m = exact_double((int32_t)a, -p - h);
-    const double2 e = __ldg(tab + t);       // (g, -ln g)
-    const double2 l2 = __ldg(tab + 256);    // (ln 2 hi, ln 2 lo)
+    const double2 e = __ldg(tab + TAB_LN + t);  // (g, -ln g)
+    const double2 l2 = __ldg(tab + TAB_LN2);    // (ln 2 hi, ln 2 lo)
     const double r = fma_(m, e.x, -1.0);
     double q = fma_(r, -1.0 / 6.0, 0.2);
     q = fma_(r, q, -0.25);
@@ -157,6 +161,34 @@ __device__ __forceinline__ double ln_u01_tab(uint32_t w, const double2* __restri
     const double lp = fma_(mul_(r, r), q, r);
     const double nd = n ? exact_double(n, 0) : 0.0;
     return add_(fma_(nd, l2.x, e.y), fma_(nd, l2.y, lp));
+}
+
+// sin(pi y) and cos(pi y) for y = num 2^-bits in [0, 2] (num <= 2^(bits+1),
+// bits >= 8), table-driven: y = j / 128 + d with j the nearest multiple
+// (read off the bits) and |d| <= 1/256, b = pi d, and from the table's
+// (cos, sin) of pi j / 128 = (C, S):
+//   cos(pi y) = C + (C (cos b - 1) - S sin b),
+//   sin(pi y) = S + (S (cos b - 1) + C sin b),
+// with cos b - 1 = b^2 (-1/2 + b^2 (1/24 - b^2 / 720)) and
+// sin b = b + b^3 (-1/6 + b^2 (1/120 - b^2 / 5040)), the Taylor series
+// (|b| <= pi/256: the first terms left out are below 1e-19).  Fifteen FP64
+// instructions for both, thirteen for the cosine alone, against ~15
+// instruction times for one general cospi.
+__device__ __forceinline__ void sincospi_tab(uint32_t num, int bits,
+                                             const double2* __restrict__ tab, double* sn,
+                                             double* cs)
+{
+    const int sh = bits - 7;
+    const uint32_t j = (num + (1u << (sh - 1))) >> sh;  // nearest j / 128
+    const int32_t res = (int32_t)num - (int32_t)(j << sh);  // d = res 2^-bits
+    const double2 t = __ldg(tab + TAB_TRIG + (j & 255u));  // (C, S)
+    // b = pi d: res 2^-bits exact, one rounding for the product with pi
+    const double b = res ? mul_(exact_double(res, -bits), 3.141592653589793) : 0.0;
+    const double b2 = mul_(b, b);
+    const double cm1 = mul_(b2, fma_(b2, fma_(b2, -1.0 / 720.0, 1.0 / 24.0), -0.5));
+    const double sb = fma_(mul_(b, b2), fma_(b2, fma_(b2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), b);
+    *cs = add_(t.x, fma_(t.x, cm1, neg_(mul_(t.y, sb))));
+    *sn = add_(t.y, fma_(t.y, cm1, mul_(t.x, sb)));
 }
 
 }  // namespace su2

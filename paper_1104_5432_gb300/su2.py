@@ -88,6 +88,7 @@ def load(build_if_needed: bool = True):
             "su2_plaquette_static": (i, [P, i, i, i, P, P]),
             "su2_selftest_math": (i, [P, P]),
             "su2_selftest_ln": (i, [P, P]),
+            "su2_selftest_trig": (i, [P, P]),
             "su2_get_links_f32": (i, [P, i, P]),
             "su2_set_links_f32": (i, [P, i, P]),
             "su2_probe_fma_rate": (i, [i, i, P, P]),
@@ -130,7 +131,8 @@ def probe_fma_rate(dtype: int, iters: Optional[int] = None) -> float:
     return v.value
 
 
-PROBE_LOG, PROBE_COSPI, PROBE_SINCOSPI, PROBE_SQRT, PROBE_RSQRT, PROBE_LN_TABLE = range(6)
+(PROBE_LOG, PROBE_COSPI, PROBE_SINCOSPI, PROBE_SQRT, PROBE_RSQRT, PROBE_LN_TABLE,
+ PROBE_COS_TABLE, PROBE_SINCOS_TABLE) = range(8)
 
 
 def probe_special_rate(fn: int, iters: int = 1024) -> float:

@@ -64,7 +64,8 @@ def test_oracle_all_cores_leg_small():
 class _FakeRates:
     """Stand-in for the throughput probes: fixed rates, no GPU."""
     F64 = 1
-    PROBE_LOG, PROBE_COSPI, PROBE_SINCOSPI, PROBE_SQRT, PROBE_RSQRT, PROBE_LN_TABLE = range(6)
+    (PROBE_LOG, PROBE_COSPI, PROBE_SINCOSPI, PROBE_SQRT, PROBE_RSQRT, PROBE_LN_TABLE,
+     PROBE_COS_TABLE, PROBE_SINCOS_TABLE) = range(8)
 
     @staticmethod
     def probe_fma_rate(dtype):
@@ -78,11 +79,12 @@ class _FakeRates:
 def test_fp64_roofline_follows_the_algorithmic_model():
     """T_roof = (420 + 10 t) / (2 x DFMA rate) + sum_f n_f / rate_f with the
     update's math-function calls (per trial 2 log + 1 cospi; 2 rsqrt,
-    2 sqrt, 1 sincospi); frac = achieved x T_roof.  The logarithm's rate is
-    that of the kernels' own table-driven logarithm (probe id 5)."""
+    2 sqrt, 1 sincospi); frac = achieved x T_roof.  The logarithm, cosine
+    and sine + cosine rates are those of the kernels' own table-driven
+    routines (probe ids 5, 6, 7)."""
     t = 1.04
     r = bench.fp64_roofline(_FakeRates, 1.2e9, t)
-    T = ((420 + 10 * t) / 1e12 + 2 * t / 6e10 + t / 2e10 + 1 / 3e10 + 2 / 4e10 + 2 / 5e10)
+    T = ((420 + 10 * t) / 1e12 + 2 * t / 6e10 + t / 7e10 + 1 / 8e10 + 2 / 4e10 + 2 / 5e10)
     assert r["peak"] == pytest.approx(1 / T, rel=1e-12)
     assert r["frac"] == pytest.approx(1.2e9 * T, abs=1e-4)
     assert r["algorithmic_flops_per_update"] == pytest.approx(430.4)

@@ -496,16 +496,32 @@ def test_special_function_rate_probe():
     fma = su2.probe_fma_rate(su2.F64)
     rates = {}
     for fn in (su2.PROBE_LOG, su2.PROBE_COSPI, su2.PROBE_SINCOSPI, su2.PROBE_SQRT,
-               su2.PROBE_RSQRT, su2.PROBE_LN_TABLE):
+               su2.PROBE_RSQRT, su2.PROBE_LN_TABLE, su2.PROBE_COS_TABLE,
+               su2.PROBE_SINCOS_TABLE):
         r = su2.probe_special_rate(fn)
         again = su2.probe_special_rate(fn)
         assert 0 < r < fma, (fn, r, fma)
         assert abs(again - r) <= 0.15 * r, (fn, r, again)
         rates[fn] = r
-    # the kernels' table-driven logarithm of a uniform beats the general one
+    # the kernels' table-driven logarithm of a uniform beats the general one,
+    # and their sine + cosine of a grid angle the general sincospi
     assert rates[su2.PROBE_LN_TABLE] > 1.5 * rates[su2.PROBE_LOG]
+    assert rates[su2.PROBE_SINCOS_TABLE] > rates[su2.PROBE_SINCOSPI]
     with pytest.raises(su2.SU2Error):
-        su2.probe_special_rate(6)
+        su2.probe_special_rate(8)
+
+
+def test_table_sine_cosine_on_every_grid_angle():
+    """The FP64 heat bath's table-driven cos(pi y) (and sin) against CUDA's
+    sincospi on every argument it is used on: the trials' 2^23 values
+    y = (2k + 1) 2^-23 and the direction's 2^18 values y = (2k + 1) 2^-18,
+    within 4.5e-16 absolute (each about 1 ulp of a value of size <= 1)."""
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    rc = su2.load().su2_selftest_trig(out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    err_trial, err_dir = out.cpu().tolist()
+    assert err_trial <= 4.5e-16 and err_dir <= 4.5e-16, (err_trial, err_dir)
 
 
 def test_table_logarithm_on_every_uniform():

@@ -26,8 +26,10 @@ struct ClusterLinks {
     uint32_t base;  // shared-window address of this CTA's links
     uint32_t C;     // links per (mu, parity) per CTA
     FastDiv div_c;
+    LinkCheck chk;  // bounds-checked builds: a bad index is recorded, link 0 read
     __device__ __forceinline__ Quat<float> load(int mu, int p, uint32_t eo) const
     {
+        if (!chk.ok(mu, p, eo)) eo = 0;
         const uint32_t r = fdiv(eo, div_c);
         const uint32_t a = base + (((uint32_t)(mu * 2 + p) * C + (eo - r * C)) << 4);
         uint32_t ra;
@@ -126,7 +128,10 @@ hb_cluster_kernel(Ctx ctx, uint32_t C, FastDiv div_c, int pl)
     }
     cluster_sync();  // every CTA's links are in place
 
-    const ClusterLinks CU{(uint32_t)__cvta_generic_to_shared(own), C, div_c};
+    ClusterLinks CU{(uint32_t)__cvta_generic_to_shared(own), C, div_c, {}};
+#ifdef SU2_CHECK_BOUNDS
+    CU.chk = {ctx.status, Vh};
+#endif
     double wplaq = 0.0;
     uint32_t ntrial = 0, ncap = 0;
     const bool plq = pl != 0;

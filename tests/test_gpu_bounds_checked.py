@@ -3,8 +3,9 @@ access checks its even/odd index and direction, and a bad one is recorded
 (SU2_E_BOUNDS at the next synchronising call) and skipped instead of
 touching memory.  The whole API surface runs on ragged batches in every
 launch shape of both precisions, with both samplers, slab walks, single
-phases with per-link trial output, link I/O and the measurements; no
-violation may be recorded.  (compute-sanitizer is not available, so the
+phases with per-link trial output, link I/O and the measurements, and the
+whole-sweep cluster kernel on single small FP32 lattices; no violation may
+be recorded.  (compute-sanitizer is not available, so the
 kernels check themselves.)"""
 import os
 import subprocess
@@ -42,6 +43,18 @@ for dtype in (su2.F32, su2.F64):
         for mu in range(4):
             for p in range(2):
                 L.heatbath_phase(2.2, mu, p, 3, trials)
+    if dtype == su2.F32:
+        # the whole-sweep cluster kernel (16 CTAs on 8^4 and 6^3 x 8, 8 on 10^4)
+        for Ns, Nt in ((8, 8), (6, 8), (10, 10)):
+            K = su2.Lattice(Ns, Nt, dtype)
+            K.set_launch_config(su2.LAUNCH_CLUSTER)
+            for creutz in (0.0, 1.7):
+                K.set_sampler(creutz)
+                K.init(su2.HOT, 3)
+                K.heatbath(0.9, 2, 4)
+                K.batch_heatbath_measure([2.3], 2, [4], 2)
+            K.sync()
+            K.close()
     x = L.get_links()
     L.set_links(x)
     L.set_links(x.astype(np.float32))
